@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the LEC-QMC sweep on GB300: Hubbard-Stratonovich field
+updates per second and sweeps per second, FP64 panels (the headline) and the
+mixed FP32-panel path on the same workload, with per-sweep latency.
+
+A step is one sweep of every chain of the workload (one persistent launch).
+Workload (synthetic, the dilute 2D Hubbard gas): 32x32 periodic square
+lattice, t = 1, U = +4, beta = 10, dtau = 0.05 (L = 200 slices), N_up = N_dn
+= 8, QR every 8 slices, 256 independent seeded chains.  Its device state
+(about 3 GB) is far larger than the 129 MB L2, so no flush is needed between
+steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank runs its own 256 chains (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HS field updates/sec & sweeps/sec vs plain FP64 same GPU; p50/p99 sweep latency"
+UNIT = "field-updates/s"
+FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64 (CUDA cores), the pool recipe's figure
+WORKLOAD = "gas32x32"
+
+
+def workload_desc(w, n_chains):
+    return ("dilute 2D Hubbard gas: %dx%d periodic square, t=1, U=%+.0f, beta=%g, dtau=%g (L=%d), N_up=N_dn=%d, "
+            "QR every %d slices, %d chains" % (w["lattice"][1], w["lattice"][2], w["U"], w["beta"], w["dtau"],
+                                               round(w["beta"] / w["dtau"]), w["n_up"], w["n_stab"], n_chains))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs (spawned worker processes, one chain each)
+# ---------------------------------------------------------------------------
+def _oracle_worker(conn, spec, seed, chain):
+    sys.path.insert(0, ROOT)
+    from oracle import OracleSim, lattices
+
+    lat = getattr(lattices, spec["lattice"][0])(*spec["lattice"][1:])
+    o = OracleSim(lat, spec["U"], spec["beta"], spec["dtau"], spec["n_up"], spec["n_dn"], spec["n_stab"], seed=seed,
+                  chain=chain, max_records=1024)
+    conn.send("ready")
+    while True:
+        cmd = conn.recv()
+        if cmd is None:
+            break
+        t0 = time.perf_counter()
+        o.sweep(int(cmd))
+        conn.send((int(o.stats()[0]), time.perf_counter() - t0))
+    conn.close()
+
+
+class OraclePool:
+    def __init__(self, spec, seed, n):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for c in range(n):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, spec, seed, c), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for a in self.conns:
+            assert a.recv() == "ready"
+
+    def step(self, nsweeps=1):
+        t0 = time.perf_counter()
+        for a in self.conns:
+            a.send(nsweeps)
+        res = [a.recv() for a in self.conns]
+        return time.perf_counter() - t0, res
+
+    def close(self):
+        for a in self.conns:
+            a.send(None)
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def oracle_cores():
+    return max(1, min(16, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()))
+
+
+def run_reference(args, spec, n_chains):
+    """--impl reference: the oracle as it stands, on the host cores."""
+    from paper_2601_08552_gb300 import inputs
+
+    P = oracle_cores()
+    pool = OraclePool(spec, inputs.SEED0, P)
+    upd = 2 * round(spec["beta"] / spec["dtau"]) * spec["lattice"][1] * spec["lattice"][2]
+    for _ in range(args.warmup):
+        pool.step(1)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = pool.step(1)
+        times.append(dt)
+    pool.close()
+    tot = sum(times)
+    value = P * upd * args.steps / tot
+    sample = "%d of the %d chains (one per host core), 1 sweep per chain per step" % (P, n_chains)
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * tot / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=workload_desc(spec, n_chains), sample=sample),
+                sweeps_per_s=P * args.steps / tot,
+                cpu_baseline=dict(value=value, unit=UNIT, cores=P, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(spec, n_chains):
+    from paper_2601_08552_gb300 import inputs
+
+    P = oracle_cores()
+    pool = OraclePool(spec, inputs.SEED0, P)
+    upd = 2 * round(spec["beta"] / spec["dtau"]) * spec["lattice"][1] * spec["lattice"][2]
+    dt, res = pool.step(1)
+    pool.close()
+    sample = "%d chains of the %d-chain workload, 1 sweep each, one process per host core (%.1f s wall)" % (
+        P, n_chains, dt)
+    return dict(value=P * upd / dt, unit=UNIT, cores=P, kind="oracle", sample=sample)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", bus_id], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=reasons, samples=len(rows))
+
+
+# ---------------------------------------------------------------------------
+# the GPU leg
+# ---------------------------------------------------------------------------
+def algorithmic_fp64_flops(spec, n_chains, accepts, attempts, G_bonds, prec):
+    """FP64 flops of one sweep of all chains: field-flip algebra (Sherman-
+    Morrison ratio and rank-1 update), and for FP64 panels the slice
+    propagation, the block Gram matrices and CholeskyQR2."""
+    N = spec["lattice"][1] * spec["lattice"][2]
+    L = round(spec["beta"] / spec["dtau"])
+    n = -(-L // spec["n_stab"])
+    ms = (spec["n_up"], spec["n_dn"])
+    a = accepts / max(attempts, 1)
+    per_attempt = sum(2 * m * m + 2 * m for m in ms) + a * sum(4 * m * m + m for m in ms)
+    flips = 2 * L * N * per_attempt
+    if prec == 0:
+        prop = sum(4 * L * (6 * G_bonds * m + N * m) for m in ms)
+        qr = sum(2 * n * 6 * N * m * m for m in ms)
+        gram = sum(2 * n * 2 * N * m * m for m in ms)
+    else:
+        prop = gram = 0
+        qr = sum(2 * n * 6 * N * m * m for m in ms)
+    return n_chains * (flips + prop + qr + gram)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2601_08552_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2601_08552_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get(kind)
+
+
+def time_steps(torch, sim, steps, stream):
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for k in range(steps):
+        sim.sweep(1, measure=True)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    return per
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    from paper_2601_08552_gb300 import inputs
+
+    w = inputs.WORKLOADS[WORKLOAD]
+    spec = {k: w[k] for k in ("lattice", "U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
+    n_chains = w["chains"]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, spec, n_chains)
+        return
+
+    # the CPU baseline runs first, in spawned processes, before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, n_chains)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2601_08552_gb300 as lq
+
+    stream = torch.cuda.current_stream()
+    lat = lq.Lattice.square(spec["lattice"][1], spec["lattice"][2])
+    N = lat.N
+    L = round(spec["beta"] / spec["dtau"])
+    upd_per_step = n_chains * 2 * L * N
+
+    def make(prec):
+        ids = [rank * n_chains + c for c in range(n_chains)]
+        s = lq.Sim([lat] * n_chains, [dict(spec, precision=prec, seed=inputs.SEED0)] * n_chains, chain_ids=ids,
+                   stream=stream.cuda_stream)
+        s.init()
+        return s
+
+    def run(prec):
+        sim = make(prec)
+        for _ in range(args.warmup):
+            sim.sweep(1, measure=True)
+        sim.sync()
+        st0 = sum(sim.stats(c) for c in range(n_chains))
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        props = torch.cuda.get_device_properties(local)
+        bus = "%08X:%02X:%02X.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+        clk = ClockSampler(bus) if prec == 0 else None
+        per = time_steps(torch, sim, args.steps, stream)
+        clocks = clk.stop() if clk else None
+        total_ms = sum(per)
+        if dist is not None:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        sim.sync()
+        st1 = sum(sim.stats(c) for c in range(n_chains))
+        d = st1 - st0
+        return sim, per, total_ms, clocks, d
+
+    sim, per, total_ms, clocks, dstat = run(0)
+    value = world * upd_per_step * args.steps / (total_ms * 1e-3)
+    sweeps = world * n_chains * args.steps / (total_ms * 1e-3)
+    flops = algorithmic_fp64_flops(spec, n_chains, dstat[1], dstat[0], lat.n_bonds, 0)
+    kern_ms = total_ms / args.steps
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    roofline = dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=achieved / FP64_PEAK_TFLOPS, traffic=profiled_traffic("fp64_bytes_per_launch"),
+                    kernel="lq::sweep_kernel<double>", flops_per_launch=flops,
+                    peak_source="GB300 dense FP64 1.25 TFLOP/s (pool recipe table); 1.19 measured by FMA loop")
+
+    # end to end through the C ABI on pinned host buffers
+    n_occ = spec["n_up"] + spec["n_dn"]
+    hf = torch.empty(n_chains * L * N, dtype=torch.int8, pin_memory=True)
+    ho = torch.empty(n_chains * n_occ, dtype=torch.int32, pin_memory=True)
+    for c in range(n_chains):
+        hf[c * L * N:(c + 1) * L * N] = torch.from_numpy(sim.get_fields(c).ravel())
+        u, dn = sim.get_fock(c)
+        ho[c * n_occ:(c + 1) * n_occ] = torch.from_numpy(np.concatenate([u, dn]).astype(np.int32))
+    hf_out = torch.empty_like(hf).pin_memory()
+    ho_out = torch.empty_like(ho).pin_memory()
+    rec = torch.empty(n_chains * lq.LQ_NOBS, dtype=torch.float64, pin_memory=True)
+    e2e_times = []
+    for k in range(args.e2e_steps + 1):
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        sim.run_host(hf, ho, 1, True, hf_out, ho_out, rec)
+        dt = time.perf_counter() - t0
+        hf, hf_out = hf_out, hf
+        ho, ho_out = ho_out, ho
+        if k > 0:
+            e2e_times.append(dt)
+    e2e_s = sum(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = dict(value=world * upd_per_step * len(e2e_times) / e2e_s, unit=UNIT,
+               h2d_bytes_per_step=int(hf.numel() + 4 * ho.numel()),
+               d2h_bytes_per_step=int(hf.numel() + 4 * ho.numel() + 8 * rec.numel()),
+               call="lq_sim_run_host (upload, QR-chain rebuild, 1 sweep, download)")
+    bytes_dev = sim.device_bytes()
+    sim.close()
+    del sim
+
+    mixed = None
+    if not args.no_mixed:
+        msim, mper, mtotal, _, mstat = run(1)
+        mixed = dict(value=world * upd_per_step * args.steps / (mtotal * 1e-3), unit=UNIT,
+                     sweeps_per_s=world * n_chains * args.steps / (mtotal * 1e-3),
+                     p50_ms=float(np.percentile(mper, 50)), p99_ms=float(np.percentile(mper, 99)),
+                     field_accept=float(mstat[1] / max(mstat[0], 1)),
+                     precision="FP32 panels and block Gram; FP64 QR, inverses, ratios")
+        mixed["speedup_vs_fp64"] = mixed["value"] / value
+        msim.close()
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f64", data="synthetic",
+                    config=dict(workload=workload_desc(spec, n_chains), chains_per_gpu=n_chains, N=N, L=L,
+                                n_up=spec["n_up"], n_dn=spec["n_dn"], n_stab=spec["n_stab"], U=spec["U"],
+                                l2="device state %.1f GB per GPU >> 129 MB L2; no flush" % (bytes_dev / 1e9),
+                                parallelism="independent chains, %d per GPU" % n_chains),
+                    sweeps_per_s=sweeps, p50_ms=float(np.percentile(per, 50)), p99_ms=float(np.percentile(per, 99)),
+                    field_accept=float(dstat[1] / max(dstat[0], 1)),
+                    swap_accept=float(dstat[3] / max(dstat[2], 1)),
+                    roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
+                    mixed=mixed)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

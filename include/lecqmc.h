@@ -1,0 +1,207 @@
+/*
+ * lecqmc.h -- C ABI of the GB300 (sm_103a) library for the hot path of
+ * linear canonical-ensemble QMC (LEC-QMC, Hong, Chen, Xu, arXiv 2601.08552).
+ *
+ * The library runs Markov chains of the canonical-ensemble determinant QMC of
+ * the Hubbard model H = sum_ij K_ij c^dag_i c_j + U sum_i n_iup n_idn
+ * (Eq. 5) at fixed N_up and N_dn.  A configuration is a pair (eta, s): a Fock
+ * state (ordered occupied sites per spin, the columns of P_eta) and discrete
+ * Hubbard-Stratonovich fields s[slice][site] = +-1.  Its weight is
+ * prod_sigma det[P^T B_sigma(beta,0) P] (Eq. 1) with
+ * B(beta,0) = B_{L-1} ... B_0 and B_l = e^{-dtau K} e^{-dtau V(s_l)}.
+ * A sweep is: field updates over all slices upward, N_up then N_dn
+ * particle-hole swaps by the stabilized QR update (removal by Givens
+ * rotations, addition by propagating one column and orthogonalising it, SM
+ * Sec. I), then field updates downward with measurements at the
+ * stabilization boundaries.  Cost O(beta N N_e^2) per sweep.
+ *
+ * Conventions
+ *  - Every call returns lq_status; nothing throws or exits across the ABI.
+ *    lq_last_error() gives a thread-local message for the last failure.
+ *  - Pointers named host_* or documented as host arrays are caller-owned host
+ *    memory; the library copies them.  The library owns its device memory.
+ *  - Handles are not thread-safe: use one handle per thread.
+ *  - Work is queued on the CUDA stream given at creation; calls that return
+ *    data to the host synchronize that stream first.  lq_sim_sync() reports
+ *    deferred device errors (LQ_ENUMERIC for a singular overlap, a CholeskyQR
+ *    breakdown or a non-finite ratio).
+ *  - Indices are 0-based: slices 0..L-1 (L = round(beta/dtau)), sites
+ *    0..N-1, spin 0 = up, 1 = down.
+ */
+#ifndef LECQMC_H
+#define LECQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LQ_OK = 0,
+  LQ_EINVAL = 1,      /* bad argument (range, size, null) */
+  LQ_ENOMEM = 2,      /* device or host allocation failed */
+  LQ_ECUDA = 3,       /* a CUDA runtime call failed */
+  LQ_ENUMERIC = 4,    /* singular overlap, QR breakdown or non-finite ratio */
+  LQ_ETIMEOUT = 5,    /* a bounded device wait gave up */
+  LQ_EBUSY = 6,       /* a queue is full */
+  LQ_ENOTFOUND = 7,   /* no such request / result not ready */
+  LQ_EUNSUPPORTED = 8 /* a size outside what this build supports */
+} lq_status;
+
+/* precision of the N x N_sigma panels (slice propagation and block Gram
+ * products); QR, log-det factors, the N_sigma x N_sigma inverses and all
+ * Metropolis ratios are FP64 in both modes. */
+#define LQ_FP64 0
+#define LQ_MIXED 1
+
+/* observables of one sweep record: the mean over the measurements of the
+ * sweep of sign * O (index 0 is the sign itself). */
+#define LQ_NOBS 9
+#define LQ_OBS_SIGN 0
+#define LQ_OBS_NUP 1   /* sum_i <n_i,up> (= N_up, an invariant) */
+#define LQ_OBS_NDN 2
+#define LQ_OBS_DOCC 3  /* (1/N) sum_i <n_i,up n_i,dn> */
+#define LQ_OBS_EKIN 4  /* (1/N) sum_sigma sum_ij K_ij <c^dag_i c_j> */
+#define LQ_OBS_SZZ00 5 /* <S^z_A S^z_A> / (N/2), sublattice label 0 */
+#define LQ_OBS_SZZ11 6
+#define LQ_OBS_SZZ01 7
+#define LQ_OBS_SPAR 8  /* S^par(q=0) = (1/(N/2)) sum_ij <S^x_i S^x_j + S^y_i S^y_j> */
+
+/* largest particle number per spin this build supports */
+#define LQ_MAX_PARTICLES 32
+
+typedef struct lq_lattice lq_lattice;
+typedef struct lq_sim lq_sim;
+
+/* ---- lattices (the hopping matrix K; Eq. 5 and SM Sec. III) ------------ */
+
+/* K from bonds: K_ij = K_ji = kij[b] for b = (bi[b], bj[b]), plus an optional
+ * onsite term onsite[i] (K_ii) and an optional sublattice label 0/1 per site
+ * (default i % 2).  The bond order fixes the checkerboard: each bond goes to
+ * the lowest family in which neither of its sites is used yet, and
+ * e^{-dtau K} is applied as E_{G-1} ... E_0 C_eps with E_g the exact product
+ * of the 2x2 bond exponentials of family g and C_eps = diag(e^{-dtau K_ii}).
+ * All arrays are host arrays of n_bonds (or n_sites) entries; copied.
+ * Errors: LQ_EINVAL for n_sites < 1, a site out of range, i == j. */
+lq_status lq_lattice_from_bonds(int32_t n_sites, int32_t n_bonds, const int32_t* bi, const int32_t* bj,
+                                const double* kij, const double* onsite, const int32_t* sublattice,
+                                lq_lattice** out);
+/* 1D chain, K = -t on (i, i+1): bonds with even i, then odd i (periodic wrap
+ * in the odd group). Sublattice i % 2. */
+lq_status lq_lattice_chain(int32_t n_sites, double t, int32_t periodic, lq_lattice** out);
+/* Lx x Ly square lattice, site x + Lx*y, K = -t: x-bonds with even x, odd x,
+ * y-bonds with even y, odd y.  Sublattice (x + y) % 2. */
+lq_status lq_lattice_square(int32_t lx, int32_t ly, double t, int32_t periodic, lq_lattice** out);
+/* One-dimensional BCL flat-band model, H_eff(k) = S(k) S(k)^dag with
+ * S1 = t1 + t2 e^{-ik}, S2 = t3 + t4 e^{-ik} (SM Sec. III): sites
+ * A1_R = 2R, A2_R = 2R+1; onsite t1^2+t2^2 (A1), t3^2+t4^2 (A2); hoppings
+ * A1_R-A1_{R+1} t1 t2, A2_R-A2_{R+1} t3 t4, A1_R-A2_R t1 t3 + t2 t4,
+ * A1_R-A2_{R+1} t1 t4, A1_R-A2_{R-1} t2 t3.  The lowest band is exactly flat
+ * at 0.  Sublattice A1 = 0, A2 = 1. */
+lq_status lq_lattice_flatband(int32_t n_cells, double t1, double t2, double t3, double t4, int32_t periodic,
+                              lq_lattice** out);
+/* Two-leg cross-stitch ladder: rung -t_intra, legs -t_leg, crossings
+ * a_R-b_{R+1}, b_R-a_{R+1} of -t_cross (flat band at +t_intra). */
+lq_status lq_lattice_cross_stitch(int32_t n_cells, double t_intra, double t_leg, double t_cross, int32_t periodic,
+                                  lq_lattice** out);
+/* sizes: sites, bonds, checkerboard families */
+lq_status lq_lattice_info(const lq_lattice* lat, int32_t* n_sites, int32_t* n_bonds, int32_t* n_families);
+/* the bond list in build order with each bond's family (host arrays of n_bonds) */
+lq_status lq_lattice_bonds(const lq_lattice* lat, int32_t* bi, int32_t* bj, double* kij, int32_t* family);
+lq_status lq_lattice_destroy(lq_lattice* lat);
+
+/* ---- simulations -------------------------------------------------------- */
+
+typedef struct {
+  double U;        /* Hubbard U: U > 0 spin-channel HS, U < 0 charge channel */
+  double beta;     /* inverse temperature */
+  double dtau;     /* Trotter step; L = round(beta/dtau) must be within 1e-9 */
+  int32_t n_up, n_dn;
+  int32_t n_stab;  /* tau_w: slices between QR restabilizations */
+  int32_t precision; /* LQ_FP64 or LQ_MIXED */
+  uint64_t seed;   /* Philox4x32-10 key */
+} lq_params;
+
+/* optional device allocator (e.g. a framework's caching allocator); stream is
+ * the cudaStream_t the memory is used on.  NULL -> cudaMalloc/cudaFree. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+} lq_allocator;
+
+/* Create n_chains independent chains.  lattices[c] and params[c] describe
+ * chain c (sizes may differ between chains; all chains share one precision).
+ * chain_ids (nullable) gives the Philox chain word of each chain (default c).
+ * cuda_stream is a cudaStream_t (NULL = default stream).  Fields start at +1
+ * and occupations at the first N_sigma sites until lq_sim_init or the setters
+ * run.  Errors: LQ_EINVAL (a parameter out of range),
+ * LQ_EUNSUPPORTED (n_up or n_dn > LQ_MAX_PARTICLES), LQ_ENOMEM. */
+lq_status lq_sim_create(const lq_lattice* const* lattices, const lq_params* params, int32_t n_chains,
+                        const uint32_t* chain_ids, void* cuda_stream, const lq_allocator* alloc, lq_sim** out);
+/* Draw fields (uniform +-1) and Fock states (Fisher-Yates, sorted) from each
+ * chain's seed on the device, then build the QR chains.  Asynchronous. */
+lq_status lq_sim_init(lq_sim* sim);
+/* Fields of one chain from a host array (L x N, row = slice, values +-1);
+ * rebuilds that chain's QR chains.  Errors: LQ_EINVAL for a value != +-1. */
+lq_status lq_sim_set_fields(lq_sim* sim, int32_t chain, const int8_t* host_s);
+lq_status lq_sim_get_fields(lq_sim* sim, int32_t chain, int8_t* host_s);
+/* Ordered occupied sites (the columns of P) of one chain; rebuilds its chains.
+ * Errors: LQ_EINVAL for a repeated or out-of-range site. */
+lq_status lq_sim_set_fock(lq_sim* sim, int32_t chain, const int32_t* host_occ_up, const int32_t* host_occ_dn);
+lq_status lq_sim_get_fock(lq_sim* sim, int32_t chain, int32_t* host_occ_up, int32_t* host_occ_dn);
+/* Set the sweep counter of every chain (the Philox counter word). */
+lq_status lq_sim_set_sweep_index(lq_sim* sim, uint32_t sweep);
+/* n_sweeps sweeps of every chain in one persistent launch (one CTA per
+ * chain, longest chains first).  measure != 0 appends one record per sweep.
+ * Asynchronous on the stream. */
+lq_status lq_sim_sweep(lq_sim* sim, int32_t n_sweeps, int32_t measure);
+/* One stateless batch call on host buffers: upload every chain's fields
+ * (host_fields: chains concatenated, each L x N) and Fock state (host_occ:
+ * each chain's n_up then n_dn sites), rebuild the QR chains, run n_sweeps
+ * sweeps, and download the final fields, occupations (same layouts, either
+ * output nullable) and the records of this call (host_records: each chain's
+ * n_sweeps x LQ_NOBS, nullable; needs measure != 0).  Synchronous.  Fields
+ * other than +-1 or repeated sites give LQ_EINVAL (checked on the device). */
+lq_status lq_sim_run_host(lq_sim* sim, const int8_t* host_fields, const int32_t* host_occ, int32_t n_sweeps,
+                          int32_t measure, int8_t* host_fields_out, int32_t* host_occ_out, double* host_records);
+/* Wait for the stream; LQ_ENUMERIC if any chain flagged a numerical error. */
+lq_status lq_sim_sync(lq_sim* sim);
+/* log|W| and sign of chain c recomputed from freshly built QR chains (this
+ * also resets the tracked weight). */
+lq_status lq_sim_log_weight(lq_sim* sim, int32_t chain, double* log_abs, int32_t* sign);
+/* log|W| and sign tracked through the accepted ratios since the last build. */
+lq_status lq_sim_tracked_weight(lq_sim* sim, int32_t chain, double* log_abs, int32_t* sign);
+/* Test hook: ratio W(s with s[slice][site] flipped) / W(s), through the
+ * stabilized Green's function at that slice on freshly built chains. */
+lq_status lq_sim_field_ratio(lq_sim* sim, int32_t chain, int32_t slice, int32_t site, double* r);
+/* Test hook: ratio of removing column k of spin `spin` and adding site j
+ * (not occupied), by the Givens / Gram-Schmidt QR update; parts (nullable,
+ * 6 doubles) = log|r|, sign, log|r_remove|, sign, log|r_add|, sign. */
+lq_status lq_sim_swap_ratio(lq_sim* sim, int32_t chain, int32_t spin, int32_t k, int32_t j, double* r,
+                            double* parts);
+/* Per-sweep records of chain c: *n_records rows of LQ_NOBS doubles into
+ * host_out (capacity max_rows rows). */
+lq_status lq_sim_records(lq_sim* sim, int32_t chain, int32_t max_rows, int32_t* n_records, double* host_out);
+lq_status lq_sim_clear_records(lq_sim* sim);
+/* counters of chain c: field attempts, field accepts, swap attempts, swap accepts */
+lq_status lq_sim_stats(lq_sim* sim, int32_t chain, int64_t* host_counts4);
+/* Test hook: panel j of the right (side 0) or left (side 1) chain of a spin,
+ * as FP64 host arrays Q (N x N_sigma) and V (N_sigma x N_sigma, nullable). */
+lq_status lq_sim_chain_panel(lq_sim* sim, int32_t chain, int32_t side, int32_t spin, int32_t j, double* host_Q,
+                             double* host_V);
+/* sizes of chain c: N, L, tau_w, n blocks, n_up, n_dn */
+lq_status lq_sim_chain_info(const lq_sim* sim, int32_t chain, int32_t* info6);
+/* device bytes held by the simulation */
+lq_status lq_sim_device_bytes(const lq_sim* sim, size_t* bytes);
+lq_status lq_sim_destroy(lq_sim* sim);
+
+const char* lq_last_error(void);
+const char* lq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LECQMC_H */

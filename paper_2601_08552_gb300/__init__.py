@@ -1,0 +1,6 @@
+"""GB300-native (sm_103a) hot path of linear canonical-ensemble QMC (LEC-QMC).
+
+The sweep runs in the CUDA library built from ``csrc/`` (C ABI in
+``include/lecqmc.h``); ``lecqmc`` is its ctypes binding.
+"""
+from .lecqmc import (LQ_FP64, LQ_MIXED, LQ_NOBS, OBS_NAMES, Lattice, LqError, Sim, load)  # noqa: F401

@@ -1,0 +1,736 @@
+// lq_api.cpp -- host runtime behind the C ABI in include/lecqmc.h: lattices
+// in checkerboard form, one device arena per simulation, chain descriptors,
+// and the launches of the sm_103a kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lecqmc.h"
+#include "lq_device.h"
+#include "lq_kernels.h"
+
+static thread_local std::string g_err;
+
+static lq_status fail(lq_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+static lq_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(LQ_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// lattices
+// ---------------------------------------------------------------------------
+struct lq_lattice {
+  int N = 0;
+  std::vector<int> bi, bj, sub, fam;
+  std::vector<double> kb, eps;
+  bool has_eps = false;
+  int G = 0;
+};
+
+// each bond, in order, goes to the lowest family where neither site is used
+static void assign_families(lq_lattice* L) {
+  std::vector<std::vector<char>> used;
+  L->fam.assign(L->bi.size(), 0);
+  L->G = 0;
+  for (size_t b = 0; b < L->bi.size(); ++b) {
+    int g = 0;
+    for (;; ++g) {
+      if (g == (int)used.size()) used.emplace_back(L->N, 0);
+      if (!used[g][L->bi[b]] && !used[g][L->bj[b]]) break;
+    }
+    used[g][L->bi[b]] = used[g][L->bj[b]] = 1;
+    L->fam[b] = g;
+    L->G = std::max(L->G, g + 1);
+  }
+}
+
+static lq_status make_lattice(int N, const std::vector<int>& bi, const std::vector<int>& bj,
+                              const std::vector<double>& kb, const double* onsite, const int* sub, lq_lattice** out) {
+  if (!out) return fail(LQ_EINVAL, "null output pointer");
+  if (N < 1) return fail(LQ_EINVAL, "n_sites must be >= 1");
+  for (size_t b = 0; b < bi.size(); ++b) {
+    if (bi[b] < 0 || bi[b] >= N || bj[b] < 0 || bj[b] >= N || bi[b] == bj[b])
+      return fail(LQ_EINVAL, "bond " + std::to_string(b) + " has a bad site index");
+    if (!std::isfinite(kb[b])) return fail(LQ_EINVAL, "non-finite hopping");
+  }
+  lq_lattice* L = new (std::nothrow) lq_lattice();
+  if (!L) return fail(LQ_ENOMEM, "host allocation");
+  L->N = N;
+  L->bi = bi; L->bj = bj; L->kb = kb;
+  L->eps.assign(N, 0.0);
+  L->sub.resize(N);
+  for (int i = 0; i < N; ++i) {
+    if (onsite) { L->eps[i] = onsite[i]; if (onsite[i] != 0.0) L->has_eps = true; }
+    L->sub[i] = sub ? (sub[i] ? 1 : 0) : (i & 1);
+  }
+  assign_families(L);
+  *out = L;
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_lattice_from_bonds(int32_t n_sites, int32_t n_bonds, const int32_t* bi, const int32_t* bj,
+                                           const double* kij, const double* onsite, const int32_t* sublattice,
+                                           lq_lattice** out) {
+  if (n_bonds < 0 || (n_bonds > 0 && (!bi || !bj || !kij))) return fail(LQ_EINVAL, "bad bond arrays");
+  std::vector<int> vi(bi, bi + n_bonds), vj(bj, bj + n_bonds);
+  std::vector<double> vk(kij, kij + n_bonds);
+  return make_lattice(n_sites, vi, vj, vk, onsite, sublattice, out);
+}
+
+extern "C" lq_status lq_lattice_chain(int32_t n, double t, int32_t periodic, lq_lattice** out) {
+  if (n < 1) return fail(LQ_EINVAL, "n_sites must be >= 1");
+  std::vector<int> bi, bj;
+  std::vector<double> kb;
+  for (int parity = 0; parity < 2; ++parity) {
+    for (int i = parity; i + 1 < n; i += 2) { bi.push_back(i); bj.push_back(i + 1); kb.push_back(-t); }
+    if (periodic && n > 2 && (n - 1) % 2 == parity) { bi.push_back(n - 1); bj.push_back(0); kb.push_back(-t); }
+  }
+  return make_lattice(n, bi, bj, kb, nullptr, nullptr, out);
+}
+
+extern "C" lq_status lq_lattice_square(int32_t lx, int32_t ly, double t, int32_t periodic, lq_lattice** out) {
+  if (lx < 1 || ly < 1) return fail(LQ_EINVAL, "lx, ly must be >= 1");
+  std::vector<int> bi, bj, sub(lx * ly);
+  std::vector<double> kb;
+  auto idx = [lx](int x, int y) { return x + lx * y; };
+  for (int parity = 0; parity < 2; ++parity)
+    for (int y = 0; y < ly; ++y)
+      for (int x = parity; x < lx; x += 2) {
+        if (x + 1 < lx) { bi.push_back(idx(x, y)); bj.push_back(idx(x + 1, y)); kb.push_back(-t); }
+        else if (periodic && lx > 2) { bi.push_back(idx(x, y)); bj.push_back(idx(0, y)); kb.push_back(-t); }
+      }
+  for (int parity = 0; parity < 2; ++parity)
+    for (int y = parity; y < ly; y += 2)
+      for (int x = 0; x < lx; ++x) {
+        if (y + 1 < ly) { bi.push_back(idx(x, y)); bj.push_back(idx(x, y + 1)); kb.push_back(-t); }
+        else if (periodic && ly > 2) { bi.push_back(idx(x, y)); bj.push_back(idx(x, 0)); kb.push_back(-t); }
+      }
+  for (int y = 0; y < ly; ++y)
+    for (int x = 0; x < lx; ++x) sub[idx(x, y)] = (x + y) & 1;
+  return make_lattice(lx * ly, bi, bj, kb, nullptr, sub.data(), out);
+}
+
+extern "C" lq_status lq_lattice_flatband(int32_t nc, double t1, double t2, double t3, double t4, int32_t periodic,
+                                         lq_lattice** out) {
+  if (nc < 1) return fail(LQ_EINVAL, "n_cells must be >= 1");
+  const int N = 2 * nc;
+  auto A1 = [nc](int R) { return 2 * (((R % nc) + nc) % nc); };
+  auto A2 = [nc](int R) { return 2 * (((R % nc) + nc) % nc) + 1; };
+  const bool wrap = periodic && nc > 2;
+  const int nR = wrap ? nc : nc - 1;
+  std::vector<int> bi, bj;
+  std::vector<double> kb;
+  auto add = [&](int i, int j, double k) { if (k != 0.0) { bi.push_back(i); bj.push_back(j); kb.push_back(k); } };
+  for (int parity = 0; parity < 2; ++parity)
+    for (int R = parity; R < nR; R += 2) add(A1(R), A1(R + 1), t1 * t2);
+  for (int parity = 0; parity < 2; ++parity)
+    for (int R = parity; R < nR; R += 2) add(A2(R), A2(R + 1), t3 * t4);
+  for (int R = 0; R < nc; ++R) add(A1(R), A2(R), t1 * t3 + t2 * t4);
+  for (int R = 0; R < nc; ++R)
+    if (R + 1 < nc || wrap) add(A1(R), A2(R + 1), t1 * t4);
+  for (int R = 0; R < nc; ++R)
+    if (R - 1 >= 0 || wrap) add(A1(R), A2(R - 1), t2 * t3);
+  std::vector<double> eps(N);
+  for (int R = 0; R < nc; ++R) { eps[2 * R] = t1 * t1 + t2 * t2; eps[2 * R + 1] = t3 * t3 + t4 * t4; }
+  return make_lattice(N, bi, bj, kb, eps.data(), nullptr, out);
+}
+
+extern "C" lq_status lq_lattice_cross_stitch(int32_t nc, double t_intra, double t_leg, double t_cross,
+                                             int32_t periodic, lq_lattice** out) {
+  if (nc < 1) return fail(LQ_EINVAL, "n_cells must be >= 1");
+  auto a = [nc](int R) { return 2 * (R % nc); };
+  auto b = [nc](int R) { return 2 * (R % nc) + 1; };
+  const bool wrap = periodic && nc > 2;
+  const int nR = wrap ? nc : nc - 1;
+  std::vector<int> bi, bj;
+  std::vector<double> kb;
+  auto add = [&](int i, int j, double k) { bi.push_back(i); bj.push_back(j); kb.push_back(k); };
+  for (int R = 0; R < nc; ++R) add(a(R), b(R), -t_intra);
+  for (int leg = 0; leg < 2; ++leg)
+    for (int parity = 0; parity < 2; ++parity)
+      for (int R = parity; R < nR; R += 2) add(leg ? b(R) : a(R), leg ? b(R + 1) : a(R + 1), -t_leg);
+  for (int parity = 0; parity < 2; ++parity)
+    for (int R = parity; R < nR; R += 2) { add(a(R), b(R + 1), -t_cross); add(b(R), a(R + 1), -t_cross); }
+  return make_lattice(2 * nc, bi, bj, kb, nullptr, nullptr, out);
+}
+
+extern "C" lq_status lq_lattice_info(const lq_lattice* L, int32_t* n_sites, int32_t* n_bonds, int32_t* n_fam) {
+  if (!L) return fail(LQ_EINVAL, "null lattice");
+  if (n_sites) *n_sites = L->N;
+  if (n_bonds) *n_bonds = (int32_t)L->bi.size();
+  if (n_fam) *n_fam = L->G;
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_lattice_bonds(const lq_lattice* L, int32_t* bi, int32_t* bj, double* kij, int32_t* fam) {
+  if (!L) return fail(LQ_EINVAL, "null lattice");
+  for (size_t b = 0; b < L->bi.size(); ++b) {
+    if (bi) bi[b] = L->bi[b];
+    if (bj) bj[b] = L->bj[b];
+    if (kij) kij[b] = L->kb[b];
+    if (fam) fam[b] = L->fam[b];
+  }
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_lattice_destroy(lq_lattice* L) {
+  delete L;
+  return LQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// simulations
+// ---------------------------------------------------------------------------
+struct ChainHost {
+  int N, L, tw, n, ns[2];
+  int G, nb;
+  double cost;
+};
+
+struct lq_sim {
+  int n_chains = 0, prec = 0;
+  cudaStream_t st = nullptr;
+  lq_allocator alloc{};
+  bool has_alloc = false;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  std::vector<LqChainDev> h;     // host mirror of the descriptors
+  std::vector<ChainHost> info;
+  LqChainDev* d_chains = nullptr;
+  int* d_order = nullptr;        // chains by decreasing cost
+  int* d_single = nullptr;       // scratch list of one chain
+  int* d_queue = nullptr;
+  int* d_all = nullptr;          // 0..n-1
+  int M = 1, Nmax = 1, buf_bytes = 0, grid = 1;
+  bool mirror_fresh = false;
+};
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static lq_status pull(lq_sim* S) {
+  CK(cudaStreamSynchronize(S->st));
+  if (!S->mirror_fresh) {
+    CK(cudaMemcpy(S->h.data(), S->d_chains, sizeof(LqChainDev) * S->n_chains, cudaMemcpyDeviceToHost));
+    S->mirror_fresh = true;
+  }
+  return LQ_OK;
+}
+
+static lq_status check_chain(const lq_sim* S, int c) {
+  if (!S) return fail(LQ_EINVAL, "null simulation");
+  if (c < 0 || c >= S->n_chains) return fail(LQ_EINVAL, "chain index out of range");
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_create(const lq_lattice* const* lats, const lq_params* params, int32_t n_chains,
+                                   const uint32_t* chain_ids, void* stream, const lq_allocator* alloc, lq_sim** out) {
+  if (!out || !lats || !params || n_chains < 1) return fail(LQ_EINVAL, "bad arguments to lq_sim_create");
+  const int prec = params[0].precision;
+  if (prec != LQ_FP64 && prec != LQ_MIXED) return fail(LQ_EINVAL, "precision must be LQ_FP64 or LQ_MIXED");
+  std::vector<ChainHost> info(n_chains);
+  int M = 1, Nmax = 1;
+  for (int c = 0; c < n_chains; ++c) {
+    const lq_lattice* Lt = lats[c];
+    const lq_params& p = params[c];
+    if (!Lt) return fail(LQ_EINVAL, "null lattice for chain " + std::to_string(c));
+    if (p.precision != prec) return fail(LQ_EINVAL, "all chains must share one precision");
+    if (!(p.beta > 0) || !(p.dtau > 0) || !std::isfinite(p.U)) return fail(LQ_EINVAL, "beta, dtau must be > 0");
+    const double Lf = p.beta / p.dtau;
+    const long Ll = std::lround(Lf);
+    if (Ll < 1 || std::fabs(Lf - (double)Ll) > 1e-9 * std::max(1.0, Lf) || Ll > (1 << 24) - 1)
+      return fail(LQ_EINVAL, "beta/dtau must be a positive integer");
+    if (p.n_stab < 1) return fail(LQ_EINVAL, "n_stab must be >= 1");
+    if (p.n_up < 0 || p.n_dn < 0 || p.n_up > Lt->N || p.n_dn > Lt->N)
+      return fail(LQ_EINVAL, "particle numbers must be in [0, N]");
+    if (p.n_up > LQ_MAX_PARTICLES || p.n_dn > LQ_MAX_PARTICLES)
+      return fail(LQ_EUNSUPPORTED, "at most LQ_MAX_PARTICLES particles per spin");
+    ChainHost& ci = info[c];
+    ci.N = Lt->N; ci.L = (int)Ll; ci.tw = p.n_stab; ci.n = (ci.L + ci.tw - 1) / ci.tw;
+    ci.ns[0] = p.n_up; ci.ns[1] = p.n_dn; ci.G = Lt->G; ci.nb = (int)Lt->bi.size();
+    ci.cost = (double)ci.L * ci.N * (ci.ns[0] * ci.ns[0] + ci.ns[1] * ci.ns[1] + (3.0 * ci.G + 1) * (ci.ns[0] + ci.ns[1]) + 1);
+    M = std::max(M, std::max(ci.ns[0], ci.ns[1]));
+    Nmax = std::max(Nmax, ci.N);
+  }
+  lq_sim* S = new (std::nothrow) lq_sim();
+  if (!S) return fail(LQ_ENOMEM, "host allocation");
+  S->n_chains = n_chains;
+  S->prec = prec;
+  S->st = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) { S->alloc = *alloc; S->has_alloc = true; }
+  S->info = info;
+  S->M = M;
+  S->Nmax = Nmax;
+  const size_t PS = prec == LQ_FP64 ? sizeof(double) : sizeof(float);
+  // shared-memory staging buffer: at least one full column of the largest
+  // panel, and room for a chunk of rows in the flip loop
+  S->buf_bytes = (int)std::max<size_t>((size_t)Nmax * 8, 48 * 1024);
+  // arena layout
+  std::vector<size_t> off(n_chains);
+  size_t tot = 0;
+  auto lat_bytes = [&](int c) {
+    const ChainHost& ci = info[c];
+    return al256((ci.G + 1) * 4) + 3 * al256(ci.nb * 4) + 3 * al256(ci.nb * 8) + 2 * al256(ci.nb * 4) +
+           3 * al256(ci.N * 8) + al256(ci.N * 4) + al256(ci.N * 4);
+  };
+  const int max_records = 1 << 16;
+  auto chain_bytes = [&](int c) {
+    const ChainHost& ci = info[c];
+    size_t b = lat_bytes(c) + al256((size_t)ci.L * ci.N);
+    for (int sg = 0; sg < 2; ++sg) {
+      const size_t pn = (size_t)ci.N * ci.ns[sg], qn = (size_t)ci.ns[sg] * ci.ns[sg];
+      b += al256(std::max(ci.ns[sg], 1) * 4);
+      b += 2 * al256((ci.n + 1) * pn * PS) + 2 * al256((ci.n + 1) * qn * 8);
+      b += al256((ci.n + 1) * pn * PS) + al256((ci.n + 1) * qn * 8);
+      b += al256(ci.tw * pn * PS) + al256(pn * PS) + al256(pn * 8);
+    }
+    b += al256((size_t)2 * ci.N * 8) + al256((size_t)ci.n * LQ_NS_MAX * 2 * 8);
+    b += al256((size_t)max_records * LQ_NOBS * 8);
+    return b;
+  };
+  for (int c = 0; c < n_chains; ++c) { off[c] = tot; tot += chain_bytes(c); }
+  const size_t desc_off = tot;
+  tot += al256(sizeof(LqChainDev) * n_chains) + 4 * al256(sizeof(int) * (n_chains + 1));
+  S->arena_bytes = tot;
+  if (S->has_alloc) S->arena = (char*)S->alloc.alloc(S->alloc.ctx, tot, stream);
+  else if (cudaMalloc((void**)&S->arena, tot) != cudaSuccess) S->arena = nullptr;
+  if (!S->arena) { delete S; return fail(LQ_ENOMEM, "device arena of " + std::to_string(tot) + " bytes"); }
+  cudaError_t e = cudaMemsetAsync(S->arena, 0, tot, S->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+  if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "arena memset"); }
+  S->d_chains = (LqChainDev*)(S->arena + desc_off);
+  size_t o2 = desc_off + al256(sizeof(LqChainDev) * n_chains);
+  S->d_order = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
+  S->d_single = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
+  S->d_queue = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
+  S->d_all = (int*)(S->arena + o2);
+  // descriptors + host-side constant data (lattice tables, P = first sites)
+  S->h.resize(n_chains);
+  std::vector<char> stage;
+  for (int c = 0; c < n_chains; ++c) {
+    const lq_lattice* Lt = lats[c];
+    const lq_params& p = params[c];
+    const ChainHost& ci = info[c];
+    LqChainDev& D = S->h[c];
+    std::memset(&D, 0, sizeof(D));
+    char* base = S->arena + off[c];
+    size_t o = 0;
+    auto take = [&](size_t bytes) { char* q = base + o; o += al256(bytes); return q; };
+    // lattice, bonds sorted by family (stable)
+    std::vector<int> order(ci.nb);
+    for (int b = 0; b < ci.nb; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Lt->fam[a] < Lt->fam[b]; });
+    std::vector<int> fo(ci.G + 1, 0), vi(ci.nb), vj(ci.nb);
+    std::vector<double> vc(ci.nb), vs(ci.nb), vk(ci.nb), ce(ci.N), ep(ci.N);
+    std::vector<float> vcf(ci.nb), vsf(ci.nb), cef(ci.N);
+    for (int b = 0; b < ci.nb; ++b) fo[Lt->fam[b] + 1]++;
+    for (int g = 0; g < ci.G; ++g) fo[g + 1] += fo[g];
+    for (int t = 0; t < ci.nb; ++t) {
+      const int b = order[t];
+      vi[t] = Lt->bi[b]; vj[t] = Lt->bj[b]; vk[t] = Lt->kb[b];
+      vc[t] = std::cosh(p.dtau * Lt->kb[b]);
+      vs[t] = -std::sinh(p.dtau * Lt->kb[b]);
+      vcf[t] = (float)vc[t]; vsf[t] = (float)vs[t];
+    }
+    for (int i = 0; i < ci.N; ++i) { ep[i] = Lt->eps[i]; ce[i] = std::exp(-p.dtau * Lt->eps[i]); cef[i] = (float)ce[i]; }
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+      return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S->st);
+    };
+    int* d_fo = (int*)take((ci.G + 1) * 4);
+    int* d_bi = (int*)take(ci.nb * 4);
+    int* d_bj = (int*)take(ci.nb * 4);
+    (void)take(ci.nb * 4);
+    double* d_bc = (double*)take(ci.nb * 8);
+    double* d_bs = (double*)take(ci.nb * 8);
+    double* d_bk = (double*)take(ci.nb * 8);
+    float* d_bcf = (float*)take(ci.nb * 4);
+    float* d_bsf = (float*)take(ci.nb * 4);
+    double* d_ce = (double*)take(ci.N * 8);
+    double* d_ep = (double*)take(ci.N * 8);
+    (void)take(ci.N * 8);
+    float* d_cef = (float*)take(ci.N * 4);
+    int* d_sub = (int*)take(ci.N * 4);
+    std::vector<cudaError_t> es;
+    es.push_back(up(d_fo, fo.data(), fo.size() * 4));
+    if (ci.nb) {
+      es.push_back(up(d_bi, vi.data(), ci.nb * 4)); es.push_back(up(d_bj, vj.data(), ci.nb * 4));
+      es.push_back(up(d_bc, vc.data(), ci.nb * 8)); es.push_back(up(d_bs, vs.data(), ci.nb * 8));
+      es.push_back(up(d_bk, vk.data(), ci.nb * 8));
+      es.push_back(up(d_bcf, vcf.data(), ci.nb * 4)); es.push_back(up(d_bsf, vsf.data(), ci.nb * 4));
+    }
+    es.push_back(up(d_ce, ce.data(), ci.N * 8)); es.push_back(up(d_ep, ep.data(), ci.N * 8));
+    es.push_back(up(d_cef, cef.data(), ci.N * 4)); es.push_back(up(d_sub, Lt->sub.data(), ci.N * 4));
+    // the staging vectors must outlive the async copies
+    for (cudaError_t ee : es)
+      if (ee != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(ee, "lattice upload"); }
+    e = cudaStreamSynchronize(S->st);
+    if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "lattice upload"); }
+    D.lat.N = ci.N; D.lat.nb = ci.nb; D.lat.G = ci.G;
+    D.lat.fam_off = d_fo; D.lat.bond_i = d_bi; D.lat.bond_j = d_bj;
+    D.lat.bond_c = d_bc; D.lat.bond_s = d_bs; D.lat.bond_cf = d_bcf; D.lat.bond_sf = d_bsf; D.lat.bond_k = d_bk;
+    D.lat.ceps = Lt->has_eps ? d_ce : nullptr;
+    D.lat.cepsf = Lt->has_eps ? d_cef : nullptr;
+    D.lat.eps = Lt->has_eps ? d_ep : nullptr;
+    D.lat.sub = d_sub;
+    D.N = ci.N; D.L = ci.L; D.tw = ci.tw; D.n = ci.n; D.ns[0] = ci.ns[0]; D.ns[1] = ci.ns[1];
+    D.charge = p.U < 0;
+    D.prec = prec;
+    D.lambda = std::acosh(std::exp(p.dtau * std::fabs(p.U) / 2.0));
+    D.dfac_p = std::exp(D.lambda); D.dfac_m = std::exp(-D.lambda);
+    D.delta_p = std::expm1(-2.0 * D.lambda); D.delta_m = std::expm1(2.0 * D.lambda);
+    D.cfac_p = std::exp(2.0 * D.lambda); D.cfac_m = std::exp(-2.0 * D.lambda);
+    D.key0 = (uint32_t)p.seed; D.key1 = (uint32_t)(p.seed >> 32);
+    D.chain_id = chain_ids ? chain_ids[c] : (uint32_t)c;
+    D.sweep = 0;
+    D.s = (int8_t*)take((size_t)ci.L * ci.N);
+    for (int sg = 0; sg < 2; ++sg) {
+      const size_t pn = (size_t)ci.N * ci.ns[sg], qn = (size_t)ci.ns[sg] * ci.ns[sg];
+      D.occ[sg] = (int*)take(std::max(ci.ns[sg], 1) * 4);
+      D.QR[sg][0] = take((ci.n + 1) * pn * PS);
+      D.QR[sg][1] = take((ci.n + 1) * pn * PS);
+      D.VR[sg][0] = (double*)take((ci.n + 1) * qn * 8);
+      D.VR[sg][1] = (double*)take((ci.n + 1) * qn * 8);
+      D.QL[sg] = take((ci.n + 1) * pn * PS);
+      D.VL[sg] = (double*)take((ci.n + 1) * qn * 8);
+      D.stored[sg] = take(ci.tw * pn * PS);
+      D.live[sg] = take(pn * PS);
+      D.work[sg] = take(pn * 8);
+      D.cur[sg] = 0;
+    }
+    D.vec = (double*)take((size_t)2 * ci.N * 8);
+    D.rot = (double*)take((size_t)ci.n * LQ_NS_MAX * 2 * 8);
+    D.records = (double*)take((size_t)max_records * LQ_NOBS * 8);
+    D.max_records = max_records;
+    D.sign = 1;
+    // default state: all fields +1, the first N_sigma sites occupied
+    std::vector<int8_t> s(ci.L * (size_t)ci.N, 1);
+    e = cudaMemcpy(D.s, s.data(), s.size(), cudaMemcpyHostToDevice);
+    for (int sg = 0; sg < 2 && e == cudaSuccess; ++sg) {
+      std::vector<int> occ(std::max(ci.ns[sg], 1));
+      for (int a = 0; a < ci.ns[sg]; ++a) occ[a] = a;
+      e = cudaMemcpy(D.occ[sg], occ.data(), occ.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "state upload"); }
+  }
+  // order: decreasing cost (longest chains first)
+  std::vector<int> ord(n_chains), all(n_chains);
+  for (int c = 0; c < n_chains; ++c) ord[c] = all[c] = c;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return info[a].cost > info[b].cost; });
+  e = cudaMemcpy(S->d_chains, S->h.data(), sizeof(LqChainDev) * n_chains, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(S->d_order, ord.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(S->d_all, all.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "descriptor upload"); }
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = lq::smem_bytes(S->M, S->Nmax, S->buf_bytes);
+  int per_sm = lq::max_active_sweep_ctas(prec, smem);
+  if (per_sm < 1) { lq_sim_destroy(S); return fail(LQ_EUNSUPPORTED, "shared-memory plan does not fit one CTA per SM"); }
+  S->grid = std::min(n_chains, sms * per_sm);
+  S->mirror_fresh = false;
+  // build the chains for the default state
+  e = lq::launch_build(prec, S->d_chains, S->d_all, n_chains, S->M, S->Nmax, S->buf_bytes, S->grid, S->st);
+  if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "initial chain build"); }
+  *out = S;
+  return LQ_OK;
+}
+
+static lq_status rebuild(lq_sim* S, const int* d_list, int n) {
+  S->mirror_fresh = false;
+  cudaError_t e = lq::launch_build(S->prec, S->d_chains, d_list, n, S->M, S->Nmax, S->buf_bytes,
+                                   std::min(n, S->grid), S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "chain build");
+  return LQ_OK;
+}
+
+static lq_status rebuild_one(lq_sim* S, int c) {
+  CK(cudaMemcpyAsync(S->d_single, &c, sizeof(int), cudaMemcpyHostToDevice, S->st));
+  CK(cudaStreamSynchronize(S->st));
+  return rebuild(S, S->d_single, 1);
+}
+
+extern "C" lq_status lq_sim_init(lq_sim* S) {
+  if (!S) return fail(LQ_EINVAL, "null simulation");
+  S->mirror_fresh = false;
+  cudaError_t e = lq::launch_init(S->d_chains, S->d_all, S->n_chains, std::min(S->n_chains, 1024), S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "init");
+  return rebuild(S, S->d_all, S->n_chains);
+}
+
+extern "C" lq_status lq_sim_set_fields(lq_sim* S, int32_t c, const int8_t* hs) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if (!hs) return fail(LQ_EINVAL, "null field array");
+  if ((st = pull(S)) != LQ_OK) return st;
+  const ChainHost& ci = S->info[c];
+  for (size_t k = 0; k < (size_t)ci.L * ci.N; ++k)
+    if (hs[k] != 1 && hs[k] != -1) return fail(LQ_EINVAL, "fields must be +-1");
+  CK(cudaMemcpy(S->h[c].s, hs, (size_t)ci.L * ci.N, cudaMemcpyHostToDevice));
+  return rebuild_one(S, c);
+}
+
+extern "C" lq_status lq_sim_get_fields(lq_sim* S, int32_t c, int8_t* hs) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if ((st = pull(S)) != LQ_OK) return st;
+  CK(cudaMemcpy(hs, S->h[c].s, (size_t)S->info[c].L * S->info[c].N, cudaMemcpyDeviceToHost));
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_set_fock(lq_sim* S, int32_t c, const int32_t* up, const int32_t* dn) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if ((st = pull(S)) != LQ_OK) return st;
+  const ChainHost& ci = S->info[c];
+  const int32_t* in[2] = {up, dn};
+  for (int sg = 0; sg < 2; ++sg) {
+    if (ci.ns[sg] && !in[sg]) return fail(LQ_EINVAL, "null occupation array");
+    std::vector<char> seen(ci.N, 0);
+    for (int a = 0; a < ci.ns[sg]; ++a) {
+      const int i = in[sg][a];
+      if (i < 0 || i >= ci.N || seen[i]) return fail(LQ_EINVAL, "occupations must be distinct sites in [0, N)");
+      seen[i] = 1;
+    }
+  }
+  for (int sg = 0; sg < 2; ++sg)
+    if (ci.ns[sg]) CK(cudaMemcpy(S->h[c].occ[sg], in[sg], ci.ns[sg] * 4, cudaMemcpyHostToDevice));
+  return rebuild_one(S, c);
+}
+
+extern "C" lq_status lq_sim_get_fock(lq_sim* S, int32_t c, int32_t* up, int32_t* dn) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if ((st = pull(S)) != LQ_OK) return st;
+  const ChainHost& ci = S->info[c];
+  int32_t* outp[2] = {up, dn};
+  for (int sg = 0; sg < 2; ++sg)
+    if (ci.ns[sg] && outp[sg]) CK(cudaMemcpy(outp[sg], S->h[c].occ[sg], ci.ns[sg] * 4, cudaMemcpyDeviceToHost));
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_set_sweep_index(lq_sim* S, uint32_t sweep) {
+  if (!S) return fail(LQ_EINVAL, "null simulation");
+  lq_status st = pull(S);
+  if (st != LQ_OK) return st;
+  for (auto& D : S->h) D.sweep = sweep;
+  CK(cudaMemcpy(S->d_chains, S->h.data(), sizeof(LqChainDev) * S->n_chains, cudaMemcpyHostToDevice));
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) {
+  if (!S || n_sweeps < 0) return fail(LQ_EINVAL, "bad arguments to lq_sim_sweep");
+  if (n_sweeps == 0) return LQ_OK;
+  S->mirror_fresh = false;
+  cudaError_t e = lq::launch_sweep(S->prec, S->d_chains, S->d_order, S->n_chains, S->d_queue, n_sweeps, measure,
+                                   S->M, S->Nmax, S->buf_bytes, S->grid, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_run_host(lq_sim* S, const int8_t* hf, const int32_t* ho, int32_t n_sweeps,
+                                     int32_t measure, int8_t* hf_out, int32_t* ho_out, double* hrec) {
+  if (!S || !hf || !ho || n_sweeps < 0) return fail(LQ_EINVAL, "bad arguments to lq_sim_run_host");
+  lq_status st = pull(S);
+  if (st != LQ_OK) return st;
+  size_t fo = 0, oo = 0;
+  for (int c = 0; c < S->n_chains; ++c) {
+    const ChainHost& ci = S->info[c];
+    const LqChainDev& D = S->h[c];
+    const size_t nf = (size_t)ci.L * ci.N;
+    CK(cudaMemcpyAsync(D.s, hf + fo, nf, cudaMemcpyHostToDevice, S->st));
+    for (int sg = 0; sg < 2; ++sg) {
+      if (ci.ns[sg]) CK(cudaMemcpyAsync(D.occ[sg], ho + oo, ci.ns[sg] * 4, cudaMemcpyHostToDevice, S->st));
+      oo += ci.ns[sg];
+    }
+    fo += nf;
+  }
+  cudaError_t e = lq::launch_clear_records(S->d_chains, S->n_chains, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear records");
+  if ((st = rebuild(S, S->d_all, S->n_chains)) != LQ_OK) return st;
+  if ((st = lq_sim_sweep(S, n_sweeps, measure)) != LQ_OK) return st;
+  S->mirror_fresh = false;
+  if ((st = pull(S)) != LQ_OK) return st;
+  for (int c = 0; c < S->n_chains; ++c)
+    if (S->h[c].err & LQ_ERR_BADINPUT) return fail(LQ_EINVAL, "chain " + std::to_string(c) + ": fields must be +-1 and occupied sites distinct in [0, N)");
+  fo = 0;
+  oo = 0;
+  for (int c = 0; c < S->n_chains; ++c) {
+    const ChainHost& ci = S->info[c];
+    const LqChainDev& D = S->h[c];
+    const size_t nf = (size_t)ci.L * ci.N;
+    if (hf_out) CK(cudaMemcpyAsync(hf_out + fo, D.s, nf, cudaMemcpyDeviceToHost, S->st));
+    for (int sg = 0; sg < 2; ++sg) {
+      if (ho_out && ci.ns[sg]) CK(cudaMemcpyAsync(ho_out + oo, D.occ[sg], ci.ns[sg] * 4, cudaMemcpyDeviceToHost, S->st));
+      oo += ci.ns[sg];
+    }
+    if (hrec && measure)
+      CK(cudaMemcpyAsync(hrec + (size_t)c * n_sweeps * LQ_NOBS, D.records, sizeof(double) * n_sweeps * LQ_NOBS,
+                         cudaMemcpyDeviceToHost, S->st));
+    fo += nf;
+  }
+  CK(cudaStreamSynchronize(S->st));
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_sync(lq_sim* S) {
+  if (!S) return fail(LQ_EINVAL, "null simulation");
+  S->mirror_fresh = false;
+  lq_status st = pull(S);
+  if (st != LQ_OK) return st;
+  for (int c = 0; c < S->n_chains; ++c)
+    if (S->h[c].err & LQ_ERR_BADINPUT)
+      return fail(LQ_EINVAL, "chain " + std::to_string(c) + " was given invalid fields or occupations");
+  for (int c = 0; c < S->n_chains; ++c)
+    if (S->h[c].err)
+      return fail(LQ_ENUMERIC, "chain " + std::to_string(c) + " reported numerical error flags " +
+                                   std::to_string(S->h[c].err));
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_log_weight(lq_sim* S, int32_t c, double* la, int32_t* sg) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if ((st = rebuild_one(S, c)) != LQ_OK) return st;
+  if ((st = pull(S)) != LQ_OK) return st;
+  if (la) *la = S->h[c].hook[6];
+  if (sg) *sg = (int32_t)S->h[c].hook[7];
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_tracked_weight(lq_sim* S, int32_t c, double* la, int32_t* sg) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if ((st = pull(S)) != LQ_OK) return st;
+  if (la) *la = S->h[c].logw;
+  if (sg) *sg = S->h[c].sign;
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_field_ratio(lq_sim* S, int32_t c, int32_t l, int32_t i, double* r) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if (l < 0 || l >= S->info[c].L || i < 0 || i >= S->info[c].N) return fail(LQ_EINVAL, "slice or site out of range");
+  if ((st = rebuild_one(S, c)) != LQ_OK) return st;
+  S->mirror_fresh = false;
+  cudaError_t e = lq::launch_field_ratio(S->prec, S->d_chains, c, l, i, S->M, S->Nmax, S->buf_bytes, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "field ratio");
+  if ((st = pull(S)) != LQ_OK) return st;
+  if (r) *r = S->h[c].hook[0];
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_swap_ratio(lq_sim* S, int32_t c, int32_t sg, int32_t k, int32_t j, double* r,
+                                       double* parts) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  const ChainHost& ci = S->info[c];
+  if (sg < 0 || sg > 1 || k < 0 || k >= ci.ns[sg] || j < 0 || j >= ci.N) return fail(LQ_EINVAL, "bad swap indices");
+  if ((st = pull(S)) != LQ_OK) return st;
+  std::vector<int> occ(ci.ns[sg]);
+  CK(cudaMemcpy(occ.data(), S->h[c].occ[sg], ci.ns[sg] * 4, cudaMemcpyDeviceToHost));
+  for (int a = 0; a < ci.ns[sg]; ++a)
+    if (occ[a] == j) return fail(LQ_EINVAL, "target site is occupied");
+  if ((st = rebuild_one(S, c)) != LQ_OK) return st;
+  S->mirror_fresh = false;
+  cudaError_t e = lq::launch_swap_ratio(S->prec, S->d_chains, c, sg, k, j, S->M, S->Nmax, S->buf_bytes, S->st);
+  if (e != cudaSuccess) return cuda_fail(e, "swap ratio");
+  if ((st = pull(S)) != LQ_OK) return st;
+  const double* h = S->h[c].hook;
+  if (r) *r = h[1] * std::exp(h[0]);
+  if (parts) for (int q = 0; q < 6; ++q) parts[q] = h[q];
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_records(lq_sim* S, int32_t c, int32_t max_rows, int32_t* n, double* out) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if ((st = pull(S)) != LQ_OK) return st;
+  const int k = std::min(S->h[c].nrec, std::max(max_rows, 0));
+  if (n) *n = S->h[c].nrec;
+  if (k > 0 && out) CK(cudaMemcpy(out, S->h[c].records, sizeof(double) * k * LQ_NOBS, cudaMemcpyDeviceToHost));
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_clear_records(lq_sim* S) {
+  if (!S) return fail(LQ_EINVAL, "null simulation");
+  lq_status st = pull(S);
+  if (st != LQ_OK) return st;
+  for (auto& D : S->h) D.nrec = 0;
+  CK(cudaMemcpy(S->d_chains, S->h.data(), sizeof(LqChainDev) * S->n_chains, cudaMemcpyHostToDevice));
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_stats(lq_sim* S, int32_t c, int64_t* out) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if ((st = pull(S)) != LQ_OK) return st;
+  for (int k = 0; k < 4; ++k) out[k] = S->h[c].cnt[k];
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_chain_panel(lq_sim* S, int32_t c, int32_t side, int32_t sg, int32_t j, double* Q,
+                                        double* V) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  const ChainHost& ci = S->info[c];
+  if (sg < 0 || sg > 1 || j < 0 || j > ci.n || side < 0 || side > 1) return fail(LQ_EINVAL, "bad panel index");
+  if ((st = pull(S)) != LQ_OK) return st;
+  const LqChainDev& D = S->h[c];
+  const size_t pn = (size_t)ci.N * ci.ns[sg], qn = (size_t)ci.ns[sg] * ci.ns[sg];
+  const size_t PS = S->prec == LQ_FP64 ? 8 : 4;
+  const char* qsrc = (const char*)(side ? D.QL[sg] : D.QR[sg][D.cur[sg]]) + j * pn * PS;
+  if (Q && pn) {
+    if (PS == 8) CK(cudaMemcpy(Q, qsrc, pn * 8, cudaMemcpyDeviceToHost));
+    else {
+      std::vector<float> tmp(pn);
+      CK(cudaMemcpy(tmp.data(), qsrc, pn * 4, cudaMemcpyDeviceToHost));
+      for (size_t k = 0; k < pn; ++k) Q[k] = tmp[k];
+    }
+  }
+  if (V && qn) {
+    const double* vsrc = (side ? D.VL[sg] : D.VR[sg][D.cur[sg]]) + j * qn;
+    CK(cudaMemcpy(V, vsrc, qn * 8, cudaMemcpyDeviceToHost));
+  }
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_chain_info(const lq_sim* S, int32_t c, int32_t* info6) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  const ChainHost& ci = S->info[c];
+  info6[0] = ci.N; info6[1] = ci.L; info6[2] = ci.tw; info6[3] = ci.n; info6[4] = ci.ns[0]; info6[5] = ci.ns[1];
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_device_bytes(const lq_sim* S, size_t* bytes) {
+  if (!S || !bytes) return fail(LQ_EINVAL, "null argument");
+  *bytes = S->arena_bytes;
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_destroy(lq_sim* S) {
+  if (!S) return LQ_OK;
+  if (S->arena) {
+    cudaStreamSynchronize(S->st);
+    if (S->has_alloc) S->alloc.free(S->alloc.ctx, S->arena, S->arena_bytes, S->st);
+    else cudaFree(S->arena);
+  }
+  delete S;
+  return LQ_OK;
+}
+
+extern "C" const char* lq_last_error(void) { return g_err.c_str(); }
+extern "C" const char* lq_version(void) { return "lecqmc-gb300 0.1 (sm_103a)"; }

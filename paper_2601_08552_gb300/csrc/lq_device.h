@@ -1,0 +1,68 @@
+// Device-side descriptors shared by the host runtime (lq_api.cpp) and the
+// CUDA kernels (lq_kernels.cu).  Plain structs of pointers and sizes; one
+// LqChainDev per Markov chain lives in device memory and is updated in place
+// by the sweep kernel.
+#pragma once
+#include <stdint.h>
+
+#define LQ_NOBS 9          // sign, n_up, n_dn, docc, ekin, szz_00, szz_11, szz_01, s_par
+#define LQ_NS_MAX 32       // particles per spin handled by the flip warps (one lane per column)
+#define LQ_THREADS 256     // threads per CTA (one CTA per chain)
+
+// Error bits a kernel may set in LqChainDev::err.
+#define LQ_ERR_SINGULAR 1  // a Gram / overlap matrix had a zero pivot
+#define LQ_ERR_CHOLESKY 2  // CholeskyQR2 broke down (non-positive pivot)
+#define LQ_ERR_NONFINITE 4 // a ratio or a log-weight became NaN / Inf
+#define LQ_ERR_BADINPUT 8  // a field != +-1 or a repeated / out-of-range occupied site
+
+// Lattice in checkerboard form: bonds sorted by family (stable in the bond
+// order the lattice was built with); family g owns bonds [fam_off[g], fam_off[g+1]).
+struct LqLatticeDev {
+  int N, nb, G;
+  const int* fam_off;       // G + 1
+  const int* bond_i;        // nb
+  const int* bond_j;        // nb
+  const double* bond_c;     // cosh(dtau k_b)
+  const double* bond_s;     // -sinh(dtau k_b)
+  const float* bond_cf;     // the same in FP32 (mixed-precision panels)
+  const float* bond_sf;
+  const double* bond_k;     // k_b (kinetic-energy measurement)
+  const double* ceps;       // exp(-dtau eps_i), or nullptr when eps == 0
+  const float* cepsf;
+  const double* eps;        // onsite eps_i, or nullptr
+  const int* sub;           // sublattice label 0/1
+};
+
+struct LqChainDev {
+  LqLatticeDev lat;
+  int N, L, tw, n;          // sites, slices, slices per block, blocks
+  int ns[2];                // particles per spin
+  int charge;               // 1: U < 0 (charge channel)
+  int prec;                 // 0: FP64 panels, 1: FP32 panels (mixed)
+  double lambda;
+  double dfac_p, dfac_m;    // e^{+lambda}, e^{-lambda}
+  double delta_p, delta_m;  // e^{-2 lambda} - 1, e^{+2 lambda} - 1
+  double cfac_p, cfac_m;    // e^{+2 lambda}, e^{-2 lambda} (charge-channel scalar ratio)
+  uint32_t key0, key1, chain_id, sweep;
+  // configuration
+  int8_t* s;                // L x N fields, row = slice
+  int* occ[2];              // ordered occupied sites (columns of P)
+  // chains: panels are N x ns row-major, of the panel type (double or float)
+  void* QR[2][2];           // right chain Q^R_0..Q^R_n, two buffers per spin
+  double* VR[2][2];         // V^R_1..V^R_n (index 0 unused), two buffers per spin
+  int cur[2];               // current buffer of the right chain
+  void* QL[2];              // left chain Q^L_0..Q^L_n
+  double* VL[2];            // V^L_0..V^L_{n-1}
+  void* stored[2];          // tau_w panels of the block being updated
+  void* live[2];            // the propagated panel of the block
+  void* work[2];            // one scratch panel (measurement)
+  double* vec;              // 2 x N scratch vectors (particle addition)
+  double* rot;              // n x LQ_NS_MAX x 2 Givens coefficients
+  double* records;          // max_records x LQ_NOBS
+  int max_records, nrec;
+  double logw;              // tracked log|W|
+  int sign;                 // tracked sign
+  int err;
+  long long cnt[4];         // field attempts, field accepts, swap attempts, swap accepts
+  double hook[8];           // test-hook outputs
+};

@@ -1,0 +1,1294 @@
+// lq_kernels.cu -- sm_103a kernels for the canonical-ensemble DQMC sweep with
+// the stabilized QR update (LEC-QMC, arXiv 2601.08552).
+//
+// One CTA owns one Markov chain for a whole sweep (persistent over a queue of
+// chains, longest first).  Inside a CTA:
+//   * slice propagation (B_l = e^{-dtau K} e^{-dtau V(s_l)}, Eq. 1 and the
+//     Trotter form of SM Sec. V) streams column chunks of an N x N_sigma panel
+//     through shared memory and applies the checkerboard families there;
+//   * restabilization every tau_w slices (B_i Q_{i-1} = Q_i V_i, SM Sec. I.A)
+//     is CholeskyQR2 with FP64 Gram matrices and a positive diagonal;
+//   * field flips (the Sherman-Morrison ratio of SM Sec. V) run on two warps,
+//     one per spin, exchanging the two g values through shared memory once
+//     per site, so two resident chains per SM keep all four FP64 pipes busy;
+//   * particle-hole swaps: removal by permutation + Givens retriangulation
+//     (Eqs. S9-S12), addition by propagating one vector and orthogonalising
+//     it twice against each Q_i (Eqs. S1-S8, Eq. 4);
+//   * equal-time measurements at the block boundaries of the down pass.
+// Panels are FP64 (LQ_FP64) or FP32 (LQ_MIXED); the N_sigma x N_sigma algebra,
+// QR, log-det factors and all ratios stay FP64 in both.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lq_device.h"
+#include "lq_kernels.h"
+
+namespace lq {
+
+// ---------------------------------------------------------------------------
+// shared-memory plan (same arithmetic on host and device)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct SmemPlan {
+  int M, MP, Nmax, buf_bytes;
+  size_t off_T0, off_T1, off_W, off_S, off_vec, off_red, off_obs, off_gx, off_ip, off_occ, off_bits, off_chain, off_buf,
+      total;
+};
+
+__host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
+  SmemPlan p;
+  p.M = M < 1 ? 1 : M;
+  p.MP = p.M | 1;
+  p.Nmax = Nmax;
+  p.buf_bytes = buf_bytes;
+  size_t mat = (size_t)p.M * p.MP * 8;
+  size_t o = 0;
+  p.off_T0 = o; o = al16(o + mat);
+  p.off_T1 = o; o = al16(o + mat);
+  p.off_W = o; o = al16(o + (size_t)p.M * 2 * p.MP * 8);  // Gauss-Jordan / Gram workspace
+  p.off_S = o; o = al16(o + 6 * mat);                       // six small matrices
+  p.off_vec = o; o = al16(o + (size_t)10 * p.M * 8);
+  p.off_red = o; o = al16(o + 64 * 8);
+  p.off_obs = o; o = al16(o + 16 * 8);
+  p.off_gx = o; o = al16(o + 8 * 8);
+  p.off_ip = o; o = al16(o + 32 * 4);
+  p.off_occ = o; o = al16(o + (size_t)2 * p.M * 4);
+  p.off_bits = o; o = al16(o + (size_t)(Nmax / 32 + 2) * 4);
+  p.off_chain = o; o = al16(o + sizeof(LqChainDev));
+  p.off_buf = o; o = al16(o + (size_t)buf_bytes);
+  p.total = o;
+  return p;
+}
+
+size_t smem_bytes(int M, int Nmax, int buf_bytes) { return plan_smem(M, Nmax, buf_bytes).total; }
+
+struct Smem {
+  double* T[2];
+  double* W;     // M x 2MP
+  double* S;     // 6 x (M x MP)
+  double* vec;   // 10 x M
+  double* red;
+  double* obs;
+  double* gx;
+  int* ip;
+  int* occ2;     // 2 x M ints
+  unsigned* bits;
+  LqChainDev* C;
+  void* buf;
+  int buf_bytes, M, MP;
+};
+
+__device__ inline Smem carve(const SmemPlan& p, char* base) {
+  Smem s;
+  s.T[0] = (double*)(base + p.off_T0);
+  s.T[1] = (double*)(base + p.off_T1);
+  s.W = (double*)(base + p.off_W);
+  s.S = (double*)(base + p.off_S);
+  s.vec = (double*)(base + p.off_vec);
+  s.red = (double*)(base + p.off_red);
+  s.obs = (double*)(base + p.off_obs);
+  s.gx = (double*)(base + p.off_gx);
+  s.ip = (int*)(base + p.off_ip);
+  s.occ2 = (int*)(base + p.off_occ);
+  s.bits = (unsigned*)(base + p.off_bits);
+  s.C = (LqChainDev*)(base + p.off_chain);
+  s.buf = (void*)(base + p.off_buf);
+  s.buf_bytes = p.buf_bytes;
+  s.M = p.M;
+  s.MP = p.MP;
+  return s;
+}
+
+#define TID ((int)threadIdx.x)
+#define FULL 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and 53-bit uniforms
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                                       uint32_t out[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ double dfac(const LqChainDev& C, int sigma, int s) {
+  int sp = C.charge ? 1 : (sigma == 0 ? 1 : -1);
+  return (sp * s > 0) ? C.dfac_p : C.dfac_m;
+}
+__device__ __forceinline__ double delta_of(const LqChainDev& C, int sigma, int s) {
+  int sp = C.charge ? 1 : (sigma == 0 ? 1 : -1);
+  return (sp * s > 0) ? C.delta_p : C.delta_m;
+}
+
+template <class R> __device__ __forceinline__ const R* bc_ptr(const LqLatticeDev& L);
+template <> __device__ __forceinline__ const double* bc_ptr<double>(const LqLatticeDev& L) { return L.bond_c; }
+template <> __device__ __forceinline__ const float* bc_ptr<float>(const LqLatticeDev& L) { return L.bond_cf; }
+template <class R> __device__ __forceinline__ const R* bs_ptr(const LqLatticeDev& L);
+template <> __device__ __forceinline__ const double* bs_ptr<double>(const LqLatticeDev& L) { return L.bond_s; }
+template <> __device__ __forceinline__ const float* bs_ptr<float>(const LqLatticeDev& L) { return L.bond_sf; }
+template <class R> __device__ __forceinline__ const R* ceps_ptr(const LqLatticeDev& L);
+template <> __device__ __forceinline__ const double* ceps_ptr<double>(const LqLatticeDev& L) { return L.ceps; }
+template <> __device__ __forceinline__ const float* ceps_ptr<float>(const LqLatticeDev& L) { return L.cepsf; }
+
+__device__ __forceinline__ void bar_pair() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+// CTA-wide sum in a fixed order (deterministic).
+__device__ double cta_sum(double v, Smem& sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  __syncthreads();
+  if ((TID & 31) == 0) sm.red[TID >> 5] = v;
+  __syncthreads();
+  if (TID < 32) {
+    double t = (TID < LQ_THREADS / 32) ? sm.red[TID] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+    if (TID == 0) sm.red[40] = t;
+  }
+  __syncthreads();
+  return sm.red[40];
+}
+
+// ---------------------------------------------------------------------------
+// Propagation: dst <- D_post * Op * D_pre * src for an N x m panel.
+// op: 0 none, 1 B_K = E_{G-1}..E_0 C_eps, 2 B_K^T = C_eps E_0..E_{G-1}.
+// Columns are independent, so the panel goes through shared memory in column
+// chunks; each family is one parallel pass of 2x2 rotations there.
+// ---------------------------------------------------------------------------
+template <class R, class S>
+__device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m, int ld, int preD, int op, int postD,
+                     Smem& sm) {
+  if (m == 0) return;
+  const int N = C.N;
+  const LqLatticeDev& lat = C.lat;
+  R* buf = (R*)sm.buf;
+  int cmax = sm.buf_bytes / (int)(sizeof(R) * N);
+  if (cmax > m) cmax = m;
+  const int8_t* spre = preD >= 0 ? C.s + (size_t)preD * N : nullptr;
+  const int8_t* spost = postD >= 0 ? C.s + (size_t)postD * N : nullptr;
+  const R* ceps = ceps_ptr<R>(lat);
+  const R* bcv = bc_ptr<R>(lat);
+  const R* bsv = bs_ptr<R>(lat);
+  for (int c0 = 0; c0 < m; c0 += cmax) {
+    const int cw = min(cmax, m - c0);
+    const int tot = N * cw;
+    for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+      int i = idx / cw, a = idx - i * cw;
+      R v = (R)src[(size_t)i * ld + c0 + a];
+      if (spre) v *= (R)dfac(C, sigma, spre[i]);
+      if (op == 1 && ceps) v *= ceps[i];
+      buf[idx] = v;
+    }
+    __syncthreads();
+    if (op != 0) {
+      for (int gg = 0; gg < lat.G; ++gg) {
+        const int g = (op == 1) ? gg : lat.G - 1 - gg;
+        const int b0 = lat.fam_off[g], work = (lat.fam_off[g + 1] - b0) * cw;
+        for (int idx = TID; idx < work; idx += LQ_THREADS) {
+          int bb = idx / cw, a = idx - bb * cw;
+          int b = b0 + bb;
+          int i = lat.bond_i[b], j = lat.bond_j[b];
+          R c = bcv[b], s = bsv[b];
+          R xi = buf[i * cw + a], xj = buf[j * cw + a];
+          buf[i * cw + a] = c * xi + s * xj;
+          buf[j * cw + a] = s * xi + c * xj;
+        }
+        __syncthreads();
+      }
+    }
+    for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+      int i = idx / cw, a = idx - i * cw;
+      R v = buf[idx];
+      if (op == 2 && ceps) v *= ceps[i];
+      if (spost) v *= (R)dfac(C, sigma, spost[i]);
+      dst[(size_t)i * ld + c0 + a] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// W[a*ldw + b] = sum_i A[i*lda + a] * B[i*ldb + b], a < ma, b < mb (rows with
+// sub[i] == mval only, when sub is given).  Accumulates in Acc.
+template <class Acc, class RA, class RB>
+__device__ void gram(const RA* A, int lda, int ma, const RB* B, int ldb, int mb, int N, double* W, int ldw,
+                     const int* sub = nullptr, int mval = 0) {
+  const int nout = ma * mb;
+  if (nout > 0) {
+    int tpo = LQ_THREADS / nout;
+    if (tpo > 32) tpo = 32;
+    if (tpo < 1) tpo = 1;
+    while (tpo & (tpo - 1)) tpo &= tpo - 1;  // power of two
+    const int per = LQ_THREADS / tpo;
+    for (int o0 = 0; o0 < nout; o0 += per) {
+      const int o = o0 + TID / tpo, part = TID % tpo;
+      Acc acc = 0;
+      int a = 0, b = 0;
+      if (o < nout) {
+        a = o / mb;
+        b = o - a * mb;
+        for (int i = part; i < N; i += tpo)
+          if (!sub || sub[i] == mval) acc += (Acc)A[(size_t)i * lda + a] * (Acc)B[(size_t)i * ldb + b];
+      }
+      for (int off = tpo >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(FULL, acc, off, tpo);
+      if (part == 0 && o < nout) W[a * ldw + b] = (double)acc;
+    }
+  }
+  __syncthreads();
+}
+
+// Gauss-Jordan inverse with partial pivoting of W (m x m, destroyed) into T.
+// Returns log|det W| and its sign; a zero pivot sets LQ_ERR_SINGULAR.
+__device__ void inverse(double* W, int ldw, double* T, int ldt, int m, Smem& sm, double* logabs, int* sgn) {
+  double* fac = sm.vec + 9 * sm.M;
+  for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+    int r = idx / m, c = idx - r * m;
+    T[r * ldt + c] = (r == c) ? 1.0 : 0.0;
+  }
+  if (TID == 0) { sm.red[41] = 0.0; sm.ip[0] = 1; sm.ip[1] = 0; }
+  __syncthreads();
+  for (int col = 0; col < m; ++col) {
+    if (TID < 32) {
+      double best = -1.0;
+      int bi = col;
+      for (int r = col + TID; r < m; r += 32) {
+        double v = fabs(W[r * ldw + col]);
+        if (v > best) { best = v; bi = r; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        double ob = __shfl_xor_sync(FULL, best, off);
+        int oi = __shfl_xor_sync(FULL, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (TID == 0) { sm.ip[2] = bi; if (!(best > 0.0)) sm.ip[1] = 1; }
+    }
+    __syncthreads();
+    if (sm.ip[1]) break;
+    const int p = sm.ip[2];
+    if (p != col) {
+      for (int c = TID; c < m; c += LQ_THREADS) {
+        double t = W[col * ldw + c]; W[col * ldw + c] = W[p * ldw + c]; W[p * ldw + c] = t;
+        t = T[col * ldt + c]; T[col * ldt + c] = T[p * ldt + c]; T[p * ldt + c] = t;
+      }
+    }
+    __syncthreads();
+    const double d = W[col * ldw + col];
+    if (TID == 0) {
+      if (p != col) sm.ip[0] = -sm.ip[0];
+      if (d < 0) sm.ip[0] = -sm.ip[0];
+      sm.red[41] += log(fabs(d));
+    }
+    for (int r = TID; r < m; r += LQ_THREADS) fac[r] = (r == col) ? 0.0 : W[r * ldw + col] / d;
+    __syncthreads();
+    for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+      int r = idx / m, c = idx - r * m;
+      if (r != col) {
+        T[r * ldt + c] -= fac[r] * T[col * ldt + c];
+        if (c > col) W[r * ldw + c] -= fac[r] * W[col * ldw + c];
+      }
+    }
+    __syncthreads();
+    for (int c = TID; c < m; c += LQ_THREADS) {
+      T[col * ldt + c] /= d;
+      if (c > col) W[col * ldw + c] /= d;
+    }
+    __syncthreads();
+  }
+  if (sm.ip[1]) {
+    for (int idx = TID; idx < m * m; idx += LQ_THREADS) T[(idx / m) * ldt + idx % m] = NAN;
+    if (TID == 0) { sm.C->err |= LQ_ERR_SINGULAR; sm.red[41] = -INFINITY; sm.ip[0] = 0; }
+  }
+  __syncthreads();
+  *logabs = sm.red[41];
+  *sgn = sm.ip[0];
+  __syncthreads();
+}
+
+// In-place Cholesky of the upper triangle of W (m x m, ld): W = R^T R.
+__device__ void cholesky(double* W, int ld, int m, Smem& sm) {
+  for (int k = 0; k < m; ++k) {
+    if (TID == 0) {
+      double d = W[k * ld + k];
+      if (!(d > 0.0)) { sm.C->err |= LQ_ERR_CHOLESKY; d = 1e-300; }
+      W[k * ld + k] = sqrt(d);
+    }
+    __syncthreads();
+    for (int j = k + 1 + TID; j < m; j += LQ_THREADS) W[k * ld + j] /= W[k * ld + k];
+    __syncthreads();
+    const int rem = m - k - 1;
+    for (int idx = TID; idx < rem * rem; idx += LQ_THREADS) {
+      int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+      if (j >= i) W[i * ld + j] -= W[k * ld + i] * W[k * ld + j];
+    }
+    __syncthreads();
+  }
+}
+
+// X (N x m) <- Q with X = Q V, V upper triangular with a positive diagonal
+// (CholeskyQR2, FP64 Gram and factors).  V goes to Vout (m x m, row-major).
+template <class R>
+__device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& sm) {
+  if (m == 0) return;
+  const int N = C.N, MP = sm.MP;
+  double* Rk[2] = {sm.S, sm.S + sm.M * MP};
+  for (int pass = 0; pass < 2; ++pass) {
+    double* W = Rk[pass];
+    gram<double>(X, m, m, X, m, m, N, W, MP);
+    cholesky(W, MP, m, sm);
+    // X <- X R^{-1}, row by row (forward substitution on the row vector)
+    for (int i = TID; i < N; i += LQ_THREADS) {
+      R* row = X + (size_t)i * m;
+      double y[LQ_NS_MAX];
+#pragma unroll 1
+      for (int j = 0; j < m; ++j) {
+        double acc = (double)row[j];
+        for (int a = 0; a < j; ++a) acc -= y[a] * W[a * MP + j];
+        y[j] = acc / W[j * MP + j];
+      }
+      for (int j = 0; j < m; ++j) row[j] = (R)y[j];
+    }
+    __syncthreads();
+  }
+  for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+    int a = idx / m, b = idx - a * m;
+    double acc = 0.0;
+    if (b >= a)
+      for (int k = a; k <= b; ++k) acc += Rk[1][a * MP + k] * Rk[0][k * MP + b];
+    Vout[idx] = acc;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Field flips over all sites of slice l (ascending).  Rp: right panels (rows
+// scaled on accept), Lp: left panels (L~ transposed), T: (L~ R~)^{-1}.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ void flip_slice(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag, Smem& sm) {
+  const int N = C.N, MP = sm.MP;
+  const int ms[2] = {C.ns[0], C.ns[1]};
+  R* Rp[2] = {Rp0, Rp1};
+  const R* Lp[2] = {Lp0, Lp1};
+  const size_t per_site = (size_t)4 * MP * 8 + 8 + 4;
+  int cs = (int)(sm.buf_bytes / per_site);
+  if (cs > 256) cs = 256;
+  double* rrow = (double*)sm.buf;
+  double* lrow = rrow + (size_t)2 * cs * MP;
+  double* uni = lrow + (size_t)2 * cs * MP;
+  int* sf = (int*)(uni + cs);
+  const int warp = TID >> 5, lane = TID & 31;
+  for (int i0 = 0; i0 < N; i0 += cs) {
+    const int cn = min(cs, N - i0);
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = ms[sg];
+      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
+        int ii = idx / m, a = idx - ii * m;
+        rrow[((size_t)sg * cs + ii) * MP + a] = (double)Rp[sg][(size_t)(i0 + ii) * m + a];
+        lrow[((size_t)sg * cs + ii) * MP + a] = (double)Lp[sg][(size_t)(i0 + ii) * m + a];
+      }
+    }
+    for (int ii = TID; ii < cn; ii += LQ_THREADS) {
+      uint32_t w[4];
+      philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
+      uni[ii] = u53(w[0], w[1]);
+      sf[ii] = C.s[(size_t)l * N + i0 + ii];
+    }
+    __syncthreads();
+    if (warp < 2) {
+      const int sg = warp, m = ms[sg];
+      double* T = sm.T[sg];
+      long long nacc = 0;
+      for (int ii = 0; ii < cn; ++ii) {
+        double* rw = rrow + ((size_t)sg * cs + ii) * MP;
+        const double* lr = lrow + ((size_t)sg * cs + ii) * MP;
+        double x = 0.0, p = 0.0;
+        if (lane < m) {
+          for (int a = 0; a < m; ++a) x = fma(rw[a], T[a * MP + lane], x);
+          p = x * lr[lane];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
+        const int par = (i0 + ii) & 1;
+        if (lane == 0) sm.gx[par * 2 + sg] = p;
+        bar_pair();
+        const double g0 = sm.gx[par * 2], g1 = sm.gx[par * 2 + 1];
+        const int s = sf[ii];
+        const double d0 = delta_of(C, 0, s), d1 = delta_of(C, 1, s);
+        double r = (1.0 + d0 * g0) * (1.0 + d1 * g1);
+        if (C.charge) r *= (s > 0) ? C.cfac_p : C.cfac_m;
+        if (!(r == r) && sg == 0 && lane == 0) C.err |= LQ_ERR_NONFINITE;
+        if (uni[ii] < fabs(r)) {
+          const double d = sg ? d1 : d0, g = sg ? g1 : g0;
+          if (m > 0 && d != 0.0) {
+            double y = 0.0;
+            if (lane < m)
+              for (int b = 0; b < m; ++b) y = fma(T[lane * MP + b], lr[b], y);
+            const double cy = (d / (1.0 + d * g)) * y;
+            for (int b = 0; b < m; ++b) {
+              const double xb = __shfl_sync(FULL, x, b);
+              if (lane < m) T[lane * MP + b] = fma(-cy, xb, T[lane * MP + b]);
+            }
+            if (lane < m) rw[lane] *= 1.0 + d;
+          }
+          if (sg == 0 && lane == 0) {
+            C.s[(size_t)l * N + i0 + ii] = (int8_t)(-s);
+            C.logw += log(fabs(r));
+            if (r < 0) C.sign = -C.sign;
+            if (!isfinite(r)) C.err |= LQ_ERR_NONFINITE;
+            ++nacc;
+          }
+        }
+        __syncwarp();
+      }
+      if (sg == 0 && lane == 0) { C.cnt[0] += cn; C.cnt[1] += nacc; }
+    }
+    __syncthreads();
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = ms[sg];
+      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
+        int ii = idx / m, a = idx - ii * m;
+        Rp[sg][(size_t)(i0 + ii) * m + a] = (R)rrow[((size_t)sg * cs + ii) * MP + a];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// helpers on the chain layout
+// ---------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ R* qr_panel(const LqChainDev& C, int sg, int buf, int j) {
+  return (R*)C.QR[sg][buf] + (size_t)j * C.N * C.ns[sg];
+}
+template <class R> __device__ __forceinline__ R* ql_panel(const LqChainDev& C, int sg, int j) {
+  return (R*)C.QL[sg] + (size_t)j * C.N * C.ns[sg];
+}
+__device__ __forceinline__ double* vr_mat(const LqChainDev& C, int sg, int buf, int j) {
+  return C.VR[sg][buf] + (size_t)j * C.ns[sg] * C.ns[sg];
+}
+__device__ __forceinline__ int bnd(const LqChainDev& C, int j) { return min(j * C.tw, C.L); }
+
+template <class R> __device__ void fill_P(const LqChainDev& C, int sg, R* P) {
+  const int m = C.ns[sg];
+  for (int idx = TID; idx < C.N * m; idx += LQ_THREADS) P[idx] = (R)0;
+  __syncthreads();
+  for (int a = TID; a < m; a += LQ_THREADS) P[(size_t)C.occ[sg][a] * m + a] = (R)1;
+  __syncthreads();
+}
+
+// Right chain Q^R_0 = P, B_j Q^R_{j-1} = Q^R_j V^R_j (current buffer).
+template <class R> __device__ void build_right(LqChainDev& C, int sg, Smem& sm) {
+  const int m = C.ns[sg], cb = C.cur[sg];
+  fill_P<R>(C, sg, qr_panel<R>(C, sg, cb, 0));
+  for (int j = 1; j <= C.n; ++j) {
+    R* X = qr_panel<R>(C, sg, cb, j);
+    const int lo = bnd(C, j - 1), hi = bnd(C, j);
+    prop<R, R>(C, sg, X, qr_panel<R>(C, sg, cb, j - 1), m, m, lo, 1, -1, sm);
+    for (int l = lo + 1; l < hi; ++l) prop<R, R>(C, sg, X, X, m, m, l, 1, -1, sm);
+    chol_qr2<R>(C, X, m, vr_mat(C, sg, cb, j), sm);
+  }
+}
+
+// Left chain Q^L_n = P, B_j^T Q^L_j = Q^L_{j-1} V^L_{j-1}.
+template <class R> __device__ void build_left(LqChainDev& C, int sg, Smem& sm) {
+  const int m = C.ns[sg];
+  fill_P<R>(C, sg, ql_panel<R>(C, sg, C.n));
+  for (int j = C.n; j >= 1; --j) {
+    R* Z = ql_panel<R>(C, sg, j - 1);
+    const int lo = bnd(C, j - 1), hi = bnd(C, j);
+    prop<R, R>(C, sg, Z, ql_panel<R>(C, sg, j), m, m, -1, 2, hi - 1, sm);
+    for (int l = hi - 2; l >= lo; --l) prop<R, R>(C, sg, Z, Z, m, m, -1, 2, l, sm);
+    chol_qr2<R>(C, Z, m, C.VL[sg] + (size_t)(j - 1) * m * m, sm);
+  }
+}
+
+// log|W| and sign from the current right chain.
+template <class R> __device__ void log_weight(LqChainDev& C, Smem& sm, double* out_log, int* out_sign) {
+  double lw = 0.0;
+  int sgn = 1;
+  for (int sg = 0; sg < 2; ++sg) {
+    const int m = C.ns[sg], cb = C.cur[sg], MP = sm.MP;
+    double part = 0.0;
+    for (int idx = TID; idx < C.n * m; idx += LQ_THREADS) {
+      int j = 1 + idx / m, a = idx % m;
+      part += log(vr_mat(C, sg, cb, j)[a * m + a]);
+    }
+    lw += cta_sum(part, sm);
+    const R* Qn = qr_panel<R>(C, sg, cb, C.n);
+    for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+      int a = idx / m, b = idx - a * m;
+      sm.W[a * MP + b] = (double)Qn[(size_t)C.occ[sg][a] * m + b];
+    }
+    __syncthreads();
+    double la;
+    int s1;
+    inverse(sm.W, MP, sm.S, MP, m, sm, &la, &s1);
+    lw += la;
+    sgn *= s1;
+  }
+  if (C.charge) {
+    double part = 0.0;
+    for (int idx = TID; idx < C.L * C.N; idx += LQ_THREADS) part += (double)C.s[idx];
+    lw += -C.lambda * cta_sum(part, sm);
+  }
+  *out_log = lw;
+  *out_sign = sgn;
+}
+
+// ---------------------------------------------------------------------------
+// Up pass: stored left panels per block, live right panel, QR at block tops.
+// ---------------------------------------------------------------------------
+template <class R> __device__ void up_pass(LqChainDev& C, Smem& sm) {
+  const int N = C.N, MP = sm.MP;
+  for (int j = 1; j <= C.n; ++j) {
+    const int lo = bnd(C, j - 1), hi = bnd(C, j), nl = hi - lo;
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = C.ns[sg];
+      const size_t pn = (size_t)N * m;
+      R* St = (R*)C.stored[sg];
+      prop<R, R>(C, sg, St + (nl - 1) * pn, ql_panel<R>(C, sg, j), m, m, -1, 2, -1, sm);
+      for (int l = hi - 2; l >= lo; --l) prop<R, R>(C, sg, St + (l - lo) * pn, St + (l + 1 - lo) * pn, m, m, l + 1, 2, -1, sm);
+      prop<R, R>(C, sg, (R*)C.live[sg], qr_panel<R>(C, sg, C.cur[sg], j - 1), m, m, lo, 0, -1, sm);
+      gram<double>((const R*)St, m, m, (const R*)C.live[sg], m, m, N, sm.W, MP);
+      double la;
+      int s1;
+      inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
+    }
+    for (int l = lo; l < hi; ++l) {
+      const size_t o0 = (size_t)(l - lo) * N * C.ns[0], o1 = (size_t)(l - lo) * N * C.ns[1];
+      flip_slice<R>(C, l, (R*)C.live[0], (R*)C.live[1], (const R*)C.stored[0] + o0, (const R*)C.stored[1] + o1, 1u, sm);
+      for (int sg = 0; sg < 2; ++sg) {
+        const int m = C.ns[sg];
+        if (l + 1 < hi) {
+          prop<R, R>(C, sg, (R*)C.live[sg], (const R*)C.live[sg], m, m, -1, 1, l + 1, sm);
+        } else {
+          R* X = qr_panel<R>(C, sg, C.cur[sg], j);
+          prop<R, R>(C, sg, X, (const R*)C.live[sg], m, m, -1, 1, -1, sm);
+          chol_qr2<R>(C, X, m, vr_mat(C, sg, C.cur[sg], j), sm);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Measurement at block boundary jb from Q^L_jb and Q^R_jb.
+// ---------------------------------------------------------------------------
+template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
+  const int N = C.N, MP = sm.MP, M = sm.M;
+  const LqLatticeDev& lat = C.lat;
+  const R* QLb[2];
+  const R* QRb[2];
+  double* A[2];
+  int sgn = 1;
+  double* Ms = sm.S;  // Ms + k*M*MP, k = 0..5
+  for (int sg = 0; sg < 2; ++sg) {
+    const int m = C.ns[sg];
+    QLb[sg] = ql_panel<R>(C, sg, jb);
+    QRb[sg] = qr_panel<R>(C, sg, C.cur[sg], jb);
+    A[sg] = (double*)C.work[sg];
+    gram<double>(QLb[sg], m, m, QRb[sg], m, m, N, sm.W, MP);
+    double la;
+    int s1;
+    inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
+    sgn *= s1;
+    const double* Tm = sm.T[sg];
+    for (int idx = TID; idx < N * m; idx += LQ_THREADS) {
+      int i = idx / m, b = idx - i * m;
+      double acc = 0.0;
+      for (int a = 0; a < m; ++a) acc += (double)QRb[sg][(size_t)i * m + a] * Tm[a * MP + b];
+      A[sg][idx] = acc;
+    }
+    __syncthreads();
+  }
+  const int m0 = C.ns[0], m1 = C.ns[1];
+  // densities, double occupancy, onsite energy, sublattice densities
+  double nu = 0, nd = 0, docc = 0, eon = 0, na[2][2] = {{0, 0}, {0, 0}};
+  for (int i = TID; i < N; i += LQ_THREADS) {
+    double du = 0, dd = 0;
+    for (int b = 0; b < m0; ++b) du += A[0][(size_t)i * m0 + b] * (double)QLb[0][(size_t)i * m0 + b];
+    for (int b = 0; b < m1; ++b) dd += A[1][(size_t)i * m1 + b] * (double)QLb[1][(size_t)i * m1 + b];
+    nu += du; nd += dd; docc += du * dd;
+    if (lat.eps) eon += lat.eps[i] * (du + dd);
+    int a = lat.sub[i];
+    na[0][a] += du; na[1][a] += dd;
+  }
+  double ekin = 0.0;
+  for (int b = TID; b < lat.nb; b += LQ_THREADS) {
+    int i = lat.bond_i[b], j = lat.bond_j[b];
+    double t = 0.0;
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = C.ns[sg];
+      for (int q = 0; q < m; ++q)
+        t += (double)QLb[sg][(size_t)i * m + q] * A[sg][(size_t)j * m + q] +
+             (double)QLb[sg][(size_t)j * m + q] * A[sg][(size_t)i * m + q];
+    }
+    ekin += lat.bond_k[b] * t;
+  }
+  nu = cta_sum(nu, sm); nd = cta_sum(nd, sm); docc = cta_sum(docc, sm);
+  ekin = cta_sum(ekin + eon, sm);
+  double Na[2][2];
+  for (int sg = 0; sg < 2; ++sg)
+    for (int a = 0; a < 2; ++a) Na[sg][a] = cta_sum(na[sg][a], sm);
+  // tr(M^s_a M^s_b), M^s_a = sum_{i in a} A[i,:]^T Q^L[i,:]
+  double trMM[2][2][2];
+  for (int sg = 0; sg < 2; ++sg) {
+    const int m = C.ns[sg];
+    for (int a = 0; a < 2; ++a) gram<double>(A[sg], m, m, QLb[sg], m, m, N, Ms + a * M * MP, MP, lat.sub, a);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        double part = 0.0;
+        for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+          int p = idx / m, q = idx - p * m;
+          part += Ms[a * M * MP + p * MP + q] * Ms[b * M * MP + q * MP + p];
+        }
+        trMM[sg][a][b] = cta_sum(part, sm);
+      }
+  }
+  // tr(rho_up rho_dn) = sum_pq X[p][q] Y[q][p], X = A_dn^T Q^L_up, Y = A_up^T Q^L_dn
+  gram<double>(A[1], m1, m1, QLb[0], m0, m0, N, Ms + 2 * M * MP, MP);
+  gram<double>(A[0], m0, m0, QLb[1], m1, m1, N, Ms + 3 * M * MP, MP);
+  double part = 0.0;
+  for (int idx = TID; idx < m1 * m0; idx += LQ_THREADS) {
+    int p = idx / m0, q = idx - p * m0;
+    part += Ms[2 * M * MP + p * MP + q] * Ms[3 * M * MP + q * MP + p];
+  }
+  const double trud = cta_sum(part, sm);
+  if (TID == 0) {
+    double szz[2][2];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        double t = 0.0;
+        for (int sg = 0; sg < 2; ++sg) t += Na[sg][a] * Na[sg][b] + (a == b ? Na[sg][a] : 0.0) - trMM[sg][a][b];
+        t -= Na[0][a] * Na[1][b] + Na[1][a] * Na[0][b];
+        szz[a][b] = 0.25 * t;
+      }
+    const double ncell = N / 2.0, s = (double)sgn;
+    sm.obs[0] += s;
+    sm.obs[1] += s * nu;
+    sm.obs[2] += s * nd;
+    sm.obs[3] += s * docc / N;
+    sm.obs[4] += s * ekin / N;
+    sm.obs[5] += s * szz[0][0] / ncell;
+    sm.obs[6] += s * szz[1][1] / ncell;
+    sm.obs[7] += s * szz[0][1] / ncell;
+    sm.obs[8] += s * 0.5 * (nu + nd - 2.0 * trud) / ncell;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Down pass: stored right panels per block, live left panel, QR at block
+// bottoms, measurement at each boundary below a finished block.
+// ---------------------------------------------------------------------------
+template <class R> __device__ void down_pass(LqChainDev& C, int do_measure, Smem& sm) {
+  const int N = C.N, MP = sm.MP;
+  for (int sg = 0; sg < 2; ++sg) fill_P<R>(C, sg, ql_panel<R>(C, sg, C.n));
+  if (TID < LQ_NOBS) sm.obs[TID] = 0.0;
+  __syncthreads();
+  for (int j = C.n; j >= 1; --j) {
+    const int lo = bnd(C, j - 1), hi = bnd(C, j), nl = hi - lo;
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = C.ns[sg];
+      const size_t pn = (size_t)N * m;
+      R* St = (R*)C.stored[sg];
+      prop<R, R>(C, sg, St, qr_panel<R>(C, sg, C.cur[sg], j - 1), m, m, lo, 0, -1, sm);
+      for (int l = lo + 1; l < hi; ++l) prop<R, R>(C, sg, St + (l - lo) * pn, St + (l - 1 - lo) * pn, m, m, -1, 1, l, sm);
+      prop<R, R>(C, sg, (R*)C.live[sg], ql_panel<R>(C, sg, j), m, m, -1, 2, -1, sm);
+      gram<double>((const R*)C.live[sg], m, m, (const R*)(St + (nl - 1) * pn), m, m, N, sm.W, MP);
+      double la;
+      int s1;
+      inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
+    }
+    for (int l = hi - 1; l >= lo; --l) {
+      const size_t o0 = (size_t)(l - lo) * N * C.ns[0], o1 = (size_t)(l - lo) * N * C.ns[1];
+      flip_slice<R>(C, l, (R*)C.stored[0] + o0, (R*)C.stored[1] + o1, (const R*)C.live[0], (const R*)C.live[1], 2u, sm);
+      for (int sg = 0; sg < 2; ++sg) {
+        const int m = C.ns[sg];
+        if (l > lo) {
+          prop<R, R>(C, sg, (R*)C.live[sg], (const R*)C.live[sg], m, m, l, 2, -1, sm);
+        } else {
+          R* Z = ql_panel<R>(C, sg, j - 1);
+          prop<R, R>(C, sg, Z, (const R*)C.live[sg], m, m, l, 0, -1, sm);
+          chol_qr2<R>(C, Z, m, C.VL[sg] + (size_t)(j - 1) * m * m, sm);
+        }
+      }
+    }
+    if (do_measure) measure<R>(C, j - 1, sm);
+  }
+  if (do_measure && TID == 0 && C.nrec < C.max_records) {
+    for (int k = 0; k < LQ_NOBS; ++k) C.records[(size_t)C.nrec * LQ_NOBS + k] = sm.obs[k] / C.n;
+    C.nrec++;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Particle-hole swap for spin sg: remove column k (Givens, Eqs. S9-S12), add
+// site j (Gram-Schmidt twice, Eqs. S1-S8).  T0 = (P^T Q^R_n)^{-1} lives in
+// sm.T[sg].  commit: 1 Metropolis with uniform u, 0 only report (hook).
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int commit, Smem& sm) {
+  const int N = C.N, m = C.ns[sg], n = C.n, MP = sm.MP, M = sm.M;
+  const int cb = C.cur[sg], tb = cb ^ 1;
+  const size_t pn = (size_t)N * m;
+  const int nrot = m - 1 - k, mr = m - 1;
+  const int warp = TID >> 5, lane = TID & 31;
+  double* Am = sm.S;                 // working V
+  double* Mi = sm.S + M * MP;        // M^{-1}
+  double* Tp = sm.S + 2 * M * MP;    // downdated inverse
+  double* rc = sm.vec;               // rotations of the current block
+  double* rs = sm.vec + M;
+  double* v1 = sm.vec + 2 * M;
+  double* v2 = sm.vec + 3 * M;
+  double* av = sm.vec + 4 * M;
+  double* bv = sm.vec + 5 * M;
+  int* occr = sm.occ2;               // reduced column order (sites), then the new order
+  const int* occ = C.occ[sg];
+  double* rot = C.rot;
+  // --- removal: retriangulate V_i U (i = 1) and V_i G_{i-1}^T (i > 1) -----
+  if (warp == 0) {
+    double logrN = 0.0;
+    int sgnrN = 1;
+    for (int i = 1; i <= n; ++i) {
+      const double* Vi = vr_mat(C, sg, cb, i);
+      if (lane < m) {
+        const int src_col = (lane < k) ? lane : (lane < m - 1 ? lane + 1 : k);
+        for (int r = 0; r < m; ++r) Am[r * MP + lane] = Vi[r * m + (i == 1 ? src_col : lane)];
+      }
+      __syncwarp();
+      if (i > 1 && lane < m) {
+        for (int t = 0; t < nrot; ++t) {
+          const int q = k + t;
+          const double c = rc[t], s = rs[t];
+          const double x = Am[lane * MP + q], y = Am[lane * MP + q + 1];
+          Am[lane * MP + q] = c * x + s * y;
+          Am[lane * MP + q + 1] = -s * x + c * y;
+        }
+      }
+      __syncwarp();
+      for (int t = 0; t < nrot; ++t) {
+        const int q = k + t;
+        const double a = Am[q * MP + q], b = Am[(q + 1) * MP + q];
+        const double r = hypot(a, b);
+        const double c = (r != 0.0) ? a / r : 1.0, s = (r != 0.0) ? b / r : 0.0;
+        __syncwarp();
+        if (lane < m) {
+          const double x = Am[q * MP + lane], y = Am[(q + 1) * MP + lane];
+          Am[q * MP + lane] = c * x + s * y;
+          Am[(q + 1) * MP + lane] = -s * x + c * y;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          Am[q * MP + q] = r;
+          Am[(q + 1) * MP + q] = 0.0;
+          rc[t] = c;
+          rs[t] = s;
+          rot[((size_t)(i - 1) * LQ_NS_MAX + t) * 2] = c;
+          rot[((size_t)(i - 1) * LQ_NS_MAX + t) * 2 + 1] = s;
+        }
+        __syncwarp();
+      }
+      double* Vt = vr_mat(C, sg, tb, i);
+      if (lane < m)
+        for (int r = 0; r < m; ++r) Vt[r * m + lane] = Am[r * MP + lane];
+      const double dN = Am[(m - 1) * MP + (m - 1)];
+      logrN += log(fabs(dN));
+      if (dN < 0) sgnrN = -sgnrN;
+      __syncwarp();
+    }
+    // M^{-1} = G_n T0 U, then the downdate of Eq. S12
+    const double* T0 = sm.T[sg];
+    if (lane < m) {
+      const int src_col = (lane < k) ? lane : (lane < m - 1 ? lane + 1 : k);
+      for (int r = 0; r < m; ++r) Mi[r * MP + lane] = T0[r * MP + src_col];
+    }
+    __syncwarp();
+    for (int t = 0; t < nrot; ++t) {
+      const int q = k + t;
+      const double c = rc[t], s = rs[t];
+      if (lane < m) {
+        const double x = Mi[q * MP + lane], y = Mi[(q + 1) * MP + lane];
+        Mi[q * MP + lane] = c * x + s * y;
+        Mi[(q + 1) * MP + lane] = -s * x + c * y;
+      }
+      __syncwarp();
+    }
+    const double mNN = Mi[(m - 1) * MP + (m - 1)];
+    if (lane < mr)
+      for (int b = 0; b < mr; ++b) Tp[lane * MP + b] = Mi[lane * MP + b] - Mi[lane * MP + (m - 1)] * Mi[(m - 1) * MP + b] / mNN;
+    if (lane < mr) occr[lane] = occ[(lane < k) ? lane : lane + 1];
+    if (lane == 0) {
+      sm.ip[11] = occ[k];
+      sm.red[48] = log(fabs(mNN)) - logrN;
+      sm.ip[8] = ((mNN < 0) ? -1 : 1) * sgnrN;
+      sm.ip[9] = (mNN != 0.0) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  // Q_i' = Q_i G_i^T for all blocks, streamed row by row
+  {
+    const R* src0 = (const R*)C.QR[sg][cb];
+    R* dst0 = (R*)C.QR[sg][tb];
+    for (size_t idx = TID; idx < (size_t)n * N; idx += LQ_THREADS) {
+      const int i = 1 + (int)(idx / N), row = (int)(idx % N);
+      const R* src = src0 + (size_t)i * pn + (size_t)row * m;
+      R* dst = dst0 + (size_t)i * pn + (size_t)row * m;
+      for (int a = 0; a < k; ++a) dst[a] = src[a];
+      double x = (double)src[k];
+      const double* rr = rot + (size_t)(i - 1) * LQ_NS_MAX * 2;
+      for (int t = 0; t < nrot; ++t) {
+        const double c = rr[2 * t], s = rr[2 * t + 1];
+        const double y = (double)src[k + t + 1];
+        dst[k + t] = (R)(c * x + s * y);
+        x = -s * x + c * y;
+      }
+      dst[m - 1] = (R)x;
+    }
+  }
+  __syncthreads();
+  // --- addition of site j on the reduced chain ------------------------------
+  double* q = C.vec;
+  double* w = C.vec + N;
+  for (int i = TID; i < N; i += LQ_THREADS) q[i] = (i == j) ? 1.0 : 0.0;
+  __syncthreads();
+  double logrho = 0.0;
+  int valid = sm.ip[9];
+  for (int i = 1; i <= n && valid; ++i) {
+    const int lo = bnd(C, i - 1), hi = bnd(C, i);
+    prop<double, double>(C, sg, w, q, 1, 1, lo, 1, -1, sm);
+    for (int l = lo + 1; l < hi; ++l) prop<double, double>(C, sg, w, w, 1, 1, l, 1, -1, sm);
+    R* Qi = qr_panel<R>(C, sg, tb, i);
+    for (int pass = 0; pass < 2; ++pass) {
+      double* vv = pass ? v2 : v1;
+      gram<double>(Qi, m, mr, w, 1, 1, N, vv, 1);
+      for (int r = TID; r < N; r += LQ_THREADS) {
+        double acc = 0.0;
+        for (int a = 0; a < mr; ++a) acc += (double)Qi[(size_t)r * m + a] * vv[a];
+        w[r] -= acc;
+      }
+      __syncthreads();
+    }
+    double part = 0.0;
+    for (int r = TID; r < N; r += LQ_THREADS) part += w[r] * w[r];
+    const double rho = sqrt(cta_sum(part, sm));
+    if (!(rho > 0.0)) { valid = 0; break; }
+    for (int r = TID; r < N; r += LQ_THREADS) {
+      const double qq = w[r] / rho;
+      q[r] = qq;
+      Qi[(size_t)r * m + (m - 1)] = (R)qq;
+    }
+    double* Vt = vr_mat(C, sg, tb, i);
+    for (int a = TID; a < mr; a += LQ_THREADS) {
+      Vt[a * m + (m - 1)] = v1[a] + v2[a];
+      Vt[(m - 1) * m + a] = 0.0;
+    }
+    if (TID == 0) Vt[(m - 1) * m + (m - 1)] = rho;
+    logrho += log(rho);
+    __syncthreads();
+  }
+  // --- Schur complement s (Eq. S7), ratio, Metropolis, commit ---------------
+  if (warp == 0) {
+    const R* Qn = qr_panel<R>(C, sg, tb, n);
+    double s_add = 0.0;
+    if (valid) {
+      if (lane < mr) {
+        double acc = 0.0;
+        for (int b = 0; b < mr; ++b) acc += Tp[lane * MP + b] * q[occr[b]];
+        av[lane] = acc;
+        double acc2 = 0.0;
+        for (int a = 0; a < mr; ++a) acc2 += (double)Qn[(size_t)j * m + a] * Tp[a * MP + lane];
+        bv[lane] = acc2;
+      }
+      __syncwarp();
+      s_add = q[j];
+      for (int a = 0; a < mr; ++a) s_add -= (double)Qn[(size_t)j * m + a] * av[a];
+      if (s_add == 0.0) valid = 0;
+    }
+    const double log_rem = sm.red[48];
+    const int sgn_rem = sm.ip[8];
+    const double log_add = log(fabs(s_add)) + logrho;
+    const int sgn_add = (s_add < 0) ? -1 : 1;
+    const double logabs = valid ? log_rem + log_add : -INFINITY;
+    const int sgn = sgn_rem * sgn_add;
+    const int accept = commit && valid && (logabs >= 0.0 || u < exp(logabs));
+    if (lane == 0) {
+      C.hook[0] = logabs; C.hook[1] = sgn; C.hook[2] = log_rem; C.hook[3] = sgn_rem;
+      C.hook[4] = log_add; C.hook[5] = sgn_add;
+      sm.ip[10] = accept;
+      if (commit) C.cnt[2]++;
+    }
+    __syncwarp();
+    if (accept) {
+      double* T0 = sm.T[sg];
+      if (lane < mr) {
+        for (int b = 0; b < mr; ++b) T0[lane * MP + b] = Tp[lane * MP + b] + av[lane] * bv[b] / s_add;
+        T0[lane * MP + (m - 1)] = -av[lane] / s_add;
+        T0[(m - 1) * MP + lane] = -bv[lane] / s_add;
+      }
+      if (lane == 0) {
+        T0[(m - 1) * MP + (m - 1)] = 1.0 / s_add;
+        occr[m - 1] = j;
+        C.logw += logabs;
+        C.sign *= sgn;
+        if (!isfinite(logabs)) C.err |= LQ_ERR_NONFINITE;
+        C.cnt[3]++;
+      }
+    }
+  }
+  __syncthreads();
+  if (sm.ip[10]) {
+    const int removed = sm.ip[11];
+    for (int a = TID; a < m; a += LQ_THREADS) C.occ[sg][a] = occr[a];
+    R* P = qr_panel<R>(C, sg, tb, 0);
+    for (size_t idx = TID; idx < pn; idx += LQ_THREADS) P[idx] = (R)0;
+    __syncthreads();
+    for (int a = TID; a < m; a += LQ_THREADS) P[(size_t)occr[a] * m + a] = (R)1;
+    if (TID == 0) {
+      sm.bits[removed >> 5] &= ~(1u << (removed & 31));
+      sm.bits[j >> 5] |= 1u << (j & 31);
+      C.cur[sg] = tb;
+    }
+  }
+  __syncthreads();
+}
+
+// Occupancy bitmap of spin sg, and T0 = (P^T Q^R_n)^{-1} into sm.T[sg].
+template <class R> __device__ void swap_setup(LqChainDev& C, int sg, Smem& sm) {
+  const int N = C.N, m = C.ns[sg], MP = sm.MP;
+  for (int w = TID; w < N / 32 + 1; w += LQ_THREADS) sm.bits[w] = 0u;
+  __syncthreads();
+  if (TID == 0)
+    for (int a = 0; a < m; ++a) sm.bits[C.occ[sg][a] >> 5] |= 1u << (C.occ[sg][a] & 31);
+  const R* Qn = qr_panel<R>(C, sg, C.cur[sg], C.n);
+  for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+    int a = idx / m, b = idx - a * m;
+    sm.W[a * MP + b] = (double)Qn[(size_t)C.occ[sg][a] * m + b];
+  }
+  __syncthreads();
+  double la;
+  int s1;
+  inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
+}
+
+// site index of the jidx-th empty site (ascending)
+__device__ int jth_empty(const Smem& sm, int N, int jidx) {
+  int t = 0;
+  for (int w = 0; w * 32 < N; ++w) {
+    unsigned occw = sm.bits[w];
+    int nbits = min(32, N - w * 32);
+    unsigned valid = (nbits == 32) ? 0xffffffffu : ((1u << nbits) - 1u);
+    unsigned emp = ~occw & valid;
+    int c = __popc(emp);
+    if (t + c > jidx) {
+      int need = jidx - t;
+      for (int b = 0; b < 32; ++b)
+        if (emp & (1u << b)) {
+          if (need == 0) return w * 32 + b;
+          --need;
+        }
+    }
+    t += c;
+  }
+  return -1;
+}
+
+template <class R> __device__ void swap_phase(LqChainDev& C, Smem& sm) {
+  for (int sg = 0; sg < 2; ++sg) {
+    const int m = C.ns[sg];
+    if (m == 0 || m == C.N) continue;
+    swap_setup<R>(C, sg, sm);
+    for (int att = 0; att < m; ++att) {
+      if (TID == 0) {
+        uint32_t w[4], w2[4];
+        const uint32_t c2 = (3u << 24) | ((uint32_t)sg << 16) | (uint32_t)att;
+        philox(C.chain_id, C.sweep, c2, 0u, C.key0, C.key1, w);
+        philox(C.chain_id, C.sweep, c2, 1u, C.key0, C.key1, w2);
+        const int k = (int)(u53(w[0], w[1]) * (double)m);
+        const int jidx = (int)(u53(w[2], w[3]) * (double)(C.N - m));
+        sm.ip[4] = k;
+        sm.ip[5] = jth_empty(sm, C.N, jidx);
+        sm.red[50] = u53(w2[0], w2[1]);
+      }
+      __syncthreads();
+      if (sm.ip[5] < 0) {  // cannot happen for jidx < N - m; never index with it
+        if (TID == 0) sm.C->err |= LQ_ERR_NONFINITE;
+        __syncthreads();
+        continue;
+      }
+      swap_attempt<R>(C, sg, sm.ip[4], sm.ip[5], sm.red[50], 1, sm);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__device__ inline void load_chain(LqChainDev* g, Smem& sm) {
+  const int words = (int)(sizeof(LqChainDev) / 4);
+  for (int w = TID; w < words; w += LQ_THREADS) ((int*)sm.C)[w] = ((const int*)g)[w];
+  __syncthreads();
+}
+__device__ inline void store_chain(LqChainDev* g, Smem& sm) {
+  __syncthreads();
+  const int words = (int)(sizeof(LqChainDev) / 4);
+  for (int w = TID; w < words; w += LQ_THREADS) ((int*)g)[w] = ((const int*)sm.C)[w];
+  __syncthreads();
+}
+
+template <class R>
+__global__ void __launch_bounds__(LQ_THREADS, 2)
+    sweep_kernel(LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps, int do_measure, SmemPlan plan) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Smem sm = carve(plan, smem_raw);
+  __shared__ int next;
+  for (;;) {
+    if (TID == 0) next = atomicAdd(queue, 1);
+    __syncthreads();
+    const int q = next;
+    __syncthreads();
+    if (q >= n_order) break;
+    LqChainDev* g = chains + order[q];
+    load_chain(g, sm);
+    LqChainDev& C = *sm.C;
+    for (int t = 0; t < n_sweeps; ++t) {
+      up_pass<R>(C, sm);
+      swap_phase<R>(C, sm);
+      down_pass<R>(C, do_measure, sm);
+      if (TID == 0) C.sweep++;
+      __syncthreads();
+    }
+    store_chain(g, sm);
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(LQ_THREADS, 2)
+    build_kernel(LqChainDev* chains, const int* order, int n_order, SmemPlan plan) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Smem sm = carve(plan, smem_raw);
+  for (int q = blockIdx.x; q < n_order; q += gridDim.x) {
+    LqChainDev* g = chains + order[q];
+    load_chain(g, sm);
+    LqChainDev& C = *sm.C;
+    // input check: fields +-1, occupied sites distinct and in range
+    if (TID == 0) sm.ip[12] = 0;
+    __syncthreads();
+    for (int idx = TID; idx < C.L * C.N; idx += LQ_THREADS)
+      if (C.s[idx] != 1 && C.s[idx] != -1) sm.ip[12] = 1;
+    for (int sg = 0; sg < 2; ++sg) {
+      for (int w = TID; w < C.N / 32 + 1; w += LQ_THREADS) sm.bits[w] = 0u;
+      __syncthreads();
+      if (TID == 0)
+        for (int a = 0; a < C.ns[sg]; ++a) {
+          const int i = C.occ[sg][a];
+          if (i < 0 || i >= C.N || (sm.bits[i >> 5] >> (i & 31)) & 1u) { sm.ip[12] = 1; break; }
+          sm.bits[i >> 5] |= 1u << (i & 31);
+        }
+      __syncthreads();
+    }
+    if (sm.ip[12]) {
+      if (TID == 0) C.err |= LQ_ERR_BADINPUT;
+      store_chain(g, sm);
+      continue;
+    }
+    for (int sg = 0; sg < 2; ++sg) { build_right<R>(C, sg, sm); build_left<R>(C, sg, sm); }
+    double lw;
+    int s1;
+    log_weight<R>(C, sm, &lw, &s1);
+    if (TID == 0) { C.logw = lw; C.sign = s1; C.hook[6] = lw; C.hook[7] = s1; }
+    store_chain(g, sm);
+  }
+}
+
+__global__ void clear_records_kernel(LqChainDev* chains, int n) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) chains[c].nrec = 0;
+}
+
+// Fields uniform +-1 and occupations by Fisher-Yates from Philox (tags 4, 5).
+__global__ void init_kernel(LqChainDev* chains, const int* order, int n_order) {
+  for (int q = blockIdx.x; q < n_order; q += gridDim.x) {
+    LqChainDev* C = chains + order[q];
+    const int N = C->N, L = C->L;
+    for (int idx = TID; idx < L * N; idx += blockDim.x) {
+      const int l = idx / N, i = idx - l * N;
+      uint32_t w[4];
+      philox(C->chain_id, 0xFFFFFFFFu, (4u << 24) | (uint32_t)l, (uint32_t)i, C->key0, C->key1, w);
+      C->s[idx] = (w[0] & 1u) ? 1 : -1;
+    }
+    if (TID < 2) {
+      const int sg = TID, m = C->ns[sg];
+      int* occ = C->occ[sg];
+      // partial Fisher-Yates on an implicit identity permutation, kept in occ
+      // (positions >= m that were swapped are remembered through a small map)
+      // N may be large, so the permutation lives in C->vec reinterpreted as ints
+      int* perm = (int*)(C->vec) + sg * N;
+      for (int i = 0; i < N; ++i) perm[i] = i;
+      for (int t = 0; t < m; ++t) {
+        uint32_t w[4];
+        philox(C->chain_id, 0xFFFFFFFFu, (5u << 24) | (uint32_t)sg, (uint32_t)t, C->key0, C->key1, w);
+        const int r = t + (int)(u53(w[0], w[1]) * (double)(N - t));
+        const int tmp = perm[t]; perm[t] = perm[r]; perm[r] = tmp;
+      }
+      for (int a = 0; a < m; ++a) occ[a] = perm[a];
+      for (int a = 1; a < m; ++a) {
+        int v = occ[a], b = a - 1;
+        while (b >= 0 && occ[b] > v) { occ[b + 1] = occ[b]; --b; }
+        occ[b + 1] = v;
+      }
+    }
+  }
+}
+
+// Ratio of flipping s at (l, i) on freshly built chains (test hook).
+template <class R>
+__global__ void __launch_bounds__(LQ_THREADS, 2) field_ratio_kernel(LqChainDev* chains, int c, int l, int i, SmemPlan plan) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Smem sm = carve(plan, smem_raw);
+  LqChainDev* g = chains + c;
+  load_chain(g, sm);
+  LqChainDev& C = *sm.C;
+  const int N = C.N, MP = sm.MP;
+  int j = 1;
+  while (bnd(C, j) <= l) ++j;
+  const int lo = bnd(C, j - 1), hi = bnd(C, j);
+  double r = 1.0;
+  const int s = C.s[(size_t)l * N + i];
+  for (int sg = 0; sg < 2; ++sg) {
+    const int m = C.ns[sg];
+    R* X = (R*)C.live[sg];
+    R* Z = (R*)C.stored[sg];
+    prop<R, R>(C, sg, X, qr_panel<R>(C, sg, C.cur[sg], j - 1), m, m, lo, 0, -1, sm);
+    for (int ll = lo; ll < l; ++ll) prop<R, R>(C, sg, X, X, m, m, -1, 1, ll + 1, sm);
+    prop<R, R>(C, sg, Z, ql_panel<R>(C, sg, j), m, m, -1, 2, -1, sm);
+    for (int ll = hi - 1; ll > l; --ll) prop<R, R>(C, sg, Z, Z, m, m, ll, 2, -1, sm);
+    gram<double>((const R*)Z, m, m, (const R*)X, m, m, N, sm.W, MP);
+    double la;
+    int s1;
+    inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
+    double part = 0.0;
+    if (TID < m) {
+      double x = 0.0;
+      for (int a = 0; a < m; ++a) x += (double)X[(size_t)i * m + a] * sm.T[sg][a * MP + TID];
+      part = x * (double)Z[(size_t)i * m + TID];
+    }
+    const double gg = cta_sum(part, sm);
+    r *= 1.0 + delta_of(C, sg, s) * gg;
+  }
+  if (C.charge) r *= (s > 0) ? C.cfac_p : C.cfac_m;
+  if (TID == 0) C.hook[0] = r;
+  store_chain(g, sm);
+}
+
+// Swap ratio (remove column k, add site j) on the current right chain (test hook).
+template <class R>
+__global__ void __launch_bounds__(LQ_THREADS, 2) swap_ratio_kernel(LqChainDev* chains, int c, int sg, int k, int j, SmemPlan plan) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Smem sm = carve(plan, smem_raw);
+  LqChainDev* g = chains + c;
+  load_chain(g, sm);
+  LqChainDev& C = *sm.C;
+  swap_setup<R>(C, sg, sm);
+  swap_attempt<R>(C, sg, k, j, 0.0, 0, sm);
+  store_chain(g, sm);
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+template <class R> static cudaError_t set_attr(const void* fn, size_t smem) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
+                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st) {
+  SmemPlan p = plan_smem(M, Nmax, buf_bytes);
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (prec == 0) {
+    if ((e = set_attr<double>((const void*)sweep_kernel<double>, p.total)) != cudaSuccess) return e;
+    sweep_kernel<double><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, do_measure, p);
+  } else {
+    if ((e = set_attr<float>((const void*)sweep_kernel<float>, p.total)) != cudaSuccess) return e;
+    sweep_kernel<float><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, do_measure, p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build(int prec, LqChainDev* chains, const int* order, int n_order, int M, int Nmax, int buf_bytes,
+                         int grid, cudaStream_t st) {
+  SmemPlan p = plan_smem(M, Nmax, buf_bytes);
+  cudaError_t e;
+  if (prec == 0) {
+    if ((e = set_attr<double>((const void*)build_kernel<double>, p.total)) != cudaSuccess) return e;
+    build_kernel<double><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, p);
+  } else {
+    if ((e = set_attr<float>((const void*)build_kernel<float>, p.total)) != cudaSuccess) return e;
+    build_kernel<float><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clear_records(LqChainDev* chains, int n, cudaStream_t st) {
+  clear_records_kernel<<<(n + 255) / 256, 256, 0, st>>>(chains, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(LqChainDev* chains, const int* order, int n_order, int grid, cudaStream_t st) {
+  init_kernel<<<grid, LQ_THREADS, 0, st>>>(chains, order, n_order);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_ratio(int prec, LqChainDev* chains, int c, int l, int i, int M, int Nmax, int buf_bytes,
+                               cudaStream_t st) {
+  SmemPlan p = plan_smem(M, Nmax, buf_bytes);
+  cudaError_t e;
+  if (prec == 0) {
+    if ((e = set_attr<double>((const void*)field_ratio_kernel<double>, p.total)) != cudaSuccess) return e;
+    field_ratio_kernel<double><<<1, LQ_THREADS, p.total, st>>>(chains, c, l, i, p);
+  } else {
+    if ((e = set_attr<float>((const void*)field_ratio_kernel<float>, p.total)) != cudaSuccess) return e;
+    field_ratio_kernel<float><<<1, LQ_THREADS, p.total, st>>>(chains, c, l, i, p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_swap_ratio(int prec, LqChainDev* chains, int c, int sg, int k, int j, int M, int Nmax,
+                              int buf_bytes, cudaStream_t st) {
+  SmemPlan p = plan_smem(M, Nmax, buf_bytes);
+  cudaError_t e;
+  if (prec == 0) {
+    if ((e = set_attr<double>((const void*)swap_ratio_kernel<double>, p.total)) != cudaSuccess) return e;
+    swap_ratio_kernel<double><<<1, LQ_THREADS, p.total, st>>>(chains, c, sg, k, j, p);
+  } else {
+    if ((e = set_attr<float>((const void*)swap_ratio_kernel<float>, p.total)) != cudaSuccess) return e;
+    swap_ratio_kernel<float><<<1, LQ_THREADS, p.total, st>>>(chains, c, sg, k, j, p);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lq
+
+namespace lq {
+int max_active_sweep_ctas(int prec, size_t smem) {
+  int n = 0;
+  const void* fn = prec == 0 ? (const void*)sweep_kernel<double> : (const void*)sweep_kernel<float>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, LQ_THREADS, smem) != cudaSuccess) return 0;
+  return n;
+}
+}  // namespace lq

@@ -1,0 +1,21 @@
+// Launch wrappers of the sm_103a kernels (host-callable, plain types).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "lq_device.h"
+
+namespace lq {
+size_t smem_bytes(int M, int Nmax, int buf_bytes);
+cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
+                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st);
+cudaError_t launch_build(int prec, LqChainDev* chains, const int* order, int n_order, int M, int Nmax, int buf_bytes,
+                         int grid, cudaStream_t st);
+cudaError_t launch_clear_records(LqChainDev* chains, int n, cudaStream_t st);
+cudaError_t launch_init(LqChainDev* chains, const int* order, int n_order, int grid, cudaStream_t st);
+cudaError_t launch_field_ratio(int prec, LqChainDev* chains, int c, int l, int i, int M, int Nmax, int buf_bytes,
+                               cudaStream_t st);
+cudaError_t launch_swap_ratio(int prec, LqChainDev* chains, int c, int sg, int k, int j, int M, int Nmax,
+                              int buf_bytes, cudaStream_t st);
+int max_active_sweep_ctas(int prec, size_t smem);
+}  // namespace lq

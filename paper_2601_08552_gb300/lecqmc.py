@@ -1,0 +1,353 @@
+"""Thin ctypes binding of the C ABI in include/lecqmc.h.
+
+Argument marshalling only: every step of the sweep runs in the sm_103a
+kernels of liblecqmc.so.  PyTorch supplies the CUDA stream and, through its
+caching allocator, the device memory.  There is no CPU fallback: without the
+built library (or without a GPU) the calls raise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LQ_FP64 = 0
+LQ_MIXED = 1
+LQ_NOBS = 9
+OBS_NAMES = ["sign", "n_up", "n_dn", "docc", "ekin", "szz_00", "szz_11", "szz_01", "s_par"]
+LQ_MAX_PARTICLES = 32
+
+_STATUS = {0: "LQ_OK", 1: "LQ_EINVAL", 2: "LQ_ENOMEM", 3: "LQ_ECUDA", 4: "LQ_ENUMERIC", 5: "LQ_ETIMEOUT",
+           6: "LQ_EBUSY", 7: "LQ_ENOTFOUND", 8: "LQ_EUNSUPPORTED"}
+
+EXPORTS = [
+    "lq_lattice_from_bonds", "lq_lattice_chain", "lq_lattice_square", "lq_lattice_flatband",
+    "lq_lattice_cross_stitch", "lq_lattice_info", "lq_lattice_bonds", "lq_lattice_destroy",
+    "lq_sim_create", "lq_sim_init", "lq_sim_set_fields", "lq_sim_get_fields", "lq_sim_set_fock",
+    "lq_sim_get_fock", "lq_sim_set_sweep_index", "lq_sim_sweep", "lq_sim_run_host", "lq_sim_sync", "lq_sim_log_weight",
+    "lq_sim_tracked_weight", "lq_sim_field_ratio", "lq_sim_swap_ratio", "lq_sim_records",
+    "lq_sim_clear_records", "lq_sim_stats", "lq_sim_chain_panel", "lq_sim_chain_info",
+    "lq_sim_device_bytes", "lq_sim_destroy", "lq_last_error", "lq_version",
+]
+
+
+class LqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("U", C.c_double), ("beta", C.c_double), ("dtau", C.c_double), ("n_up", C.c_int32),
+                ("n_dn", C.c_int32), ("n_stab", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64)]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN)]
+
+
+_lib = None
+
+
+def load(build_if_missing=True):
+    """Load liblecqmc.so (building it with nvcc if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and (not os.path.exists(path) or _build._stale()):
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError("liblecqmc.so is not built (run paper_2601_08552_gb300/build.py)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    i32, dbl, u32 = C.c_int32, C.c_double, C.c_uint32
+    pi32, pdbl = C.POINTER(C.c_int32), C.POINTER(C.c_double)
+    lib.lq_last_error.restype = C.c_char_p
+    lib.lq_version.restype = C.c_char_p
+    sig = {
+        "lq_lattice_from_bonds": [i32, i32, pi32, pi32, pdbl, pdbl, pi32, C.POINTER(P)],
+        "lq_lattice_chain": [i32, dbl, i32, C.POINTER(P)],
+        "lq_lattice_square": [i32, i32, dbl, i32, C.POINTER(P)],
+        "lq_lattice_flatband": [i32, dbl, dbl, dbl, dbl, i32, C.POINTER(P)],
+        "lq_lattice_cross_stitch": [i32, dbl, dbl, dbl, i32, C.POINTER(P)],
+        "lq_lattice_info": [P, pi32, pi32, pi32],
+        "lq_lattice_bonds": [P, pi32, pi32, pdbl, pi32],
+        "lq_lattice_destroy": [P],
+        "lq_sim_create": [C.POINTER(P), C.POINTER(Params), i32, C.POINTER(u32), P, C.POINTER(Allocator),
+                          C.POINTER(P)],
+        "lq_sim_init": [P],
+        "lq_sim_set_fields": [P, i32, C.POINTER(C.c_int8)],
+        "lq_sim_get_fields": [P, i32, C.POINTER(C.c_int8)],
+        "lq_sim_set_fock": [P, i32, pi32, pi32],
+        "lq_sim_get_fock": [P, i32, pi32, pi32],
+        "lq_sim_set_sweep_index": [P, u32],
+        "lq_sim_sweep": [P, i32, i32],
+        "lq_sim_run_host": [P, C.POINTER(C.c_int8), pi32, i32, i32, C.POINTER(C.c_int8), pi32, pdbl],
+        "lq_sim_sync": [P],
+        "lq_sim_log_weight": [P, i32, pdbl, pi32],
+        "lq_sim_tracked_weight": [P, i32, pdbl, pi32],
+        "lq_sim_field_ratio": [P, i32, i32, i32, pdbl],
+        "lq_sim_swap_ratio": [P, i32, i32, i32, i32, pdbl, pdbl],
+        "lq_sim_records": [P, i32, i32, pi32, pdbl],
+        "lq_sim_clear_records": [P],
+        "lq_sim_stats": [P, i32, C.POINTER(C.c_int64)],
+        "lq_sim_chain_panel": [P, i32, i32, i32, i32, pdbl, pdbl],
+        "lq_sim_chain_info": [P, i32, pi32],
+        "lq_sim_device_bytes": [P, C.POINTER(C.c_size_t)],
+        "lq_sim_destroy": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise LqError(status, _lib.lq_last_error().decode())
+
+
+def _addr(a):
+    return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class Lattice:
+    """A hopping matrix in checkerboard form (see include/lecqmc.h)."""
+
+    def __init__(self, handle):
+        self.h = C.c_void_p(handle)
+        n, nb, g = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(_lib.lq_lattice_info(self.h, C.byref(n), C.byref(nb), C.byref(g)))
+        self.N, self.n_bonds, self.n_families = n.value, nb.value, g.value
+
+    @classmethod
+    def _make(cls, fn, *args):
+        load()
+        out = C.c_void_p()
+        _check(fn(*args, C.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def from_bonds(cls, n_sites, bi, bj, kij, onsite=None, sublattice=None):
+        load()
+        bi = np.ascontiguousarray(bi, dtype=np.int32)
+        bj = np.ascontiguousarray(bj, dtype=np.int32)
+        kij = np.ascontiguousarray(kij, dtype=np.float64)
+        on = None if onsite is None else np.ascontiguousarray(onsite, dtype=np.float64)
+        sb = None if sublattice is None else np.ascontiguousarray(sublattice, dtype=np.int32)
+        return cls._make(_lib.lq_lattice_from_bonds, int(n_sites), len(bi), _p(bi, C.c_int32), _p(bj, C.c_int32),
+                         _p(kij, C.c_double), None if on is None else _p(on, C.c_double),
+                         None if sb is None else _p(sb, C.c_int32))
+
+    @classmethod
+    def chain(cls, n, t=1.0, periodic=True):
+        return cls._make(load().lq_lattice_chain, int(n), float(t), int(bool(periodic)))
+
+    @classmethod
+    def square(cls, lx, ly, t=1.0, periodic=True):
+        return cls._make(load().lq_lattice_square, int(lx), int(ly), float(t), int(bool(periodic)))
+
+    @classmethod
+    def flatband(cls, n_cells, t1=-0.2, t2=1.0, t3=1.0, t4=-0.2, periodic=True):
+        return cls._make(load().lq_lattice_flatband, int(n_cells), float(t1), float(t2), float(t3), float(t4),
+                         int(bool(periodic)))
+
+    @classmethod
+    def cross_stitch(cls, n_cells, t_intra=1.0, t_leg=1.0, t_cross=1.0, periodic=True):
+        return cls._make(load().lq_lattice_cross_stitch, int(n_cells), float(t_intra), float(t_leg),
+                         float(t_cross), int(bool(periodic)))
+
+    def bonds(self):
+        bi = np.zeros(max(self.n_bonds, 1), np.int32)
+        bj = np.zeros_like(bi)
+        k = np.zeros(max(self.n_bonds, 1))
+        f = np.zeros_like(bi)
+        _check(_lib.lq_lattice_bonds(self.h, _p(bi, C.c_int32), _p(bj, C.c_int32), _p(k, C.c_double),
+                                     _p(f, C.c_int32)))
+        nb = self.n_bonds
+        return bi[:nb], bj[:nb], k[:nb], f[:nb]
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.lq_lattice_destroy(self.h)
+            self.h = None
+
+
+def _torch_allocator():
+    """lq_allocator backed by PyTorch's CUDA caching allocator."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def _alloc(ctx, nbytes, stream):
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream))
+
+    def _free(ctx, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = Allocator()
+    a.ctx = None
+    a.alloc = _ALLOC_FN(_alloc)
+    a.free = _FREE_FN(_free)
+    return a
+
+
+class Sim:
+    """A batch of independent Markov chains on one GPU."""
+
+    def __init__(self, lattices, params, chain_ids=None, stream=None, use_torch_allocator=True):
+        load()
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("lecqmc needs a CUDA GPU; there is no CPU fallback")
+        n = len(lattices)
+        if len(params) != n:
+            raise ValueError("one params entry per lattice")
+        self._lattices = list(lattices)
+        lh = (C.c_void_p * n)(*[l.h.value for l in lattices])
+        pp = (Params * n)()
+        for c, p in enumerate(params):
+            pp[c] = Params(float(p["U"]), float(p["beta"]), float(p["dtau"]), int(p["n_up"]), int(p["n_dn"]),
+                           int(p["n_stab"]), int(p.get("precision", LQ_FP64)), int(p.get("seed", 0)) & (2**64 - 1))
+        ids = None
+        if chain_ids is not None:
+            ids = (C.c_uint32 * n)(*[int(x) for x in chain_ids])
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self._alloc = _torch_allocator() if use_torch_allocator else None
+        out = C.c_void_p()
+        _check(_lib.lq_sim_create(C.cast(lh, C.POINTER(C.c_void_p)), pp, n, ids, C.c_void_p(stream),
+                                  C.byref(self._alloc) if self._alloc is not None else None, C.byref(out)))
+        self.h = out
+        self.n_chains = n
+        self.info = []
+        for c in range(n):
+            a = np.zeros(6, np.int32)
+            _check(_lib.lq_sim_chain_info(self.h, c, _p(a, C.c_int32)))
+            self.info.append(dict(N=int(a[0]), L=int(a[1]), tw=int(a[2]), n=int(a[3]), n_up=int(a[4]),
+                                  n_dn=int(a[5])))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.lq_sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self):
+        _check(_lib.lq_sim_init(self.h))
+
+    def set_fields(self, c, s):
+        i = self.info[c]
+        s = np.ascontiguousarray(s, dtype=np.int8).reshape(i["L"], i["N"])
+        _check(_lib.lq_sim_set_fields(self.h, c, _p(s, C.c_int8)))
+
+    def get_fields(self, c):
+        i = self.info[c]
+        s = np.zeros((i["L"], i["N"]), np.int8)
+        _check(_lib.lq_sim_get_fields(self.h, c, _p(s, C.c_int8)))
+        return s
+
+    def set_fock(self, c, occ_up, occ_dn):
+        u = np.ascontiguousarray(occ_up, dtype=np.int32)
+        d = np.ascontiguousarray(occ_dn, dtype=np.int32)
+        i = self.info[c]
+        if len(u) != i["n_up"] or len(d) != i["n_dn"]:
+            raise ValueError("occupation lists must have n_up / n_dn entries")
+        _check(_lib.lq_sim_set_fock(self.h, c, _p(u, C.c_int32) if len(u) else None,
+                                    _p(d, C.c_int32) if len(d) else None))
+
+    def get_fock(self, c):
+        i = self.info[c]
+        u = np.zeros(max(i["n_up"], 1), np.int32)
+        d = np.zeros(max(i["n_dn"], 1), np.int32)
+        _check(_lib.lq_sim_get_fock(self.h, c, _p(u, C.c_int32), _p(d, C.c_int32)))
+        return u[: i["n_up"]].copy(), d[: i["n_dn"]].copy()
+
+    def set_sweep_index(self, k):
+        _check(_lib.lq_sim_set_sweep_index(self.h, int(k)))
+
+    def sweep(self, n=1, measure=True):
+        _check(_lib.lq_sim_sweep(self.h, int(n), int(bool(measure))))
+
+    def run_host(self, fields, occ, n_sweeps, measure=True, fields_out=None, occ_out=None, records_out=None):
+        """Batch call on host arrays (ideally pinned): fields int8 (all chains
+        concatenated), occ int32 (n_up then n_dn per chain)."""
+        f = fields
+        o = occ
+        _check(_lib.lq_sim_run_host(
+            self.h, C.cast(f.data_ptr() if hasattr(f, "data_ptr") else f.ctypes.data, C.POINTER(C.c_int8)),
+            C.cast(o.data_ptr() if hasattr(o, "data_ptr") else o.ctypes.data, C.POINTER(C.c_int32)), int(n_sweeps),
+            int(bool(measure)),
+            None if fields_out is None else C.cast(_addr(fields_out), C.POINTER(C.c_int8)),
+            None if occ_out is None else C.cast(_addr(occ_out), C.POINTER(C.c_int32)),
+            None if records_out is None else C.cast(_addr(records_out), C.POINTER(C.c_double))))
+
+    def sync(self):
+        _check(_lib.lq_sim_sync(self.h))
+
+    def log_weight(self, c):
+        la, sg = C.c_double(), C.c_int32()
+        _check(_lib.lq_sim_log_weight(self.h, c, C.byref(la), C.byref(sg)))
+        return la.value, sg.value
+
+    def tracked_weight(self, c):
+        la, sg = C.c_double(), C.c_int32()
+        _check(_lib.lq_sim_tracked_weight(self.h, c, C.byref(la), C.byref(sg)))
+        return la.value, sg.value
+
+    def field_ratio(self, c, l, i):
+        r = C.c_double()
+        _check(_lib.lq_sim_field_ratio(self.h, c, int(l), int(i), C.byref(r)))
+        return r.value
+
+    def swap_ratio(self, c, spin, k, j):
+        r = C.c_double()
+        parts = np.zeros(6)
+        _check(_lib.lq_sim_swap_ratio(self.h, c, int(spin), int(k), int(j), C.byref(r), _p(parts, C.c_double)))
+        return r.value, parts
+
+    def records(self, c, max_rows=1 << 16):
+        n = C.c_int32()
+        out = np.zeros((max_rows, LQ_NOBS))
+        _check(_lib.lq_sim_records(self.h, c, max_rows, C.byref(n), _p(out, C.c_double)))
+        return out[: min(n.value, max_rows)].copy()
+
+    def clear_records(self):
+        _check(_lib.lq_sim_clear_records(self.h))
+
+    def stats(self, c):
+        out = np.zeros(4, np.int64)
+        _check(_lib.lq_sim_stats(self.h, c, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def chain_panel(self, c, side, spin, j):
+        i = self.info[c]
+        m = i["n_up"] if spin == 0 else i["n_dn"]
+        Q = np.zeros((i["N"], max(m, 1)))
+        V = np.zeros((max(m, 1), max(m, 1)))
+        _check(_lib.lq_sim_chain_panel(self.h, c, side, spin, j, _p(Q, C.c_double), _p(V, C.c_double)))
+        return Q[:, :m].copy(), V[:m, :m].copy()
+
+    def device_bytes(self):
+        b = C.c_size_t()
+        _check(_lib.lq_sim_device_bytes(self.h, C.byref(b)))
+        return b.value
