@@ -82,6 +82,7 @@ static lq_status make_lattice(int N, const std::vector<int>& bi, const std::vect
   return LQ_OK;
 }
 
+
 extern "C" lq_status lq_lattice_from_bonds(int32_t n_sites, int32_t n_bonds, const int32_t* bi, const int32_t* bj,
                                            const double* kij, const double* onsite, const int32_t* sublattice,
                                            lq_lattice** out) {
@@ -303,7 +304,8 @@ extern "C" lq_status lq_sim_create(const lq_lattice* const* lats, const lq_param
   };
   for (int c = 0; c < n_chains; ++c) { off[c] = tot; tot += chain_bytes(c); }
   const size_t desc_off = tot;
-  tot += al256(sizeof(LqChainDev) * n_chains) + 4 * al256(sizeof(int) * (n_chains + 1));
+  tot += al256(sizeof(LqChainDev) * n_chains) + 3 * al256(sizeof(int) * (n_chains + 1)) +
+         al256(sizeof(int) * (n_chains + 1 + 1024));
   S->arena_bytes = tot;
   if (S->has_alloc) S->arena = (char*)S->alloc.alloc(S->alloc.ctx, tot, stream);
   else if (cudaMalloc((void**)&S->arena, tot) != cudaSuccess) S->arena = nullptr;
@@ -315,8 +317,8 @@ extern "C" lq_status lq_sim_create(const lq_lattice* const* lats, const lq_param
   size_t o2 = desc_off + al256(sizeof(LqChainDev) * n_chains);
   S->d_order = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
   S->d_single = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
-  S->d_queue = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
-  S->d_all = (int*)(S->arena + o2);
+  S->d_all = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
+  S->d_queue = (int*)(S->arena + o2);  // [0]: chain queue, [1..1024]: per-SM CTA counters
   // descriptors + host-side constant data (lattice tables, P = first sites)
   S->h.resize(n_chains);
   std::vector<char> stage;
