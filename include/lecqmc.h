@@ -198,6 +198,43 @@ lq_status lq_sim_chain_info(const lq_sim* sim, int32_t chain, int32_t* info6);
 lq_status lq_sim_device_bytes(const lq_sim* sim, size_t* bytes);
 lq_status lq_sim_destroy(lq_sim* sim);
 
+/* ---- allocation-free single-chain sweep ----------------------------------
+ * No counterpart in the paper: this entry point exists for callers that
+ * cannot allocate device memory themselves, for example a plug-in that must
+ * run inside a host framework which reserves all GPU memory up front, or code
+ * that may not call cudaMalloc on a latency-critical path.  It runs n_sweeps
+ * sweeps of ONE chain and allocates no device memory (and no host memory
+ * unless it fails): the caller owns the inputs and outputs, and every scratch
+ * buffer (QR chains, panels, lattice tables, the chain descriptor) lives in
+ * one fixed array of LQ_NOALLOC_SCRATCH_BYTES in device memory, which each GPU
+ * that loads the library holds until the process exits.
+ *
+ * dev_fields: device int8 L x N, +-1, updated in place.
+ * dev_occ:    device int32, n_up then n_dn occupied sites (the columns of P),
+ *             updated in place.
+ * dev_records: device double n_sweeps x LQ_NOBS per-sweep records (nullable:
+ *             no measurements).
+ * sweep_index: the Philox sweep word of the first sweep (continue a chain by
+ *             passing the previous index + n_sweeps).
+ * host_log_weight / host_sign / host_counts4 (all nullable): if any is given,
+ *             the call synchronizes the stream and returns the tracked
+ *             log|W|, its sign, and the field/swap attempt and accept counts
+ *             of this call.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the scratch, which keeps the last call's
+ * contents (every call rebuilds what it reads), so calls whose work overlaps
+ * on the GPU race; serialize them on one stream.
+ * Errors: LQ_EINVAL (bad arguments; bad fields or sites, reported when a
+ * host output is requested), LQ_EUNSUPPORTED (the chain needs more scratch
+ * than LQ_NOALLOC_SCRATCH_BYTES, or more than LQ_MAX_PARTICLES per spin),
+ * LQ_ECUDA, LQ_ENUMERIC. */
+#define LQ_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+lq_status lq_sweep_noalloc(const lq_lattice* lattice, const lq_params* params, uint32_t chain_id,
+                           uint32_t sweep_index, int8_t* dev_fields, int32_t* dev_occ, int32_t n_sweeps,
+                           double* dev_records, void* cuda_stream, double* host_log_weight, int32_t* host_sign,
+                           int64_t* host_counts4);
+
 const char* lq_last_error(void);
 const char* lq_version(void);
 

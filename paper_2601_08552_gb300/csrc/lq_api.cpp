@@ -14,6 +14,7 @@
 #include "../../include/lecqmc.h"
 #include "lq_device.h"
 #include "lq_kernels.h"
+#include "lq_lattice.h"
 
 static thread_local std::string g_err;
 
@@ -39,6 +40,9 @@ struct lq_lattice {
   std::vector<double> kb, eps;
   bool has_eps = false;
   int G = 0;
+  // family-sorted copies (read by the allocation-free entry point)
+  std::vector<int> fam_off, sorted_i, sorted_j;
+  std::vector<double> sorted_k;
 };
 
 // each bond, in order, goes to the lowest family where neither site is used
@@ -78,10 +82,31 @@ static lq_status make_lattice(int N, const std::vector<int>& bi, const std::vect
     L->sub[i] = sub ? (sub[i] ? 1 : 0) : (i & 1);
   }
   assign_families(L);
+  const int nb = (int)L->bi.size();
+  std::vector<int> order(nb);
+  for (int b = 0; b < nb; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return L->fam[a] < L->fam[b]; });
+  L->fam_off.assign(L->G + 1, 0);
+  for (int b = 0; b < nb; ++b) L->fam_off[L->fam[b] + 1]++;
+  for (int g = 0; g < L->G; ++g) L->fam_off[g + 1] += L->fam_off[g];
+  for (int t = 0; t < nb; ++t) {
+    L->sorted_i.push_back(L->bi[order[t]]);
+    L->sorted_j.push_back(L->bj[order[t]]);
+    L->sorted_k.push_back(L->kb[order[t]]);
+  }
   *out = L;
   return LQ_OK;
 }
 
+lq_lattice_view lq_lattice_get_view(const lq_lattice* L) {
+  lq_lattice_view v;
+  v.N = L->N; v.nb = (int)L->bi.size(); v.G = L->G; v.has_eps = L->has_eps;
+  v.fam_off = L->fam_off.data(); v.sorted_i = L->sorted_i.data(); v.sorted_j = L->sorted_j.data();
+  v.sorted_k = L->sorted_k.data(); v.eps = L->eps.data(); v.sub = L->sub.data();
+  return v;
+}
+
+lq_status lq_internal_fail(lq_status s, const std::string& msg) { return fail(s, msg); }
 
 extern "C" lq_status lq_lattice_from_bonds(int32_t n_sites, int32_t n_bonds, const int32_t* bi, const int32_t* bj,
                                            const double* kij, const double* onsite, const int32_t* sublattice,

@@ -28,7 +28,7 @@ EXPORTS = [
     "lq_sim_get_fock", "lq_sim_set_sweep_index", "lq_sim_sweep", "lq_sim_run_host", "lq_sim_sync", "lq_sim_log_weight",
     "lq_sim_tracked_weight", "lq_sim_field_ratio", "lq_sim_swap_ratio", "lq_sim_records",
     "lq_sim_clear_records", "lq_sim_stats", "lq_sim_chain_panel", "lq_sim_chain_info",
-    "lq_sim_device_bytes", "lq_sim_destroy", "lq_last_error", "lq_version",
+    "lq_sim_device_bytes", "lq_sim_destroy", "lq_sweep_noalloc", "lq_last_error", "lq_version",
 ]
 
 
@@ -101,6 +101,7 @@ def load(build_if_missing=True):
         "lq_sim_chain_info": [P, i32, pi32],
         "lq_sim_device_bytes": [P, C.POINTER(C.c_size_t)],
         "lq_sim_destroy": [P],
+        "lq_sweep_noalloc": [P, C.POINTER(Params), u32, u32, P, P, i32, P, P, pdbl, pi32, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -183,6 +184,31 @@ class Lattice:
         if getattr(self, "h", None) is not None and _lib is not None:
             _lib.lq_lattice_destroy(self.h)
             self.h = None
+
+
+def sweep_noalloc(lattice, params, chain_id, sweep_index, dev_fields, dev_occ, n_sweeps, dev_records=None,
+                  stream=None, want_state=True):
+    """Allocation-free single-chain sweep (lq_sweep_noalloc): dev_fields (int8
+    L x N), dev_occ (int32 n_up + n_dn) and dev_records (float64 n_sweeps x
+    LQ_NOBS, optional) are caller-owned CUDA tensors, updated in place.
+    Returns (log|W|, sign, counts4) when want_state."""
+    load()
+    import torch
+
+    p = Params(float(params["U"]), float(params["beta"]), float(params["dtau"]), int(params["n_up"]),
+               int(params["n_dn"]), int(params["n_stab"]), int(params.get("precision", LQ_FP64)),
+               int(params.get("seed", 0)) & (2**64 - 1))
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    lw, sg = C.c_double(), C.c_int32()
+    cnt = np.zeros(4, np.int64)
+    _check(_lib.lq_sweep_noalloc(lattice.h, C.byref(p), int(chain_id), int(sweep_index),
+                                 C.c_void_p(dev_fields.data_ptr()), C.c_void_p(dev_occ.data_ptr()), int(n_sweeps),
+                                 C.c_void_p(dev_records.data_ptr()) if dev_records is not None else None,
+                                 C.c_void_p(stream),
+                                 C.byref(lw) if want_state else None, C.byref(sg) if want_state else None,
+                                 cnt.ctypes.data_as(C.POINTER(C.c_int64)) if want_state else None))
+    return (lw.value, sg.value, cnt) if want_state else None
 
 
 def _torch_allocator():
