@@ -292,6 +292,7 @@ def main():
             sim.sweep(1, measure=True)
         sim.sync()
         st0 = sum(sim.stats(c) for c in range(n_chains))
+        pr0 = sum(sim.profile(c) for c in range(n_chains))
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
@@ -308,9 +309,13 @@ def main():
         sim.sync()
         st1 = sum(sim.stats(c) for c in range(n_chains))
         d = st1 - st0
-        return sim, per, total_ms, clocks, d
+        pr = sum(sim.profile(c) for c in range(n_chains)) - pr0
+        tot = max(float(pr[:6].sum()), 1.0)
+        phases = {k: round(float(pr[i]) / tot, 4) for i, k in
+                  enumerate(["flips", "propagation", "qr", "block_inverse", "swaps", "measure"])}
+        return sim, per, total_ms, clocks, d, phases
 
-    sim, per, total_ms, clocks, dstat = run(0)
+    sim, per, total_ms, clocks, dstat, phases = run(0)
     value = world * upd_per_step * args.steps / (total_ms * 1e-3)
     sweeps = world * n_chains * args.steps / (total_ms * 1e-3)
     flops = algorithmic_fp64_flops(spec, n_chains, dstat[1], dstat[0], lat.n_bonds, 0)
@@ -358,14 +363,18 @@ def main():
 
     mixed = None
     if not args.no_mixed:
-        msim, mper, mtotal, _, mstat = run(1)
-        mixed = dict(value=world * upd_per_step * args.steps / (mtotal * 1e-3), unit=UNIT,
+        mixed = {}
+        for prec, key, desc in ((1, "mixed", "FP32 panels; FP64 QR, inverses, flip algebra, ratios"),
+                                (2, "mixed_dw", "FP32 panels; double-word FP32 flip algebra; FP64 QR, inverses, "
+                                                "log-weights")):
+            msim, mper, mtotal, _, mstat, mphases = run(prec)
+            d = dict(value=world * upd_per_step * args.steps / (mtotal * 1e-3), unit=UNIT,
                      sweeps_per_s=world * n_chains * args.steps / (mtotal * 1e-3),
                      p50_ms=float(np.percentile(mper, 50)), p99_ms=float(np.percentile(mper, 99)),
-                     field_accept=float(mstat[1] / max(mstat[0], 1)),
-                     precision="FP32 panels and block Gram; FP64 QR, inverses, ratios")
-        mixed["speedup_vs_fp64"] = mixed["value"] / value
-        msim.close()
+                     field_accept=float(mstat[1] / max(mstat[0], 1)), phase_cycle_share=mphases, precision=desc)
+            d["speedup_vs_fp64"] = d["value"] / value
+            mixed[key] = d
+            msim.close()
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -377,9 +386,9 @@ def main():
                                 parallelism="independent chains, %d per GPU" % n_chains),
                     sweeps_per_s=sweeps, p50_ms=float(np.percentile(per, 50)), p99_ms=float(np.percentile(per, 99)),
                     field_accept=float(dstat[1] / max(dstat[0], 1)),
-                    swap_accept=float(dstat[3] / max(dstat[2], 1)),
+                    swap_accept=float(dstat[3] / max(dstat[2], 1)), phase_cycle_share=phases,
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
-                    mixed=mixed)
+                    reduced_precision=mixed)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

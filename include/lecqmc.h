@@ -50,11 +50,19 @@ typedef enum {
   LQ_EUNSUPPORTED = 8 /* a size outside what this build supports */
 } lq_status;
 
-/* precision of the N x N_sigma panels (slice propagation and block Gram
- * products); QR, log-det factors, the N_sigma x N_sigma inverses and all
- * Metropolis ratios are FP64 in both modes. */
+/* precision modes.
+ * LQ_FP64: everything in FP64.
+ * LQ_MIXED: the N x N_sigma panels (storage and slice propagation) in FP32;
+ *   QR, log-det factors, the N_sigma x N_sigma inverses, field-flip algebra and
+ *   all Metropolis ratios in FP64.
+ * LQ_MIXED_DW: as LQ_MIXED, but the per-site field-flip algebra (the
+ *   Sherman-Morrison ratio and rank-1 update of the inverse) runs in
+ *   double-word FP32 arithmetic (pairs of floats, about 2^-46 relative per
+ *   operation) instead of FP64, whose per-instruction cost on GB300 makes the
+ *   sequential flip loop latency bound. */
 #define LQ_FP64 0
 #define LQ_MIXED 1
+#define LQ_MIXED_DW 2
 
 /* observables of one sweep record: the mean over the measurements of the
  * sweep of sign * O (index 0 is the sign itself). */
@@ -120,7 +128,7 @@ typedef struct {
   double dtau;     /* Trotter step; L = round(beta/dtau) must be within 1e-9 */
   int32_t n_up, n_dn;
   int32_t n_stab;  /* tau_w: slices between QR restabilizations */
-  int32_t precision; /* LQ_FP64 or LQ_MIXED */
+  int32_t precision; /* LQ_FP64, LQ_MIXED or LQ_MIXED_DW */
   uint64_t seed;   /* Philox4x32-10 key */
 } lq_params;
 
@@ -188,6 +196,10 @@ lq_status lq_sim_records(lq_sim* sim, int32_t chain, int32_t max_rows, int32_t* 
 lq_status lq_sim_clear_records(lq_sim* sim);
 /* counters of chain c: field attempts, field accepts, swap attempts, swap accepts */
 lq_status lq_sim_stats(lq_sim* sim, int32_t chain, int64_t* host_counts4);
+/* SM cycles chain c spent, summed over its sweeps, per phase: field flips,
+ * slice propagation, QR restabilization, block-start Gram and inverse,
+ * particle-hole swaps, measurement, and two unused slots (host array of 8). */
+lq_status lq_sim_profile(lq_sim* sim, int32_t chain, int64_t* host_cycles8);
 /* Test hook: panel j of the right (side 0) or left (side 1) chain of a spin,
  * as FP64 host arrays Q (N x N_sigma) and V (N_sigma x N_sigma, nullable). */
 lq_status lq_sim_chain_panel(lq_sim* sim, int32_t chain, int32_t side, int32_t spin, int32_t j, double* host_Q,

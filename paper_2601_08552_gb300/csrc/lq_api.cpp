@@ -266,7 +266,8 @@ extern "C" lq_status lq_sim_create(const lq_lattice* const* lats, const lq_param
                                    const uint32_t* chain_ids, void* stream, const lq_allocator* alloc, lq_sim** out) {
   if (!out || !lats || !params || n_chains < 1) return fail(LQ_EINVAL, "bad arguments to lq_sim_create");
   const int prec = params[0].precision;
-  if (prec != LQ_FP64 && prec != LQ_MIXED) return fail(LQ_EINVAL, "precision must be LQ_FP64 or LQ_MIXED");
+  if (prec != LQ_FP64 && prec != LQ_MIXED && prec != LQ_MIXED_DW)
+    return fail(LQ_EINVAL, "precision must be LQ_FP64, LQ_MIXED or LQ_MIXED_DW");
   std::vector<ChainHost> info(n_chains);
   int M = 1, Nmax = 1;
   for (int c = 0; c < n_chains; ++c) {
@@ -419,6 +420,9 @@ extern "C" lq_status lq_sim_create(const lq_lattice* const* lats, const lq_param
     D.dfac_p = std::exp(D.lambda); D.dfac_m = std::exp(-D.lambda);
     D.delta_p = std::expm1(-2.0 * D.lambda); D.delta_m = std::expm1(2.0 * D.lambda);
     D.cfac_p = std::exp(2.0 * D.lambda); D.cfac_m = std::exp(-2.0 * D.lambda);
+    D.opd_p = 1.0 + D.delta_p; D.opd_m = 1.0 + D.delta_m;
+    lq_dw_split(D.delta_p, D.dw_delta_p); lq_dw_split(D.delta_m, D.dw_delta_m);
+    lq_dw_split(D.cfac_p, D.dw_cfac_p); lq_dw_split(D.cfac_m, D.dw_cfac_m);
     D.key0 = (uint32_t)p.seed; D.key1 = (uint32_t)(p.seed >> 32);
     D.chain_id = chain_ids ? chain_ids[c] : (uint32_t)c;
     D.sweep = 0;
@@ -705,6 +709,15 @@ extern "C" lq_status lq_sim_stats(lq_sim* S, int32_t c, int64_t* out) {
   if (st != LQ_OK) return st;
   if ((st = pull(S)) != LQ_OK) return st;
   for (int k = 0; k < 4; ++k) out[k] = S->h[c].cnt[k];
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_profile(lq_sim* S, int32_t c, int64_t* out) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if (!out) return fail(LQ_EINVAL, "null output");
+  if ((st = pull(S)) != LQ_OK) return st;
+  for (int k = 0; k < 8; ++k) out[k] = S->h[c].prof[k];
   return LQ_OK;
 }
 

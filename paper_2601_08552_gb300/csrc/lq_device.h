@@ -5,6 +5,12 @@
 #pragma once
 #include <stdint.h>
 
+// x = h + l as two FP32 values (host side; the double-word algebra of LQ_MIXED_DW)
+static inline void lq_dw_split(double x, float out[2]) {
+  out[0] = (float)x;
+  out[1] = (float)(x - (double)out[0]);
+}
+
 #define LQ_NOBS 9          // sign, n_up, n_dn, docc, ekin, szz_00, szz_11, szz_01, s_par
 #define LQ_NS_MAX 32       // particles per spin handled by the flip warps (one lane per column)
 #define LQ_THREADS 256     // threads per CTA (one CTA per chain)
@@ -38,11 +44,13 @@ struct LqChainDev {
   int N, L, tw, n;          // sites, slices, slices per block, blocks
   int ns[2];                // particles per spin
   int charge;               // 1: U < 0 (charge channel)
-  int prec;                 // 0: FP64 panels, 1: FP32 panels (mixed)
+  int prec;                 // 0: FP64 panels, 1: FP32 panels (mixed), 2: FP32 panels + double-word flips
   double lambda;
   double dfac_p, dfac_m;    // e^{+lambda}, e^{-lambda}
   double delta_p, delta_m;  // e^{-2 lambda} - 1, e^{+2 lambda} - 1
   double cfac_p, cfac_m;    // e^{+2 lambda}, e^{-2 lambda} (charge-channel scalar ratio)
+  double opd_p, opd_m;      // 1 + delta_p, 1 + delta_m (row factor of an accepted flip)
+  float dw_delta_p[2], dw_delta_m[2], dw_cfac_p[2], dw_cfac_m[2];  // double-word forms (LQ_MIXED_DW)
   uint32_t key0, key1, chain_id, sweep;
   // configuration
   int8_t* s;                // L x N fields, row = slice
@@ -65,4 +73,5 @@ struct LqChainDev {
   int err;
   long long cnt[4];         // field attempts, field accepts, swap attempts, swap accepts
   double hook[8];           // test-hook outputs
+  long long prof[8];        // cycles per phase: flips, propagation, QR, block inverse, swaps, measurement
 };

@@ -104,6 +104,36 @@ __device__ inline Smem carve(const SmemPlan& p, char* base) {
 #define TID ((int)threadIdx.x)
 #define FULL 0xffffffffu
 
+// Per-phase cycle counters of a chain (thread 0, clock64), for profiling.
+enum { PH_FLIP = 0, PH_PROP = 1, PH_QR = 2, PH_BLOCKINV = 3, PH_SWAP = 4, PH_MEAS = 5 };
+// Only the outermost timer of a nest records, so the phases add up.
+struct ProfShared {
+  LqChainDev* C;
+  int depth;
+};
+__device__ ProfShared* prof_shared() {
+  __shared__ ProfShared ps;
+  return &ps;
+}
+struct PhaseTimer {
+  int ph, outer;
+  long long t0;
+  __device__ explicit PhaseTimer(int p) : ph(p), outer(0), t0(0) {
+    if (threadIdx.x == 0) {
+      ProfShared* ps = prof_shared();
+      outer = (ps->depth++ == 0);
+      t0 = clock64();
+    }
+  }
+  __device__ ~PhaseTimer() {
+    if (threadIdx.x == 0) {
+      ProfShared* ps = prof_shared();
+      --ps->depth;
+      if (outer && ps->C) ps->C->prof[ph] += clock64() - t0;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and 53-bit uniforms
 // ---------------------------------------------------------------------------
@@ -131,6 +161,11 @@ __device__ __forceinline__ double dfac(const LqChainDev& C, int sigma, int s) {
 __device__ __forceinline__ double delta_of(const LqChainDev& C, int sigma, int s) {
   int sp = C.charge ? 1 : (sigma == 0 ? 1 : -1);
   return (sp * s > 0) ? C.delta_p : C.delta_m;
+}
+
+__device__ __forceinline__ double opd_of(const LqChainDev& C, int sigma, int s) {
+  int sp = C.charge ? 1 : (sigma == 0 ? 1 : -1);
+  return (sp * s > 0) ? C.opd_p : C.opd_m;
 }
 
 template <class R> __device__ __forceinline__ const R* bc_ptr(const LqLatticeDev& L);
@@ -162,6 +197,72 @@ __device__ double cta_sum(double v, Smem& sm) {
   return sm.red[40];
 }
 
+
+// ---------------------------------------------------------------------------
+// Double-word arithmetic on FP32 pairs (value = h + l, |l| <= ulp(h)/2):
+// Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based TwoProd error-free
+// transformations, combined into sum and product as in Joldes, Muller and
+// Popescu (ACM TOMS 2017).  Relative error about 2^-46 per operation.  The
+// _rn intrinsics keep the compiler from contracting or reassociating.
+// ---------------------------------------------------------------------------
+struct dw {
+  float h, l;
+};
+__device__ __forceinline__ dw two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dw dw_add(dw a, dw b) {
+  const dw s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dw dw_neg(dw a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dw dw_mul(dw a, dw b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dw dw_mulf(dw a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  float e = __fmaf_rn(a.h, b, -p);
+  e = __fmaf_rn(a.l, b, e);
+  return fast_two_sum(p, e);
+}
+// acc += a * t (a FP32, t double-word), unnormalized accumulator
+__device__ __forceinline__ void dw_acc(dw& acc, float a, dw t) {
+  const float ph = __fmul_rn(a, t.h);
+  float pl = __fmaf_rn(a, t.h, -ph);
+  pl = __fmaf_rn(a, t.l, pl);
+  const dw s = two_sum(acc.h, ph);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(pl, s.l));
+}
+__device__ __forceinline__ dw dw_div(dw a, dw b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const dw r = dw_add(a, dw_neg(dw_mulf(b, q1)));
+  return fast_two_sum(q1, __fdiv_rn(r.h, b.h));
+}
+__device__ __forceinline__ dw dw_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ dw dw_shfl_xor(dw a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
+__device__ __forceinline__ dw dw_shfl(dw a, int src) {
+  return {__shfl_sync(0xffffffffu, a.h, src), __shfl_sync(0xffffffffu, a.l, src)};
+}
+// a > b for normalized double-words
+__device__ __forceinline__ bool dw_gt(dw a, dw b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+
 // ---------------------------------------------------------------------------
 // Propagation: dst <- D_post * Op * D_pre * src for an N x m panel.
 // op: 0 none, 1 B_K = E_{G-1}..E_0 C_eps, 2 B_K^T = C_eps E_0..E_{G-1}.
@@ -171,6 +272,7 @@ __device__ double cta_sum(double v, Smem& sm) {
 template <class R, class S>
 __device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m, int ld, int preD, int op, int postD,
                      Smem& sm) {
+  PhaseTimer pt_(1);
   if (m == 0) return;
   const int N = C.N;
   const LqLatticeDev& lat = C.lat;
@@ -341,6 +443,7 @@ __device__ void cholesky(double* W, int ld, int m, Smem& sm) {
 // (CholeskyQR2, FP64 Gram and factors).  V goes to Vout (m x m, row-major).
 template <class R>
 __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& sm) {
+  PhaseTimer pt_(2);
   if (m == 0) return;
   const int N = C.N, MP = sm.MP;
   double* Rk[2] = {sm.S, sm.S + sm.M * MP};
@@ -348,6 +451,9 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
     double* W = Rk[pass];
     gram<double>(X, m, m, X, m, m, N, W, MP);
     cholesky(W, MP, m, sm);
+    double* rdiag = sm.vec + 8 * sm.M;
+    for (int j = TID; j < m; j += LQ_THREADS) rdiag[j] = 1.0 / W[j * MP + j];
+    __syncthreads();
     // X <- X R^{-1}, row by row (forward substitution on the row vector)
     for (int i = TID; i < N; i += LQ_THREADS) {
       R* row = X + (size_t)i * m;
@@ -356,7 +462,7 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
       for (int j = 0; j < m; ++j) {
         double acc = (double)row[j];
         for (int a = 0; a < j; ++a) acc -= y[a] * W[a * MP + j];
-        y[j] = acc / W[j * MP + j];
+        y[j] = acc * rdiag[j];
       }
       for (int j = 0; j < m; ++j) row[j] = (R)y[j];
     }
@@ -378,6 +484,7 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
 // ---------------------------------------------------------------------------
 template <class R>
 __device__ void flip_slice(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag, Smem& sm) {
+  PhaseTimer pt_(0);
   const int N = C.N, MP = sm.MP;
   const int ms[2] = {C.ns[0], C.ns[1]};
   R* Rp[2] = {Rp0, Rp1};
@@ -409,69 +516,84 @@ __device__ void flip_slice(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, c
     __syncthreads();
     const int role = (warp == sm.ip[14]) ? 0 : (warp == sm.ip[15]) ? 1 : -1;
     if (role >= 0) {
-      // One warp per spin, lane b < m owns column b of T.  FP64 work on this
-      // part is paid per active lane, so every scalar step runs on lane 0
-      // only and the reduction touches only the m live lanes.
+      // One warp per spin.  An FP64 instruction costs the same whatever the
+      // number of active lanes, so the m x m products are spread over all 32
+      // lanes: lane = (group, column) with mp2 = next power of two >= m
+      // columns and q = 32 / mp2 groups; each lane sums every q-th term and a
+      // butterfly over the groups completes the dot products.  x = R~_i T and
+      // y = T L~_i^T are computed together (y is needed on accept, ~always);
+      // comparisons run on integer bit patterns and 1/r by rcp.approx plus
+      // two Newton steps, so a site costs about 24 FP64 warp instructions.
       const int sg = role, m = ms[sg];
-      int mw = 1;
-      while (mw < m) mw <<= 1;
+      int mp2 = 1;
+      while (mp2 < m) mp2 <<= 1;
+      const int q = 32 / mp2, col = lane % mp2, grp = lane / mp2;
+      const bool live = col < m;
       double* T = sm.T[sg];
       long long nacc = 0;
-      double wprod = 1.0;  // running |r| product (lane 0 of warp 0), mantissa in [0.5, 1)
+      double wprod = 1.0;  // running |r| product (warp 0), mantissa in [0.5, 1)
       long long wexp = 0;
       int wsign = 1;
+      const int nk = (m + q - 1) / q;           // terms per lane
+      const bool upd = m > 0 && C.lambda != 0.0; // U = 0: fields are inert
       for (int ii = 0; ii < cn; ++ii) {
         double* rw = rrow + ((size_t)sg * cs + ii) * MP;
         const double* lr = lrow + ((size_t)sg * cs + ii) * MP;
-        double x = 0.0, p = 0.0;
-        if (lane < m) {
-          for (int a = 0; a < m; ++a) x = fma(rw[a], T[a * MP + lane], x);
-          p = x * lr[lane];
+        // x_b (lane column b = col) and y_a (lane column a = col)
+        double xp = 0.0, yp = 0.0;
+        if (live) {
+          for (int k = grp; k < m; k += q) {
+            xp = fma(rw[k], T[k * MP + col], xp);
+            yp = fma(T[col * MP + k], lr[k], yp);
+          }
         }
-        for (int o = mw >> 1; o > 0; o >>= 1) {
-          const double t = __shfl_down_sync(FULL, p, o);
-          if (lane < o) p += t;
+        for (int o = mp2; o < 32; o <<= 1) {
+          xp += __shfl_xor_sync(FULL, xp, o);
+          yp += __shfl_xor_sync(FULL, yp, o);
         }
-        const int par = (i0 + ii) & 1;
-        if (lane == 0) sm.gx[par * 2 + sg] = p;
-        bar_pair();
-        int acc = 0;
-        double cf = 0.0;
+        // g = sum_b x_b L~_b
+        double pg = live ? xp * lr[col] : 0.0;
+        for (int o = 1; o < mp2; o <<= 1) pg += __shfl_xor_sync(FULL, pg, o);
         const int s = sf[ii];
         const double d = delta_of(C, sg, s);
-        if (lane == 0) {
-          const double g0 = sm.gx[par * 2], g1 = sm.gx[par * 2 + 1];
-          const double d0 = delta_of(C, 0, s), d1 = delta_of(C, 1, s);
-          double r = (1.0 + d0 * g0) * (1.0 + d1 * g1);
-          if (C.charge) r *= (s > 0) ? C.cfac_p : C.cfac_m;
-          acc = uni[ii] < fabs(r);
-          if (acc) cf = d / (1.0 + d * (sg ? g1 : g0));
-          if (sg == 0) {
-            if (!(r == r) || !isfinite(r)) C.err |= LQ_ERR_NONFINITE;
-            if (acc) {
-              C.s[(size_t)l * N + i0 + ii] = (int8_t)(-s);
-              if (r < 0) wsign = -wsign;
-              wprod *= fabs(r);
-              const long long bits = __double_as_longlong(wprod);
-              wexp += ((bits >> 52) & 0x7ff) - 1022;
-              wprod = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1022LL << 52));
-              ++nacc;
-            }
+        const double rs = fma(d, pg, 1.0);  // 1 + Delta_sigma g_sigma
+        const int par = (i0 + ii) & 1;
+        if (lane == 0) sm.gx[par * 2 + sg] = rs;
+        bar_pair();
+        double r = sm.gx[par * 2] * sm.gx[par * 2 + 1];
+        if (C.charge) r *= (s > 0) ? C.cfac_p : C.cfac_m;
+        // |r| > u on the IEEE bit patterns (both non-negative doubles)
+        const long long rb = __double_as_longlong(r) & 0x7fffffffffffffffLL;
+        const long long ub = __double_as_longlong(uni[ii]);
+        const bool nan = rb > 0x7ff0000000000000LL;
+        const bool acc = !nan && rb > ub;
+        if (sg == 0 && lane == 0) {
+          if (nan || rb == 0x7ff0000000000000LL) C.err |= LQ_ERR_NONFINITE;
+          if (acc) {
+            C.s[(size_t)l * N + i0 + ii] = (int8_t)(-s);
+            if (__double_as_longlong(r) < 0) wsign = -wsign;
+            wprod *= __longlong_as_double(rb);
+            const long long bits = __double_as_longlong(wprod);
+            wexp += ((bits >> 52) & 0x7ff) - 1022;
+            wprod = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1022LL << 52));
+            ++nacc;
           }
         }
-        acc = __shfl_sync(FULL, acc, 0);
-        if (acc && m > 0 && d != 0.0) {
-          cf = __shfl_sync(FULL, cf, 0);
-          double y = 0.0;
-          if (lane < m) {
-            for (int b = 0; b < m; ++b) y = fma(T[lane * MP + b], lr[b], y);
-            y *= cf;
+        if (acc && upd) {
+          // c = Delta / r_sigma: reciprocal estimate and two Newton steps
+          double x0;
+          asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x0) : "d"(rs));
+          double e = fma(-rs, x0, 1.0);
+          x0 = fma(x0, e, x0);
+          e = fma(-rs, x0, 1.0);
+          x0 = fma(x0, e, x0);
+          const double cxb = (d * x0) * xp;  // c x_b
+          for (int t = 0; t < nk; ++t) {     // uniform trip count: shuffles stay converged
+            const int k = grp + t * q;
+            const double ya = __shfl_sync(FULL, yp, k < m ? k : 0);
+            if (live && k < m) T[k * MP + col] = fma(-ya, cxb, T[k * MP + col]);
           }
-          for (int b = 0; b < m; ++b) {
-            const double xb = __shfl_sync(FULL, x, b);
-            if (lane < m) T[lane * MP + b] = fma(-y, xb, T[lane * MP + b]);
-          }
-          if (lane < m) rw[lane] *= 1.0 + d;
+          if (lane < m) rw[lane] *= opd_of(C, sg, s);
         }
         __syncwarp();
       }
@@ -494,6 +616,175 @@ __device__ void flip_slice(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, c
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Field flips with double-word FP32 algebra (LQ_MIXED_DW): FP32 panels, the
+// inverse T in double-word form, the same lane layout as flip_slice.  The
+// dependent chain of a site is FP32 operations (~4 cycles each) instead of
+// FP64 ones, which on GB300 issue once per 64 cycles per sub-partition.
+// ---------------------------------------------------------------------------
+__device__ void flip_slice_dw(LqChainDev& C, int l, float* Rp0, float* Rp1, const float* Lp0, const float* Lp1,
+                              uint32_t tag, Smem& sm) {
+  PhaseTimer pt_(PH_FLIP);
+  const int N = C.N, MP = sm.MP;
+  const int ms[2] = {C.ns[0], C.ns[1]};
+  float* Rp[2] = {Rp0, Rp1};
+  const float* Lp[2] = {Lp0, Lp1};
+  const size_t per_site = (size_t)4 * MP * 4 + 8 + 4;
+  int cs = (int)(sm.buf_bytes / per_site);
+  if (cs > 512) cs = 512;
+  float* rrow = (float*)sm.buf;
+  float* lrow = rrow + (size_t)2 * cs * MP;
+  dw* uni = (dw*)(lrow + (size_t)2 * cs * MP);
+  int* sf = (int*)(uni + cs);
+  const int warp = TID >> 5, lane = TID & 31;
+  const int role = (warp == sm.ip[14]) ? 0 : (warp == sm.ip[15]) ? 1 : -1;
+  for (int i0 = 0; i0 < N; i0 += cs) {
+    const int cn = min(cs, N - i0);
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = ms[sg];
+      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
+        int ii = idx / m, a = idx - ii * m;
+        rrow[((size_t)sg * cs + ii) * MP + a] = Rp[sg][(size_t)(i0 + ii) * m + a];
+        lrow[((size_t)sg * cs + ii) * MP + a] = Lp[sg][(size_t)(i0 + ii) * m + a];
+      }
+    }
+    for (int ii = TID; ii < cn; ii += LQ_THREADS) {
+      uint32_t w[4];
+      philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
+      uni[ii] = dw_from(u53(w[0], w[1]));
+      sf[ii] = C.s[(size_t)l * N + i0 + ii];
+    }
+    __syncthreads();
+    if (role >= 0) {
+      const int sg = role, m = ms[sg];
+      int mp2 = 1;
+      while (mp2 < m) mp2 <<= 1;
+      const int q = 32 / mp2, col = lane % mp2, grp = lane / mp2;
+      const bool live = col < m;
+      const int nk = (m + q - 1) / q;
+      float* Th = (float*)sm.T[sg];
+      float* Tl = Th + (size_t)sm.M * MP;
+      const bool upd = m > 0 && C.lambda != 0.0;
+      const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
+      const dw dlt_p = {C.dw_delta_p[0], C.dw_delta_p[1]}, dlt_m = {C.dw_delta_m[0], C.dw_delta_m[1]};
+      const dw cf_p = {C.dw_cfac_p[0], C.dw_cfac_p[1]}, cf_m = {C.dw_cfac_m[0], C.dw_cfac_m[1]};
+      const float opf_p = (float)C.opd_p, opf_m = (float)C.opd_m;
+      long long nacc = 0;
+      dw wprod = {0.5f, 0.0f};  // running |r| product, kept in [0.5, 1) by exact power-of-two scaling
+      long long wexp = 1;
+      int wsign = 1;
+      for (int ii = 0; ii < cn; ++ii) {
+        float* rw = rrow + ((size_t)sg * cs + ii) * MP;
+        const float* lr = lrow + ((size_t)sg * cs + ii) * MP;
+        dw xp = {0.f, 0.f}, yp = {0.f, 0.f};
+        if (live) {
+          for (int k = grp; k < m; k += q) {
+            dw_acc(xp, rw[k], dw{Th[k * MP + col], Tl[k * MP + col]});
+            dw_acc(yp, lr[k], dw{Th[col * MP + k], Tl[col * MP + k]});
+          }
+          xp = fast_two_sum(xp.h, xp.l);
+          yp = fast_two_sum(yp.h, yp.l);
+        }
+        for (int o = mp2; o < 32; o <<= 1) {
+          xp = dw_add(xp, dw_shfl_xor(xp, o));
+          yp = dw_add(yp, dw_shfl_xor(yp, o));
+        }
+        dw pg = live ? dw_mulf(xp, lr[col]) : dw{0.f, 0.f};
+        for (int o = 1; o < mp2; o <<= 1) pg = dw_add(pg, dw_shfl_xor(pg, o));
+        const int s = sf[ii];
+        const dw d = (sp * s > 0) ? dlt_p : dlt_m;
+        const dw rs = dw_add(dw{1.0f, 0.0f}, dw_mul(d, pg));  // 1 + Delta_sigma g_sigma
+        const dw c = dw_div(d, rs);                            // used on accept
+        const int par = (i0 + ii) & 1;
+        if (lane == 0) { sm.gx[par * 2 + sg] = __longlong_as_double(((long long)__float_as_int(rs.l) << 32) | (unsigned)__float_as_int(rs.h)); }
+        bar_pair();
+        const long long b0 = __double_as_longlong(sm.gx[par * 2]), b1 = __double_as_longlong(sm.gx[par * 2 + 1]);
+        dw r = dw_mul(dw{__int_as_float((int)(b0 & 0xffffffff)), __int_as_float((int)(b0 >> 32))},
+                      dw{__int_as_float((int)(b1 & 0xffffffff)), __int_as_float((int)(b1 >> 32))});
+        if (C.charge) r = dw_mul(r, s > 0 ? cf_p : cf_m);
+        const bool neg = r.h < 0.f;
+        const dw ra = neg ? dw_neg(r) : r;
+        const bool nan = !(r.h == r.h);
+        const bool acc = !nan && dw_gt(ra, uni[ii]);
+        if (sg == 0 && lane == 0) {
+          if (nan || isinf(r.h)) C.err |= LQ_ERR_NONFINITE;
+          if (acc) {
+            C.s[(size_t)l * N + i0 + ii] = (int8_t)(-s);
+            if (neg) wsign = -wsign;
+            wprod = dw_mul(wprod, ra);
+            int e2;
+            frexpf(wprod.h, &e2);
+            wprod.h = ldexpf(wprod.h, -e2);
+            wprod.l = ldexpf(wprod.l, -e2);
+            wexp += e2;
+            ++nacc;
+          }
+        }
+        if (acc && upd) {
+          const dw cx = dw_mul(c, xp);
+          for (int t = 0; t < nk; ++t) {
+            const int k = grp + t * q;
+            const dw ya = dw_shfl(yp, k < m ? k : 0);
+            if (live && k < m) {
+              const dw tv = dw_add(dw{Th[k * MP + col], Tl[k * MP + col]}, dw_neg(dw_mul(ya, cx)));
+              Th[k * MP + col] = tv.h;
+              Tl[k * MP + col] = tv.l;
+            }
+          }
+          if (lane < m) rw[lane] *= (sp * s > 0) ? opf_p : opf_m;
+        }
+        __syncwarp();
+      }
+      if (sg == 0 && lane == 0) {
+        C.cnt[0] += cn;
+        C.cnt[1] += nacc;
+        C.logw += log((double)wprod.h + (double)wprod.l) + (double)wexp * 0.69314718055994530942;
+        if (wsign < 0) C.sign = -C.sign;
+      }
+    }
+    __syncthreads();
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = ms[sg];
+      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
+        int ii = idx / m, a = idx - ii * m;
+        Rp[sg][(size_t)(i0 + ii) * m + a] = rrow[((size_t)sg * cs + ii) * MP + a];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// T (FP64, ld MP) -> double-word halves in place of T[sg]
+__device__ void t_to_dw(Smem& sm, int sg, int m) {
+  double* T = sm.T[sg];
+  const int MP = sm.MP;
+  __syncthreads();
+  double* tmp = sm.W;  // staging copy
+  for (int idx = TID; idx < m * MP; idx += LQ_THREADS) tmp[idx] = T[idx];
+  __syncthreads();
+  float* Th = (float*)T;
+  float* Tl = Th + (size_t)sm.M * MP;
+  for (int idx = TID; idx < m * MP; idx += LQ_THREADS) {
+    const dw v = dw_from(tmp[idx]);
+    Th[idx] = v.h;
+    Tl[idx] = v.l;
+  }
+  __syncthreads();
+}
+
+template <class R> struct FlipDispatch {
+  __device__ static void run(LqChainDev& C, int l, R* a, R* b, const R* c, const R* d, uint32_t tag, Smem& sm) {
+    flip_slice<R>(C, l, a, b, c, d, tag, sm);
+  }
+};
+template <> struct FlipDispatch<float> {
+  __device__ static void run(LqChainDev& C, int l, float* a, float* b, const float* c, const float* d, uint32_t tag,
+                             Smem& sm) {
+    if (C.prec == 2) flip_slice_dw(C, l, a, b, c, d, tag, sm);
+    else flip_slice<float>(C, l, a, b, c, d, tag, sm);
+  }
+};
 // ---------------------------------------------------------------------------
 // helpers on the chain layout
 // ---------------------------------------------------------------------------
@@ -589,14 +880,16 @@ template <class R> __device__ void up_pass(LqChainDev& C, Smem& sm) {
       prop<R, R>(C, sg, St + (nl - 1) * pn, ql_panel<R>(C, sg, j), m, m, -1, 2, -1, sm);
       for (int l = hi - 2; l >= lo; --l) prop<R, R>(C, sg, St + (l - lo) * pn, St + (l + 1 - lo) * pn, m, m, l + 1, 2, -1, sm);
       prop<R, R>(C, sg, (R*)C.live[sg], qr_panel<R>(C, sg, C.cur[sg], j - 1), m, m, lo, 0, -1, sm);
+      PhaseTimer pt_(PH_BLOCKINV);
       gram<double>((const R*)St, m, m, (const R*)C.live[sg], m, m, N, sm.W, MP);
       double la;
       int s1;
       inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
+      if (C.prec == 2) t_to_dw(sm, sg, m);
     }
     for (int l = lo; l < hi; ++l) {
       const size_t o0 = (size_t)(l - lo) * N * C.ns[0], o1 = (size_t)(l - lo) * N * C.ns[1];
-      flip_slice<R>(C, l, (R*)C.live[0], (R*)C.live[1], (const R*)C.stored[0] + o0, (const R*)C.stored[1] + o1, 1u, sm);
+      FlipDispatch<R>::run(C, l, (R*)C.live[0], (R*)C.live[1], (const R*)C.stored[0] + o0, (const R*)C.stored[1] + o1, 1u, sm);
       for (int sg = 0; sg < 2; ++sg) {
         const int m = C.ns[sg];
         if (l + 1 < hi) {
@@ -615,6 +908,7 @@ template <class R> __device__ void up_pass(LqChainDev& C, Smem& sm) {
 // Measurement at block boundary jb from Q^L_jb and Q^R_jb.
 // ---------------------------------------------------------------------------
 template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
+  PhaseTimer pt_(5);
   const int N = C.N, MP = sm.MP, M = sm.M;
   const LqLatticeDev& lat = C.lat;
   const R* QLb[2];
@@ -735,14 +1029,16 @@ template <class R> __device__ void down_pass(LqChainDev& C, int do_measure, Smem
       prop<R, R>(C, sg, St, qr_panel<R>(C, sg, C.cur[sg], j - 1), m, m, lo, 0, -1, sm);
       for (int l = lo + 1; l < hi; ++l) prop<R, R>(C, sg, St + (l - lo) * pn, St + (l - 1 - lo) * pn, m, m, -1, 1, l, sm);
       prop<R, R>(C, sg, (R*)C.live[sg], ql_panel<R>(C, sg, j), m, m, -1, 2, -1, sm);
+      PhaseTimer pt_(PH_BLOCKINV);
       gram<double>((const R*)C.live[sg], m, m, (const R*)(St + (nl - 1) * pn), m, m, N, sm.W, MP);
       double la;
       int s1;
       inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
+      if (C.prec == 2) t_to_dw(sm, sg, m);
     }
     for (int l = hi - 1; l >= lo; --l) {
       const size_t o0 = (size_t)(l - lo) * N * C.ns[0], o1 = (size_t)(l - lo) * N * C.ns[1];
-      flip_slice<R>(C, l, (R*)C.stored[0] + o0, (R*)C.stored[1] + o1, (const R*)C.live[0], (const R*)C.live[1], 2u, sm);
+      FlipDispatch<R>::run(C, l, (R*)C.stored[0] + o0, (R*)C.stored[1] + o1, (const R*)C.live[0], (const R*)C.live[1], 2u, sm);
       for (int sg = 0; sg < 2; ++sg) {
         const int m = C.ns[sg];
         if (l > lo) {
@@ -1035,6 +1331,7 @@ __device__ int jth_empty(const Smem& sm, int N, int jidx) {
 }
 
 template <class R> __device__ void swap_phase(LqChainDev& C, Smem& sm) {
+  PhaseTimer pt_(4);
   for (int sg = 0; sg < 2; ++sg) {
     const int m = C.ns[sg];
     if (m == 0 || m == C.N) continue;
@@ -1066,6 +1363,7 @@ template <class R> __device__ void swap_phase(LqChainDev& C, Smem& sm) {
 // kernels
 // ---------------------------------------------------------------------------
 __device__ inline void load_chain(LqChainDev* g, Smem& sm) {
+  if (TID == 0) { prof_shared()->C = sm.C; prof_shared()->depth = 0; }
   const int words = (int)(sizeof(LqChainDev) / 4);
   for (int w = TID; w < words; w += LQ_THREADS) ((int*)sm.C)[w] = ((const int*)g)[w];
   __syncthreads();

@@ -53,7 +53,8 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
                                       int32_t* host_sign, int64_t* host_counts4) {
   if (!lat || !p || !dev_fields || !dev_occ || n_sweeps < 0) return lq_internal_fail(LQ_EINVAL, "bad arguments to lq_sweep_noalloc");
   const lq_lattice_view v = lq_lattice_get_view(lat);
-  if (p->precision != LQ_FP64 && p->precision != LQ_MIXED) return lq_internal_fail(LQ_EINVAL, "bad precision");
+  if (p->precision != LQ_FP64 && p->precision != LQ_MIXED && p->precision != LQ_MIXED_DW)
+    return lq_internal_fail(LQ_EINVAL, "bad precision");
   if (!(p->beta > 0) || !(p->dtau > 0) || !std::isfinite(p->U)) return lq_internal_fail(LQ_EINVAL, "beta, dtau must be > 0");
   const double Lf = p->beta / p->dtau;
   const long Ll = std::lround(Lf);
@@ -141,6 +142,9 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   D.dfac_p = std::exp(D.lambda); D.dfac_m = std::exp(-D.lambda);
   D.delta_p = std::expm1(-2.0 * D.lambda); D.delta_m = std::expm1(2.0 * D.lambda);
   D.cfac_p = std::exp(2.0 * D.lambda); D.cfac_m = std::exp(-2.0 * D.lambda);
+  D.opd_p = 1.0 + D.delta_p; D.opd_m = 1.0 + D.delta_m;
+  lq_dw_split(D.delta_p, D.dw_delta_p); lq_dw_split(D.delta_m, D.dw_delta_m);
+  lq_dw_split(D.cfac_p, D.dw_cfac_p); lq_dw_split(D.cfac_m, D.dw_cfac_m);
   D.key0 = (uint32_t)p->seed; D.key1 = (uint32_t)(p->seed >> 32);
   D.chain_id = chain_id;
   D.sweep = sweep_index;

@@ -14,6 +14,7 @@ from . import build as _build
 
 LQ_FP64 = 0
 LQ_MIXED = 1
+LQ_MIXED_DW = 2
 LQ_NOBS = 9
 OBS_NAMES = ["sign", "n_up", "n_dn", "docc", "ekin", "szz_00", "szz_11", "szz_01", "s_par"]
 LQ_MAX_PARTICLES = 32
@@ -27,7 +28,7 @@ EXPORTS = [
     "lq_sim_create", "lq_sim_init", "lq_sim_set_fields", "lq_sim_get_fields", "lq_sim_set_fock",
     "lq_sim_get_fock", "lq_sim_set_sweep_index", "lq_sim_sweep", "lq_sim_run_host", "lq_sim_sync", "lq_sim_log_weight",
     "lq_sim_tracked_weight", "lq_sim_field_ratio", "lq_sim_swap_ratio", "lq_sim_records",
-    "lq_sim_clear_records", "lq_sim_stats", "lq_sim_chain_panel", "lq_sim_chain_info",
+    "lq_sim_clear_records", "lq_sim_stats", "lq_sim_profile", "lq_sim_chain_panel", "lq_sim_chain_info",
     "lq_sim_device_bytes", "lq_sim_destroy", "lq_sweep_noalloc", "lq_last_error", "lq_version",
 ]
 
@@ -97,6 +98,7 @@ def load(build_if_missing=True):
         "lq_sim_records": [P, i32, i32, pi32, pdbl],
         "lq_sim_clear_records": [P],
         "lq_sim_stats": [P, i32, C.POINTER(C.c_int64)],
+        "lq_sim_profile": [P, i32, C.POINTER(C.c_int64)],
         "lq_sim_chain_panel": [P, i32, i32, i32, i32, pdbl, pdbl],
         "lq_sim_chain_info": [P, i32, pi32],
         "lq_sim_device_bytes": [P, C.POINTER(C.c_size_t)],
@@ -363,6 +365,12 @@ class Sim:
     def stats(self, c):
         out = np.zeros(4, np.int64)
         _check(_lib.lq_sim_stats(self.h, c, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def profile(self, c):
+        """SM cycles per phase: flips, propagation, QR, block inverse, swaps, measurement."""
+        out = np.zeros(8, np.int64)
+        _check(_lib.lq_sim_profile(self.h, c, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return out
 
     def chain_panel(self, c, side, spin, j):
