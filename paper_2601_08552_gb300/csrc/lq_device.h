@@ -14,6 +14,9 @@ static inline void lq_dw_split(double x, float out[2]) {
 #define LQ_NOBS 9          // sign, n_up, n_dn, docc, ekin, szz_00, szz_11, szz_01, s_par
 #define LQ_NS_MAX 32       // particles per spin handled by the flip warps (one lane per column)
 #define LQ_THREADS 256     // threads per CTA (one CTA per chain)
+#define LQ_WIN 8           // sites per field-flip window (submatrix update)
+// 8-byte elements of one spin's window: x rows, y rows (K x MP each), G (K x (K+1)), c (K)
+#define LQ_WIN_ELEMS(MP) (2 * LQ_WIN * (MP) + LQ_WIN * (LQ_WIN + 1) + LQ_WIN)
 
 // Error bits a kernel may set in LqChainDev::err.
 #define LQ_ERR_SINGULAR 1  // a Gram / overlap matrix had a zero pivot

@@ -33,7 +33,7 @@ __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15
 
 struct SmemPlan {
   int M, MP, Nmax, buf_bytes;
-  size_t off_T0, off_T1, off_W, off_S, off_vec, off_red, off_obs, off_gx, off_ip, off_occ, off_bits, off_chain, off_buf,
+  size_t off_T0, off_T1, off_W, off_S, off_vec, off_red, off_obs, off_gx, off_ip, off_occ, off_bits, off_chain, off_win, off_buf,
       total;
 };
 
@@ -57,6 +57,7 @@ __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
   p.off_occ = o; o = al16(o + (size_t)2 * p.M * 4);
   p.off_bits = o; o = al16(o + (size_t)(Nmax / 32 + 2) * 4);
   p.off_chain = o; o = al16(o + sizeof(LqChainDev));
+  p.off_win = o; o = al16(o + (size_t)2 * LQ_WIN_ELEMS(p.MP) * 8);
   p.off_buf = o; o = al16(o + (size_t)buf_bytes);
   p.total = o;
   return p;
@@ -76,6 +77,7 @@ struct Smem {
   int* occ2;     // 2 x M ints
   unsigned* bits;
   LqChainDev* C;
+  void* win;     // field-flip window (X, Y, G, c) per spin
   void* buf;
   int buf_bytes, M, MP;
 };
@@ -94,6 +96,7 @@ __device__ inline Smem carve(const SmemPlan& p, char* base) {
   s.occ2 = (int*)(base + p.off_occ);
   s.bits = (unsigned*)(base + p.off_bits);
   s.C = (LqChainDev*)(base + p.off_chain);
+  s.win = (void*)(base + p.off_win);
   s.buf = (void*)(base + p.off_buf);
   s.buf_bytes = p.buf_bytes;
   s.M = p.M;
@@ -479,129 +482,281 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
 }
 
 // ---------------------------------------------------------------------------
-// Field flips over all sites of slice l (ascending).  Rp: right panels (rows
-// scaled on accept), Lp: left panels (L~ transposed), T: (L~ R~)^{-1}.
+// Arithmetic policies of the field-flip loop: native FP64 (OpsF64) or
+// double-word FP32 (OpsDW).  Row is the type of the panel rows staged in
+// shared memory; T lives in shared memory as double (FP64) or as two float
+// planes (double-word).
 // ---------------------------------------------------------------------------
-template <class R>
-__device__ void flip_slice(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag, Smem& sm) {
-  PhaseTimer pt_(0);
+template <class RowT> struct OpsF64 {
+  typedef double V;
+  typedef RowT Row;
+  typedef double U;
+  struct TRef {
+    double* t;
+    __device__ V ld(int i) const { return t[i]; }
+    __device__ void st(int i, V v) const { t[i] = v; }
+  };
+  __device__ static TRef tref(Smem& sm, int sg) { return TRef{sm.T[sg]}; }
+  __device__ static V zero() { return 0.0; }
+  __device__ static void acc(V& s, Row a, V t) { s = fma((double)a, t, s); }
+  __device__ static void accT(V& s, V t, Row a) { s = fma(t, (double)a, s); }
+  __device__ static V finish(V s) { return s; }
+  __device__ static V add(V a, V b) { return a + b; }
+  __device__ static V mul(V a, V b) { return a * b; }
+  __device__ static V mulr(V a, Row b) { return a * (double)b; }
+  __device__ static V fnma(V a, V b, V c) { return fma(-a, b, c); }  // c - a b
+  __device__ static V xor_(V a, int o) { return __shfl_xor_sync(FULL, a, o); }
+  __device__ static V from_lane(V a, int src) { return __shfl_sync(FULL, a, src); }
+  __device__ static V one_plus(V d, V g) { return fma(d, g, 1.0); }
+  __device__ static V div(V d, V r) {
+    double x0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x0) : "d"(r));
+    double e = fma(-r, x0, 1.0);
+    x0 = fma(x0, e, x0);
+    e = fma(-r, x0, 1.0);
+    x0 = fma(x0, e, x0);
+    return d * x0;
+  }
+  __device__ static double pack(V v) { return v; }
+  __device__ static V unpack(double v) { return v; }
+  __device__ static U make_u(double u) { return u; }
+  __device__ static V delta(const LqChainDev& C, bool pos) { return pos ? C.delta_p : C.delta_m; }
+  __device__ static V cfac(const LqChainDev& C, bool pos) { return pos ? C.cfac_p : C.cfac_m; }
+  // |r| > u, sign and non-finite flags, on the IEEE bit patterns
+  __device__ static bool accept(V r, U u, bool* neg, bool* bad) {
+    const long long rb = __double_as_longlong(r) & 0x7fffffffffffffffLL;
+    *neg = __double_as_longlong(r) < 0;
+    *bad = rb >= 0x7ff0000000000000LL;
+    return !(*bad) && rb > __double_as_longlong(u);
+  }
+  // running product of accepted |r| as a mantissa in [0.5, 1) and an exponent
+  struct Prod {
+    double m;
+    long long e;
+    __device__ void init() { m = 1.0; e = 0; }
+    __device__ void mul(V r) {
+      m *= fabs(r);
+      const long long bits = __double_as_longlong(m);
+      e += ((bits >> 52) & 0x7ff) - 1022;
+      m = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1022LL << 52));
+    }
+    __device__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
+  };
+};
+
+struct OpsDW {
+  typedef dw V;
+  typedef float Row;
+  typedef dw U;
+  struct TRef {
+    float* h;
+    float* l;
+    __device__ V ld(int i) const { return dw{h[i], l[i]}; }
+    __device__ void st(int i, V v) const { h[i] = v.h; l[i] = v.l; }
+  };
+  __device__ static TRef tref(Smem& sm, int sg) {
+    float* h = (float*)sm.T[sg];
+    return TRef{h, h + (size_t)sm.M * sm.MP};
+  }
+  __device__ static V zero() { return dw{0.f, 0.f}; }
+  __device__ static void acc(V& s, Row a, V t) { dw_acc(s, a, t); }
+  __device__ static void accT(V& s, V t, Row a) { dw_acc(s, a, t); }
+  __device__ static V finish(V s) { return fast_two_sum(s.h, s.l); }
+  __device__ static V add(V a, V b) { return dw_add(a, b); }
+  __device__ static V mul(V a, V b) { return dw_mul(a, b); }
+  __device__ static V mulr(V a, Row b) { return dw_mulf(a, b); }
+  __device__ static V fnma(V a, V b, V c) { return dw_add(c, dw_neg(dw_mul(a, b))); }
+  __device__ static V xor_(V a, int o) { return dw_shfl_xor(a, o); }
+  __device__ static V from_lane(V a, int src) { return dw_shfl(a, src); }
+  __device__ static V one_plus(V d, V g) { return dw_add(dw{1.f, 0.f}, dw_mul(d, g)); }
+  __device__ static V div(V d, V r) { return dw_div(d, r); }
+  __device__ static double pack(V v) {
+    return __longlong_as_double(((long long)__float_as_int(v.l) << 32) | (unsigned)__float_as_int(v.h));
+  }
+  __device__ static V unpack(double x) {
+    const long long b = __double_as_longlong(x);
+    return dw{__int_as_float((int)(b & 0xffffffff)), __int_as_float((int)(b >> 32))};
+  }
+  __device__ static U make_u(double u) { return dw_from(u); }
+  __device__ static V delta(const LqChainDev& C, bool pos) {
+    return pos ? dw{C.dw_delta_p[0], C.dw_delta_p[1]} : dw{C.dw_delta_m[0], C.dw_delta_m[1]};
+  }
+  __device__ static V cfac(const LqChainDev& C, bool pos) {
+    return pos ? dw{C.dw_cfac_p[0], C.dw_cfac_p[1]} : dw{C.dw_cfac_m[0], C.dw_cfac_m[1]};
+  }
+  __device__ static bool accept(V r, U u, bool* neg, bool* bad) {
+    *neg = r.h < 0.f;
+    *bad = !(fabsf(r.h) <= 3.4e38f);
+    const dw ra = *neg ? dw_neg(r) : r;
+    return !(*bad) && dw_gt(ra, u);
+  }
+  struct Prod {
+    dw m;
+    long long e;
+    __device__ void init() { m = dw{1.f, 0.f}; e = 0; }
+    __device__ void mul(V r) {
+      m = dw_mul(m, r.h < 0.f ? dw_neg(r) : r);
+      // exact rescale by a power of two: keep m.h in [0.5, 1)
+      const int ex = ((__float_as_int(m.h) >> 23) & 0xff) - 126;
+      const float sc = __int_as_float((127 - ex) << 23);
+      m.h *= sc;
+      m.l *= sc;
+      e += ex;
+    }
+    __device__ double log_value() const { return log((double)m.h + (double)m.l) + (double)e * 0.69314718055994530942; }
+  };
+};
+
+// ---------------------------------------------------------------------------
+// Field flips over all sites of slice l (ascending) by the submatrix update:
+// windows of K consecutive sites.  With X = R~_W T (rows x_t), Y = T L~_W
+// (columns y_t) and the window Green's block G = X L~_W (K x K), a flip at
+// window site t has ratio factor 1 + Delta G[t][t] and, by Sherman-Morrison,
+//   T' = T - c y_t x_t^T,   c = Delta / (1 + Delta G[t][t]),
+// which changes the rest of the window as
+//   G[u][v] -= c G[u][t] G[t][v],  x_j -= c G[j][t] x_t,  y_j -= c G[t][j] y_t  (u, v, j > t).
+// So the serial chain of a site is G[t][t], the ratio, the exchange of the
+// two spins' factors and one K x K rank-1 update; the m-length dot products
+// are batched per window, and T takes the window's rank-1 terms at its end.
+// One warp per spin.  Rp: right panels (rows scaled on accept), Lp: left
+// panels (L~ transposed), T: (L~ R~)^{-1} in shared memory.
+// ---------------------------------------------------------------------------
+template <class R, class Ops>
+__device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag,
+                               Smem& sm) {
+  PhaseTimer pt_(PH_FLIP);
+  typedef typename Ops::V V;
+  typedef typename Ops::Row Row;
+  typedef typename Ops::U U;
   const int N = C.N, MP = sm.MP;
+  const int K = LQ_WIN, KP = LQ_WIN + 1;
   const int ms[2] = {C.ns[0], C.ns[1]};
   R* Rp[2] = {Rp0, Rp1};
   const R* Lp[2] = {Lp0, Lp1};
-  const size_t per_site = (size_t)4 * MP * 8 + 8 + 4;
+  const size_t per_site = (size_t)4 * MP * sizeof(Row) + sizeof(U) + 4 + 4;
   int cs = (int)(sm.buf_bytes / per_site);
-  if (cs > 256) cs = 256;
-  double* rrow = (double*)sm.buf;
-  double* lrow = rrow + (size_t)2 * cs * MP;
-  double* uni = lrow + (size_t)2 * cs * MP;
+  if (cs > 512) cs = 512;
+  Row* rrow = (Row*)sm.buf;
+  Row* lrow = rrow + (size_t)2 * cs * MP;
+  U* uni = (U*)(lrow + (size_t)2 * cs * MP);
   int* sf = (int*)(uni + cs);
+  int* af = sf + cs;
   const int warp = TID >> 5, lane = TID & 31;
+  const int role = (warp == sm.ip[14]) ? 0 : (warp == sm.ip[15]) ? 1 : -1;
   for (int i0 = 0; i0 < N; i0 += cs) {
     const int cn = min(cs, N - i0);
     for (int sg = 0; sg < 2; ++sg) {
       const int m = ms[sg];
       for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
         int ii = idx / m, a = idx - ii * m;
-        rrow[((size_t)sg * cs + ii) * MP + a] = (double)Rp[sg][(size_t)(i0 + ii) * m + a];
-        lrow[((size_t)sg * cs + ii) * MP + a] = (double)Lp[sg][(size_t)(i0 + ii) * m + a];
+        rrow[((size_t)sg * cs + ii) * MP + a] = (Row)Rp[sg][(size_t)(i0 + ii) * m + a];
+        lrow[((size_t)sg * cs + ii) * MP + a] = (Row)Lp[sg][(size_t)(i0 + ii) * m + a];
       }
     }
     for (int ii = TID; ii < cn; ii += LQ_THREADS) {
       uint32_t w[4];
       philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
-      uni[ii] = u53(w[0], w[1]);
+      uni[ii] = Ops::make_u(u53(w[0], w[1]));
       sf[ii] = C.s[(size_t)l * N + i0 + ii];
     }
     __syncthreads();
-    const int role = (warp == sm.ip[14]) ? 0 : (warp == sm.ip[15]) ? 1 : -1;
     if (role >= 0) {
-      // One warp per spin.  An FP64 instruction costs the same whatever the
-      // number of active lanes, so the m x m products are spread over all 32
-      // lanes: lane = (group, column) with mp2 = next power of two >= m
-      // columns and q = 32 / mp2 groups; each lane sums every q-th term and a
-      // butterfly over the groups completes the dot products.  x = R~_i T and
-      // y = T L~_i^T are computed together (y is needed on accept, ~always);
-      // comparisons run on integer bit patterns and 1/r by rcp.approx plus
-      // two Newton steps, so a site costs about 24 FP64 warp instructions.
       const int sg = role, m = ms[sg];
-      int mp2 = 1;
-      while (mp2 < m) mp2 <<= 1;
-      const int q = 32 / mp2, col = lane % mp2, grp = lane / mp2;
-      const bool live = col < m;
-      double* T = sm.T[sg];
-      long long nacc = 0;
-      double wprod = 1.0;  // running |r| product (warp 0), mantissa in [0.5, 1)
-      long long wexp = 0;
-      int wsign = 1;
-      const int nk = (m + q - 1) / q;           // terms per lane
-      const bool upd = m > 0 && C.lambda != 0.0; // U = 0: fields are inert
-      for (int ii = 0; ii < cn; ++ii) {
-        double* rw = rrow + ((size_t)sg * cs + ii) * MP;
-        const double* lr = lrow + ((size_t)sg * cs + ii) * MP;
-        // x_b (lane column b = col) and y_a (lane column a = col)
-        double xp = 0.0, yp = 0.0;
-        if (live) {
-          for (int k = grp; k < m; k += q) {
-            xp = fma(rw[k], T[k * MP + col], xp);
-            yp = fma(T[col * MP + k], lr[k], yp);
+      const typename Ops::TRef T = Ops::tref(sm, sg);
+      const bool upd = m > 0 && C.lambda != 0.0;
+      const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
+      const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
+      V* Xw = (V*)sm.win + (size_t)sg * LQ_WIN_ELEMS(MP);
+      V* Yw = Xw + K * MP;
+      V* Gw = Yw + K * MP;
+      V* cw = Gw + K * KP;
+      typename Ops::Prod wp;
+      wp.init();
+      int wsign = 1, nacc = 0, nbad = 0;
+      for (int t0 = 0; t0 < cn; t0 += K) {
+        const int kw = min(K, cn - t0);
+        // window set-up: x_t = R_t T, y_t = T L_t
+        for (int e = lane; e < kw * m; e += 32) {
+          const int t = e / m, b = e - t * m;
+          const Row* rw = rrow + ((size_t)sg * cs + t0 + t) * MP;
+          const Row* lr = lrow + ((size_t)sg * cs + t0 + t) * MP;
+          V xa = Ops::zero(), ya = Ops::zero();
+          for (int a = 0; a < m; ++a) {
+            Ops::acc(xa, rw[a], T.ld(a * MP + b));
+            Ops::accT(ya, T.ld(b * MP + a), lr[a]);
           }
+          Xw[t * MP + b] = Ops::finish(xa);
+          Yw[t * MP + b] = Ops::finish(ya);
         }
-        for (int o = mp2; o < 32; o <<= 1) {
-          xp += __shfl_xor_sync(FULL, xp, o);
-          yp += __shfl_xor_sync(FULL, yp, o);
+        __syncwarp();
+        // G[u][v] = x_u . L_v
+        for (int e = lane; e < kw * kw; e += 32) {
+          const int u = e / kw, v = e - u * kw;
+          const Row* lr = lrow + ((size_t)sg * cs + t0 + v) * MP;
+          V ga = Ops::zero();
+          for (int b = 0; b < m; ++b) Ops::accT(ga, Xw[u * MP + b], lr[b]);
+          Gw[u * KP + v] = Ops::finish(ga);
         }
-        // g = sum_b x_b L~_b
-        double pg = live ? xp * lr[col] : 0.0;
-        for (int o = 1; o < mp2; o <<= 1) pg += __shfl_xor_sync(FULL, pg, o);
-        const int s = sf[ii];
-        const double d = delta_of(C, sg, s);
-        const double rs = fma(d, pg, 1.0);  // 1 + Delta_sigma g_sigma
-        const int par = (i0 + ii) & 1;
-        if (lane == 0) sm.gx[par * 2 + sg] = rs;
-        bar_pair();
-        double r = sm.gx[par * 2] * sm.gx[par * 2 + 1];
-        if (C.charge) r *= (s > 0) ? C.cfac_p : C.cfac_m;
-        // |r| > u on the IEEE bit patterns (both non-negative doubles)
-        const long long rb = __double_as_longlong(r) & 0x7fffffffffffffffLL;
-        const long long ub = __double_as_longlong(uni[ii]);
-        const bool nan = rb > 0x7ff0000000000000LL;
-        const bool acc = !nan && rb > ub;
-        if (sg == 0 && lane == 0) {
-          if (nan || rb == 0x7ff0000000000000LL) C.err |= LQ_ERR_NONFINITE;
-          if (acc) {
-            C.s[(size_t)l * N + i0 + ii] = (int8_t)(-s);
-            if (__double_as_longlong(r) < 0) wsign = -wsign;
-            wprod *= __longlong_as_double(rb);
-            const long long bits = __double_as_longlong(wprod);
-            wexp += ((bits >> 52) & 0x7ff) - 1022;
-            wprod = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1022LL << 52));
-            ++nacc;
+        __syncwarp();
+        for (int t = 0; t < kw; ++t) {
+          const int ii = t0 + t;
+          const int s = sf[ii];
+          const bool pos = sp * s > 0;
+          const V d = Ops::delta(C, pos);
+          const V g = m > 0 ? Gw[t * KP + t] : Ops::zero();
+          const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt
+          const V c = Ops::div(d, rs);       // used if accepted
+          const int par = (i0 + ii) & 1;
+          if (lane == 0) sm.gx[par * 2 + sg] = Ops::pack(rs);
+          bar_pair();
+          V r = Ops::mul(Ops::unpack(sm.gx[par * 2]), Ops::unpack(sm.gx[par * 2 + 1]));
+          if (C.charge) r = Ops::mul(r, Ops::cfac(C, s > 0));
+          bool neg, bad;
+          const bool acc = Ops::accept(r, uni[ii], &neg, &bad);
+          const bool flip = acc && upd;
+          if (lane == 0) cw[t] = flip ? c : Ops::zero();
+          if (flip) {
+            const int rem = kw - t - 1;
+            for (int e = lane; e < rem * rem; e += 32) {
+              const int u = t + 1 + e / rem, v = t + 1 + e % rem;
+              Gw[u * KP + v] = Ops::fnma(Ops::mul(c, Gw[u * KP + t]), Gw[t * KP + v], Gw[u * KP + v]);
+            }
+            for (int e = lane; e < rem * m; e += 32) {
+              const int j = t + 1 + e / m, b = e % m;
+              Xw[j * MP + b] = Ops::fnma(Ops::mul(c, Gw[j * KP + t]), Xw[t * MP + b], Xw[j * MP + b]);
+              Yw[j * MP + b] = Ops::fnma(Ops::mul(c, Gw[t * KP + j]), Yw[t * MP + b], Yw[j * MP + b]);
+            }
+            if (lane < m) {
+              Row* rw = rrow + ((size_t)sg * cs + ii) * MP;
+              rw[lane] *= pos ? opf_p : opf_m;
+            }
           }
-        }
-        if (acc && upd) {
-          // c = Delta / r_sigma: reciprocal estimate and two Newton steps
-          double x0;
-          asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x0) : "d"(rs));
-          double e = fma(-rs, x0, 1.0);
-          x0 = fma(x0, e, x0);
-          e = fma(-rs, x0, 1.0);
-          x0 = fma(x0, e, x0);
-          const double cxb = (d * x0) * xp;  // c x_b
-          for (int t = 0; t < nk; ++t) {     // uniform trip count: shuffles stay converged
-            const int k = grp + t * q;
-            const double ya = __shfl_sync(FULL, yp, k < m ? k : 0);
-            if (live && k < m) T[k * MP + col] = fma(-ya, cxb, T[k * MP + col]);
+          if (sg == 0) {
+            if (lane == 0) af[ii] = acc ? 1 : 0;
+            nbad += bad;
+            if (acc) {
+              wp.mul(r);
+              wsign = neg ? -wsign : wsign;
+              ++nacc;
+            }
           }
-          if (lane < m) rw[lane] *= opd_of(C, sg, s);
+          __syncwarp();
+        }
+        // T <- T - sum_t c_t y_t x_t^T
+        for (int e = lane; e < m * m; e += 32) {
+          const int a = e / m, b = e - a * m;
+          V tv = T.ld(a * MP + b);
+          for (int t = 0; t < kw; ++t) tv = Ops::fnma(Ops::mul(cw[t], Yw[t * MP + a]), Xw[t * MP + b], tv);
+          T.st(a * MP + b, tv);
         }
         __syncwarp();
       }
       if (sg == 0 && lane == 0) {
         C.cnt[0] += cn;
         C.cnt[1] += nacc;
-        C.logw += log(wprod) + (double)wexp * 0.69314718055994530942;
+        C.logw += wp.log_value();
         if (wsign < 0) C.sign = -C.sign;
+        if (nbad) C.err |= LQ_ERR_NONFINITE;
       }
     }
     __syncthreads();
@@ -612,145 +767,8 @@ __device__ void flip_slice(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, c
         Rp[sg][(size_t)(i0 + ii) * m + a] = (R)rrow[((size_t)sg * cs + ii) * MP + a];
       }
     }
-    __syncthreads();
-  }
-}
-
-
-// ---------------------------------------------------------------------------
-// Field flips with double-word FP32 algebra (LQ_MIXED_DW): FP32 panels, the
-// inverse T in double-word form, the same lane layout as flip_slice.  The
-// dependent chain of a site is FP32 operations (~4 cycles each) instead of
-// FP64 ones, which on GB300 issue once per 64 cycles per sub-partition.
-// ---------------------------------------------------------------------------
-__device__ void flip_slice_dw(LqChainDev& C, int l, float* Rp0, float* Rp1, const float* Lp0, const float* Lp1,
-                              uint32_t tag, Smem& sm) {
-  PhaseTimer pt_(PH_FLIP);
-  const int N = C.N, MP = sm.MP;
-  const int ms[2] = {C.ns[0], C.ns[1]};
-  float* Rp[2] = {Rp0, Rp1};
-  const float* Lp[2] = {Lp0, Lp1};
-  const size_t per_site = (size_t)4 * MP * 4 + 8 + 4;
-  int cs = (int)(sm.buf_bytes / per_site);
-  if (cs > 512) cs = 512;
-  float* rrow = (float*)sm.buf;
-  float* lrow = rrow + (size_t)2 * cs * MP;
-  dw* uni = (dw*)(lrow + (size_t)2 * cs * MP);
-  int* sf = (int*)(uni + cs);
-  const int warp = TID >> 5, lane = TID & 31;
-  const int role = (warp == sm.ip[14]) ? 0 : (warp == sm.ip[15]) ? 1 : -1;
-  for (int i0 = 0; i0 < N; i0 += cs) {
-    const int cn = min(cs, N - i0);
-    for (int sg = 0; sg < 2; ++sg) {
-      const int m = ms[sg];
-      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
-        int ii = idx / m, a = idx - ii * m;
-        rrow[((size_t)sg * cs + ii) * MP + a] = Rp[sg][(size_t)(i0 + ii) * m + a];
-        lrow[((size_t)sg * cs + ii) * MP + a] = Lp[sg][(size_t)(i0 + ii) * m + a];
-      }
-    }
-    for (int ii = TID; ii < cn; ii += LQ_THREADS) {
-      uint32_t w[4];
-      philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
-      uni[ii] = dw_from(u53(w[0], w[1]));
-      sf[ii] = C.s[(size_t)l * N + i0 + ii];
-    }
-    __syncthreads();
-    if (role >= 0) {
-      const int sg = role, m = ms[sg];
-      int mp2 = 1;
-      while (mp2 < m) mp2 <<= 1;
-      const int q = 32 / mp2, col = lane % mp2, grp = lane / mp2;
-      const bool live = col < m;
-      const int nk = (m + q - 1) / q;
-      float* Th = (float*)sm.T[sg];
-      float* Tl = Th + (size_t)sm.M * MP;
-      const bool upd = m > 0 && C.lambda != 0.0;
-      const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
-      const dw dlt_p = {C.dw_delta_p[0], C.dw_delta_p[1]}, dlt_m = {C.dw_delta_m[0], C.dw_delta_m[1]};
-      const dw cf_p = {C.dw_cfac_p[0], C.dw_cfac_p[1]}, cf_m = {C.dw_cfac_m[0], C.dw_cfac_m[1]};
-      const float opf_p = (float)C.opd_p, opf_m = (float)C.opd_m;
-      long long nacc = 0;
-      dw wprod = {0.5f, 0.0f};  // running |r| product, kept in [0.5, 1) by exact power-of-two scaling
-      long long wexp = 1;
-      int wsign = 1;
-      for (int ii = 0; ii < cn; ++ii) {
-        float* rw = rrow + ((size_t)sg * cs + ii) * MP;
-        const float* lr = lrow + ((size_t)sg * cs + ii) * MP;
-        dw xp = {0.f, 0.f}, yp = {0.f, 0.f};
-        if (live) {
-          for (int k = grp; k < m; k += q) {
-            dw_acc(xp, rw[k], dw{Th[k * MP + col], Tl[k * MP + col]});
-            dw_acc(yp, lr[k], dw{Th[col * MP + k], Tl[col * MP + k]});
-          }
-          xp = fast_two_sum(xp.h, xp.l);
-          yp = fast_two_sum(yp.h, yp.l);
-        }
-        for (int o = mp2; o < 32; o <<= 1) {
-          xp = dw_add(xp, dw_shfl_xor(xp, o));
-          yp = dw_add(yp, dw_shfl_xor(yp, o));
-        }
-        dw pg = live ? dw_mulf(xp, lr[col]) : dw{0.f, 0.f};
-        for (int o = 1; o < mp2; o <<= 1) pg = dw_add(pg, dw_shfl_xor(pg, o));
-        const int s = sf[ii];
-        const dw d = (sp * s > 0) ? dlt_p : dlt_m;
-        const dw rs = dw_add(dw{1.0f, 0.0f}, dw_mul(d, pg));  // 1 + Delta_sigma g_sigma
-        const dw c = dw_div(d, rs);                            // used on accept
-        const int par = (i0 + ii) & 1;
-        if (lane == 0) { sm.gx[par * 2 + sg] = __longlong_as_double(((long long)__float_as_int(rs.l) << 32) | (unsigned)__float_as_int(rs.h)); }
-        bar_pair();
-        const long long b0 = __double_as_longlong(sm.gx[par * 2]), b1 = __double_as_longlong(sm.gx[par * 2 + 1]);
-        dw r = dw_mul(dw{__int_as_float((int)(b0 & 0xffffffff)), __int_as_float((int)(b0 >> 32))},
-                      dw{__int_as_float((int)(b1 & 0xffffffff)), __int_as_float((int)(b1 >> 32))});
-        if (C.charge) r = dw_mul(r, s > 0 ? cf_p : cf_m);
-        const bool neg = r.h < 0.f;
-        const dw ra = neg ? dw_neg(r) : r;
-        const bool nan = !(r.h == r.h);
-        const bool acc = !nan && dw_gt(ra, uni[ii]);
-        if (sg == 0 && lane == 0) {
-          if (nan || isinf(r.h)) C.err |= LQ_ERR_NONFINITE;
-          if (acc) {
-            C.s[(size_t)l * N + i0 + ii] = (int8_t)(-s);
-            if (neg) wsign = -wsign;
-            wprod = dw_mul(wprod, ra);
-            int e2;
-            frexpf(wprod.h, &e2);
-            wprod.h = ldexpf(wprod.h, -e2);
-            wprod.l = ldexpf(wprod.l, -e2);
-            wexp += e2;
-            ++nacc;
-          }
-        }
-        if (acc && upd) {
-          const dw cx = dw_mul(c, xp);
-          for (int t = 0; t < nk; ++t) {
-            const int k = grp + t * q;
-            const dw ya = dw_shfl(yp, k < m ? k : 0);
-            if (live && k < m) {
-              const dw tv = dw_add(dw{Th[k * MP + col], Tl[k * MP + col]}, dw_neg(dw_mul(ya, cx)));
-              Th[k * MP + col] = tv.h;
-              Tl[k * MP + col] = tv.l;
-            }
-          }
-          if (lane < m) rw[lane] *= (sp * s > 0) ? opf_p : opf_m;
-        }
-        __syncwarp();
-      }
-      if (sg == 0 && lane == 0) {
-        C.cnt[0] += cn;
-        C.cnt[1] += nacc;
-        C.logw += log((double)wprod.h + (double)wprod.l) + (double)wexp * 0.69314718055994530942;
-        if (wsign < 0) C.sign = -C.sign;
-      }
-    }
-    __syncthreads();
-    for (int sg = 0; sg < 2; ++sg) {
-      const int m = ms[sg];
-      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
-        int ii = idx / m, a = idx - ii * m;
-        Rp[sg][(size_t)(i0 + ii) * m + a] = rrow[((size_t)sg * cs + ii) * MP + a];
-      }
-    }
+    for (int ii = TID; ii < cn; ii += LQ_THREADS)
+      if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
     __syncthreads();
   }
 }
@@ -775,14 +793,14 @@ __device__ void t_to_dw(Smem& sm, int sg, int m) {
 
 template <class R> struct FlipDispatch {
   __device__ static void run(LqChainDev& C, int l, R* a, R* b, const R* c, const R* d, uint32_t tag, Smem& sm) {
-    flip_slice<R>(C, l, a, b, c, d, tag, sm);
+    flip_slice_win<R, OpsF64<R> >(C, l, a, b, c, d, tag, sm);
   }
 };
 template <> struct FlipDispatch<float> {
   __device__ static void run(LqChainDev& C, int l, float* a, float* b, const float* c, const float* d, uint32_t tag,
                              Smem& sm) {
-    if (C.prec == 2) flip_slice_dw(C, l, a, b, c, d, tag, sm);
-    else flip_slice<float>(C, l, a, b, c, d, tag, sm);
+    if (C.prec == 2) flip_slice_win<float, OpsDW>(C, l, a, b, c, d, tag, sm);
+    else flip_slice_win<float, OpsF64<float> >(C, l, a, b, c, d, tag, sm);
   }
 };
 // ---------------------------------------------------------------------------
