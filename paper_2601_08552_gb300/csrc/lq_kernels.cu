@@ -248,10 +248,13 @@ __device__ __forceinline__ void dw_acc(dw& acc, float a, dw t) {
   acc.h = s.h;
   acc.l = __fadd_rn(acc.l, __fadd_rn(pl, s.l));
 }
+// a / b: a fast FP32 quotient estimate, then one correction with the
+// double-word remainder a - b q1 (the estimate's few-ulp error is removed by
+// the second term, whose own relative error is FP32 level)
 __device__ __forceinline__ dw dw_div(dw a, dw b) {
-  const float q1 = __fdiv_rn(a.h, b.h);
+  const float q1 = __fdividef(a.h, b.h);
   const dw r = dw_add(a, dw_neg(dw_mulf(b, q1)));
-  return fast_two_sum(q1, __fdiv_rn(r.h, b.h));
+  return fast_two_sum(q1, __fdividef(r.h, b.h));
 }
 __device__ __forceinline__ dw dw_from(double x) {
   const float h = __double2float_rn(x);
@@ -617,22 +620,27 @@ struct OpsDW {
 //   G[u][v] -= c G[u][t] G[t][v],  x_j -= c G[j][t] x_t,  y_j -= c G[t][j] y_t  (u, v, j > t).
 // So the serial chain of a site is G[t][t], the ratio, the exchange of the
 // two spins' factors and one K x K rank-1 update; the m-length dot products
-// are batched per window, and T takes the window's rank-1 terms at its end.
-// One warp per spin.  Rp: right panels (rows scaled on accept), Lp: left
-// panels (L~ transposed), T: (L~ R~)^{-1} in shared memory.
+// are batched per window, the x/y recurrences run after the window's sites,
+// and T takes the window's rank-1 terms at its end.
+// One warp per spin.  MT is a compile-time bound on m (a power of two <= 32)
+// so that every lane-to-element map is a shift and every element loop
+// unrolls.  Rp: right panels (rows scaled on accept), Lp: left panels (L~
+// transposed), T: (L~ R~)^{-1} in shared memory.
 // ---------------------------------------------------------------------------
-template <class R, class Ops>
+template <class R, class Ops, int MT>
 __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag,
                                Smem& sm) {
   PhaseTimer pt_(PH_FLIP);
   typedef typename Ops::V V;
   typedef typename Ops::Row Row;
   typedef typename Ops::U U;
+  constexpr int K = LQ_WIN, KP = LQ_WIN + 1;
+  constexpr int XE = (K * MT + 31) / 32;         // x/y elements per lane
+  constexpr int GE = (K * K) / 32;               // window-block elements per lane
+  constexpr int TE = (MT * MT + 31) / 32;        // T elements per lane
+  constexpr int XU = XE < 2 ? XE : 2, TU = TE < 2 ? TE : 2;  // unroll of the per-lane element loops
   const int N = C.N, MP = sm.MP;
-  const int K = LQ_WIN, KP = LQ_WIN + 1;
-  const int ms[2] = {C.ns[0], C.ns[1]};
-  R* Rp[2] = {Rp0, Rp1};
-  const R* Lp[2] = {Lp0, Lp1};
+  const int m0 = C.ns[0], m1 = C.ns[1];
   const size_t per_site = (size_t)4 * MP * sizeof(Row) + sizeof(U) + 4 + 4;
   int cs = (int)(sm.buf_bytes / per_site);
   if (cs > 512) cs = 512;
@@ -646,11 +654,17 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
   for (int i0 = 0; i0 < N; i0 += cs) {
     const int cn = min(cs, N - i0);
     for (int sg = 0; sg < 2; ++sg) {
-      const int m = ms[sg];
-      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
-        int ii = idx / m, a = idx - ii * m;
-        rrow[((size_t)sg * cs + ii) * MP + a] = (Row)Rp[sg][(size_t)(i0 + ii) * m + a];
-        lrow[((size_t)sg * cs + ii) * MP + a] = (Row)Lp[sg][(size_t)(i0 + ii) * m + a];
+      const int m = sg ? m1 : m0;
+      const R* rp = sg ? Rp1 : Rp0;
+      const R* lp = sg ? Lp1 : Lp0;
+      Row* rr = rrow + (size_t)sg * cs * MP;
+      Row* ll = lrow + (size_t)sg * cs * MP;
+      for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
+        const int a = TID % MT;
+        if (a < m) {
+          rr[(size_t)ii * MP + a] = (Row)rp[(size_t)(i0 + ii) * m + a];
+          ll[(size_t)ii * MP + a] = (Row)lp[(size_t)(i0 + ii) * m + a];
+        }
       }
     }
     for (int ii = TID; ii < cn; ii += LQ_THREADS) {
@@ -661,48 +675,62 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
     }
     __syncthreads();
     if (role >= 0) {
-      const int sg = role, m = ms[sg];
+      const int sg = role, m = sg ? m1 : m0;
       const typename Ops::TRef T = Ops::tref(sm, sg);
       const bool upd = m > 0 && C.lambda != 0.0;
       const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
       const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
+      const V d_p = Ops::delta(C, true), d_m = Ops::delta(C, false);
+      const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
       V* Xw = (V*)sm.win + (size_t)sg * LQ_WIN_ELEMS(MP);
       V* Yw = Xw + K * MP;
       V* Gw = Yw + K * MP;
       V* cw = Gw + K * KP;
+      const Row* rbase = rrow + (size_t)sg * cs * MP;
+      const Row* lbase = lrow + (size_t)sg * cs * MP;
       typename Ops::Prod wp;
       wp.init();
       int wsign = 1, nacc = 0, nbad = 0;
       for (int t0 = 0; t0 < cn; t0 += K) {
         const int kw = min(K, cn - t0);
-        // window set-up: x_t = R_t T, y_t = T L_t
-        for (int e = lane; e < kw * m; e += 32) {
-          const int t = e / m, b = e - t * m;
-          const Row* rw = rrow + ((size_t)sg * cs + t0 + t) * MP;
-          const Row* lr = lrow + ((size_t)sg * cs + t0 + t) * MP;
-          V xa = Ops::zero(), ya = Ops::zero();
-          for (int a = 0; a < m; ++a) {
-            Ops::acc(xa, rw[a], T.ld(a * MP + b));
-            Ops::accT(ya, T.ld(b * MP + a), lr[a]);
+        // window set-up: x_t = R_t T, y_t = T L_t   (element (t, b), b = lane % MT)
+#pragma unroll XU
+        for (int it = 0; it < XE; ++it) {
+          const int e = lane + 32 * it, t = e / MT, b = e % MT;
+          if (e < K * MT && t < kw && b < m) {
+            const Row* rw = rbase + (size_t)(t0 + t) * MP;
+            const Row* lr = lbase + (size_t)(t0 + t) * MP;
+            V xa = Ops::zero(), ya = Ops::zero();
+#pragma unroll
+            for (int a = 0; a < MT; ++a)
+              if (a < m) {
+                Ops::acc(xa, rw[a], T.ld(a * MP + b));
+                Ops::accT(ya, T.ld(b * MP + a), lr[a]);
+              }
+            Xw[t * MP + b] = Ops::finish(xa);
+            Yw[t * MP + b] = Ops::finish(ya);
           }
-          Xw[t * MP + b] = Ops::finish(xa);
-          Yw[t * MP + b] = Ops::finish(ya);
         }
         __syncwarp();
-        // G[u][v] = x_u . L_v
-        for (int e = lane; e < kw * kw; e += 32) {
-          const int u = e / kw, v = e - u * kw;
-          const Row* lr = lrow + ((size_t)sg * cs + t0 + v) * MP;
-          V ga = Ops::zero();
-          for (int b = 0; b < m; ++b) Ops::accT(ga, Xw[u * MP + b], lr[b]);
-          Gw[u * KP + v] = Ops::finish(ga);
+        // G[u][v] = x_u . L_v   (element (u, v), v = lane % K)
+#pragma unroll
+        for (int it = 0; it < GE; ++it) {
+          const int e = lane + 32 * it, u = e / K, v = e % K;
+          if (u < kw && v < kw) {
+            const Row* lr = lbase + (size_t)(t0 + v) * MP;
+            V ga = Ops::zero();
+#pragma unroll
+            for (int b = 0; b < MT; ++b)
+              if (b < m) Ops::accT(ga, Xw[u * MP + b], lr[b]);
+            Gw[u * KP + v] = Ops::finish(ga);
+          }
         }
         __syncwarp();
         for (int t = 0; t < kw; ++t) {
           const int ii = t0 + t;
           const int s = sf[ii];
           const bool pos = sp * s > 0;
-          const V d = Ops::delta(C, pos);
+          const V d = pos ? d_p : d_m;
           const V g = m > 0 ? Gw[t * KP + t] : Ops::zero();
           const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt
           const V c = Ops::div(d, rs);       // used if accepted
@@ -710,21 +738,17 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
           if (lane == 0) sm.gx[par * 2 + sg] = Ops::pack(rs);
           bar_pair();
           V r = Ops::mul(Ops::unpack(sm.gx[par * 2]), Ops::unpack(sm.gx[par * 2 + 1]));
-          if (C.charge) r = Ops::mul(r, Ops::cfac(C, s > 0));
+          if (C.charge) r = Ops::mul(r, s > 0 ? cf_p : cf_m);
           bool neg, bad;
           const bool acc = Ops::accept(r, uni[ii], &neg, &bad);
           const bool flip = acc && upd;
           if (lane == 0) cw[t] = flip ? c : Ops::zero();
           if (flip) {
-            const int rem = kw - t - 1;
-            for (int e = lane; e < rem * rem; e += 32) {
-              const int u = t + 1 + e / rem, v = t + 1 + e % rem;
-              Gw[u * KP + v] = Ops::fnma(Ops::mul(c, Gw[u * KP + t]), Gw[t * KP + v], Gw[u * KP + v]);
-            }
-            for (int e = lane; e < rem * m; e += 32) {
-              const int j = t + 1 + e / m, b = e % m;
-              Xw[j * MP + b] = Ops::fnma(Ops::mul(c, Gw[j * KP + t]), Xw[t * MP + b], Xw[j * MP + b]);
-              Yw[j * MP + b] = Ops::fnma(Ops::mul(c, Gw[t * KP + j]), Yw[t * MP + b], Yw[j * MP + b]);
+#pragma unroll
+            for (int it = 0; it < GE; ++it) {
+              const int e = lane + 32 * it, u = e / K, v = e % K;
+              if (u > t && v > t && u < kw && v < kw)
+                Gw[u * KP + v] = Ops::fnma(Ops::mul(c, Gw[u * KP + t]), Gw[t * KP + v], Gw[u * KP + v]);
             }
             if (lane < m) {
               Row* rw = rrow + ((size_t)sg * cs + ii) * MP;
@@ -742,12 +766,33 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
           }
           __syncwarp();
         }
-        // T <- T - sum_t c_t y_t x_t^T
-        for (int e = lane; e < m * m; e += 32) {
-          const int a = e / m, b = e - a * m;
-          V tv = T.ld(a * MP + b);
-          for (int t = 0; t < kw; ++t) tv = Ops::fnma(Ops::mul(cw[t], Yw[t * MP + a]), Xw[t * MP + b], tv);
-          T.st(a * MP + b, tv);
+        // the window's x_j, y_j at their flip times: column t and row t of the
+        // block are frozen once site t is done, so the recurrences
+        //   x_j -= c_t G[j][t] x_t,  y_j -= c_t G[t][j] y_t  (j > t)
+        // run here, t ascending, parallel over (j, b)
+        for (int t = 0; t + 1 < kw; ++t) {
+          const V ct = cw[t];
+#pragma unroll XU
+          for (int it = 0; it < XE; ++it) {
+            const int e = lane + 32 * it, j = e / MT, b = e % MT;
+            if (e < K * MT && j > t && j < kw && b < m) {
+              Xw[j * MP + b] = Ops::fnma(Ops::mul(ct, Gw[j * KP + t]), Xw[t * MP + b], Xw[j * MP + b]);
+              Yw[j * MP + b] = Ops::fnma(Ops::mul(ct, Gw[t * KP + j]), Yw[t * MP + b], Yw[j * MP + b]);
+            }
+          }
+          __syncwarp();
+        }
+        // T <- T - sum_t c_t y_t x_t^T   (element (a, b), b = lane % MT)
+#pragma unroll TU
+        for (int it = 0; it < TE; ++it) {
+          const int e = lane + 32 * it, a = e / MT, b = e % MT;
+          if (e < MT * MT && a < m && b < m) {
+            V tv = T.ld(a * MP + b);
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+              if (t < kw) tv = Ops::fnma(Ops::mul(cw[t], Yw[t * MP + a]), Xw[t * MP + b], tv);
+            T.st(a * MP + b, tv);
+          }
         }
         __syncwarp();
       }
@@ -761,16 +806,28 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
     }
     __syncthreads();
     for (int sg = 0; sg < 2; ++sg) {
-      const int m = ms[sg];
-      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
-        int ii = idx / m, a = idx - ii * m;
-        Rp[sg][(size_t)(i0 + ii) * m + a] = (R)rrow[((size_t)sg * cs + ii) * MP + a];
+      const int m = sg ? m1 : m0;
+      R* rp = sg ? Rp1 : Rp0;
+      const Row* rr = rrow + (size_t)sg * cs * MP;
+      for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
+        const int a = TID % MT;
+        if (a < m) rp[(size_t)(i0 + ii) * m + a] = (R)rr[(size_t)ii * MP + a];
       }
     }
     for (int ii = TID; ii < cn; ii += LQ_THREADS)
       if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
     __syncthreads();
   }
+}
+
+// the smallest compile-time column bound that holds both spins' particle numbers
+template <class R, class Ops>
+__device__ void flip_slice_any(LqChainDev& C, int l, R* a, R* b, const R* c, const R* d, uint32_t tag, Smem& sm) {
+  const int m = max(C.ns[0], C.ns[1]);
+  if (m <= 4) flip_slice_win<R, Ops, 4>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 8) flip_slice_win<R, Ops, 8>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 16) flip_slice_win<R, Ops, 16>(C, l, a, b, c, d, tag, sm);
+  else flip_slice_win<R, Ops, 32>(C, l, a, b, c, d, tag, sm);
 }
 
 // T (FP64, ld MP) -> double-word halves in place of T[sg]
@@ -793,14 +850,14 @@ __device__ void t_to_dw(Smem& sm, int sg, int m) {
 
 template <class R> struct FlipDispatch {
   __device__ static void run(LqChainDev& C, int l, R* a, R* b, const R* c, const R* d, uint32_t tag, Smem& sm) {
-    flip_slice_win<R, OpsF64<R> >(C, l, a, b, c, d, tag, sm);
+    flip_slice_any<R, OpsF64<R> >(C, l, a, b, c, d, tag, sm);
   }
 };
 template <> struct FlipDispatch<float> {
   __device__ static void run(LqChainDev& C, int l, float* a, float* b, const float* c, const float* d, uint32_t tag,
                              Smem& sm) {
-    if (C.prec == 2) flip_slice_win<float, OpsDW>(C, l, a, b, c, d, tag, sm);
-    else flip_slice_win<float, OpsF64<float> >(C, l, a, b, c, d, tag, sm);
+    if (C.prec == 2) flip_slice_any<float, OpsDW>(C, l, a, b, c, d, tag, sm);
+    else flip_slice_any<float, OpsF64<float> >(C, l, a, b, c, d, tag, sm);
   }
 };
 // ---------------------------------------------------------------------------
