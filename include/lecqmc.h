@@ -210,6 +210,57 @@ lq_status lq_sim_chain_info(const lq_sim* sim, int32_t chain, int32_t* info6);
 lq_status lq_sim_device_bytes(const lq_sim* sim, size_t* bytes);
 lq_status lq_sim_destroy(lq_sim* sim);
 
+/* Sign-weighted means <sign O>/<sign> over chain c's per-sweep records and
+ * their jackknife errors over n_bins bins (host arrays of LQ_NOBS; index 0
+ * holds the mean sign and a zero error). */
+lq_status lq_sim_measure(lq_sim* sim, int32_t chain, int32_t n_bins, double* host_mean, double* host_err);
+
+/* ---- serving loop (continuous batching) -----------------------------------
+ * A host thread owns one non-blocking CUDA stream on `device` and runs ticks:
+ * admit queued requests first come first served while their device footprint
+ * fits hbm_budget and fewer than max_active run; then one sweep of every
+ * active request in ONE persistent launch (requests that arrive while others
+ * run join the next launch); then retire requests that finished their sweeps.
+ * All requests share the server's precision.  Device memory comes from
+ * cudaMalloc (the allocator hook is not used from the server thread). */
+typedef struct lq_server lq_server;
+typedef struct {
+  const lq_lattice* lattice; /* copied at submit; the caller may destroy it */
+  lq_params params;
+  int32_t n_sweeps;          /* sweeps, each measured */
+  uint32_t chain_id;         /* Philox chain word */
+} lq_request;
+typedef struct {
+  int32_t status;            /* LQ_OK or the error that ended the request */
+  int32_t n_records;
+  double obs_mean[LQ_NOBS];  /* sign-weighted means, index 0 = mean sign */
+  double obs_err[LQ_NOBS];   /* jackknife errors */
+  double log_weight;         /* tracked log|W| at the end */
+  int32_t sign;
+  int64_t counts[4];         /* field attempts, accepts, swap attempts, accepts */
+  double queue_ms;           /* submit -> admission */
+  double total_ms;           /* submit -> retirement */
+  double sweep_ms_mean;      /* mean per-sweep latency this request saw */
+} lq_result;
+typedef struct {
+  double p50_sweep_ms, p99_sweep_ms; /* per-sweep latency over all active requests and ticks */
+  double updates_per_s;              /* field-update attempts per second of device busy time */
+  double busy_s, wall_s;
+  int64_t submitted, admitted, completed, rejected, active, queued;
+  size_t hbm_in_use;
+} lq_server_info;
+/* Errors: LQ_EINVAL for a bad budget, slot count, queue capacity or precision. */
+lq_status lq_server_create(int32_t device, size_t hbm_budget, int32_t precision, int32_t max_active,
+                           int32_t queue_capacity, lq_server** out);
+/* Never blocks.  LQ_EBUSY when the queue is full; LQ_EINVAL when the request's
+ * footprint exceeds the whole budget or its precision differs. */
+lq_status lq_server_submit(lq_server* srv, const lq_request* request, uint64_t* id);
+/* LQ_ENOTFOUND until the request is done; then fills *out once and forgets it. */
+lq_status lq_server_poll(lq_server* srv, uint64_t id, lq_result* out);
+lq_status lq_server_stats(lq_server* srv, lq_server_info* out);
+/* Finishes every admitted request, drops the queued ones, joins the thread. */
+lq_status lq_server_destroy(lq_server* srv);
+
 /* ---- allocation-free single-chain sweep ----------------------------------
  * No counterpart in the paper: this entry point exists for callers that
  * cannot allocate device memory themselves, for example a plug-in that must

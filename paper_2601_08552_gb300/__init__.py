@@ -3,4 +3,4 @@
 The sweep runs in the CUDA library built from ``csrc/`` (C ABI in
 ``include/lecqmc.h``); ``lecqmc`` is its ctypes binding.
 """
-from .lecqmc import (LQ_FP64, LQ_MIXED, LQ_MIXED_DW, LQ_NOBS, OBS_NAMES, Lattice, LqError, Sim, load)  # noqa: F401
+from .lecqmc import (LQ_FP64, LQ_MIXED, LQ_MIXED_DW, LQ_NOBS, OBS_NAMES, Lattice, LqError, Server, Sim, load)  # noqa: F401

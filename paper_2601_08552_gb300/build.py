@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblecqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lq_kernels.cu", "lq_api.cpp", "lq_noalloc.cu"]
+SOURCES = ["lq_kernels.cu", "lq_api.cpp", "lq_noalloc.cu", "lq_server.cpp"]
 
 
 def _nvcc():

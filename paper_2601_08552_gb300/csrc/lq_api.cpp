@@ -15,6 +15,7 @@
 #include "lq_device.h"
 #include "lq_kernels.h"
 #include "lq_lattice.h"
+#include "lq_internal.h"
 
 static thread_local std::string g_err;
 
@@ -260,6 +261,22 @@ static lq_status check_chain(const lq_sim* S, int c) {
   if (!S) return fail(LQ_EINVAL, "null simulation");
   if (c < 0 || c >= S->n_chains) return fail(LQ_EINVAL, "chain index out of range");
   return LQ_OK;
+}
+
+static size_t footprint_one(int N, int nb, int G, int L, int tw, const int ns[2], int prec, int max_records) {
+  const size_t PS = prec == LQ_FP64 ? sizeof(double) : sizeof(float);
+  const int n = (L + tw - 1) / tw;
+  size_t b = al256((G + 1) * 4) + 3 * al256(nb * 4) + 3 * al256(nb * 8) + 2 * al256(nb * 4) + 3 * al256(N * 8) +
+             al256(N * 4) + al256(N * 4) + al256((size_t)L * N);
+  for (int sg = 0; sg < 2; ++sg) {
+    const size_t pn = (size_t)N * ns[sg], qn = (size_t)ns[sg] * ns[sg];
+    b += al256(std::max(ns[sg], 1) * 4);
+    b += 2 * al256((n + 1) * pn * PS) + 2 * al256((n + 1) * qn * 8);
+    b += al256((n + 1) * pn * PS) + al256((n + 1) * qn * 8);
+    b += al256(tw * pn * PS) + al256(pn * PS) + al256(pn * 8);
+  }
+  b += al256((size_t)2 * N * 8) + al256((size_t)n * LQ_NS_MAX * 2 * 8) + al256((size_t)max_records * LQ_NOBS * 8);
+  return b + al256(sizeof(LqChainDev)) + 4 * al256(sizeof(int) * 1026);
 }
 
 extern "C" lq_status lq_sim_create(const lq_lattice* const* lats, const lq_params* params, int32_t n_chains,
@@ -774,3 +791,67 @@ extern "C" lq_status lq_sim_destroy(lq_sim* S) {
 
 extern "C" const char* lq_last_error(void) { return g_err.c_str(); }
 extern "C" const char* lq_version(void) { return "lecqmc-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// internal hooks (serving loop) and observable statistics
+// ---------------------------------------------------------------------------
+lq_sim_launch_info lq_internal_sim_info(const lq_sim* S) {
+  lq_sim_launch_info i;
+  i.d_chains = S->d_chains; i.n_chains = S->n_chains; i.prec = S->prec; i.M = S->M; i.Nmax = S->Nmax;
+  i.buf_bytes = S->buf_bytes; i.arena_bytes = S->arena_bytes;
+  return i;
+}
+
+void lq_internal_sim_invalidate(lq_sim* S) { S->mirror_fresh = false; }
+
+size_t lq_internal_footprint(const lq_lattice* L, const lq_params* p) {
+  const long Ll = std::lround(p->beta / p->dtau);
+  const int ns[2] = {p->n_up, p->n_dn};
+  return footprint_one(L->N, (int)L->bi.size(), L->G, (int)Ll, std::max(p->n_stab, 1), ns, p->precision, 1 << 16);
+}
+
+void lq_internal_obs_stats(const double* rec, int n, int nbins, double* mean, double* err) {
+  for (int k = 0; k < LQ_NOBS; ++k) { mean[k] = NAN; err[k] = NAN; }
+  if (n <= 0) return;
+  double tot[LQ_NOBS] = {0};
+  for (int r = 0; r < n; ++r)
+    for (int k = 0; k < LQ_NOBS; ++k) tot[k] += rec[(size_t)r * LQ_NOBS + k];
+  mean[0] = tot[0] / n;
+  for (int k = 1; k < LQ_NOBS; ++k) mean[k] = tot[k] / tot[0];
+  err[0] = 0.0;
+  nbins = std::min(nbins, n);
+  if (nbins < 2) return;
+  const int per = n / nbins;
+  std::vector<double> bsum((size_t)nbins * LQ_NOBS, 0.0);
+  for (int b = 0; b < nbins; ++b)
+    for (int r = b * per; r < (b + 1) * per; ++r)
+      for (int k = 0; k < LQ_NOBS; ++k) bsum[(size_t)b * LQ_NOBS + k] += rec[(size_t)r * LQ_NOBS + k];
+  double used[LQ_NOBS] = {0};
+  for (int b = 0; b < nbins; ++b)
+    for (int k = 0; k < LQ_NOBS; ++k) used[k] += bsum[(size_t)b * LQ_NOBS + k];
+  for (int k = 0; k < LQ_NOBS; ++k) {
+    double jm = 0.0, j2 = 0.0;
+    for (int b = 0; b < nbins; ++b) {
+      const double num = used[k] - bsum[(size_t)b * LQ_NOBS + k];
+      const double den = (k == 0) ? (double)(nbins - 1) * per : used[0] - bsum[(size_t)b * LQ_NOBS];
+      const double v = num / den;
+      jm += v;
+      j2 += v * v;
+    }
+    jm /= nbins;
+    const double var = (double)(nbins - 1) / nbins * std::max(0.0, j2 - nbins * jm * jm);
+    err[k] = std::sqrt(var);
+  }
+}
+
+extern "C" lq_status lq_sim_measure(lq_sim* S, int32_t c, int32_t n_bins, double* mean, double* err) {
+  lq_status st = check_chain(S, c);
+  if (st != LQ_OK) return st;
+  if (!mean || !err || n_bins < 2) return fail(LQ_EINVAL, "need mean/err outputs and n_bins >= 2");
+  if ((st = pull(S)) != LQ_OK) return st;
+  const int n = S->h[c].nrec;
+  std::vector<double> rec((size_t)std::max(n, 1) * LQ_NOBS);
+  if (n > 0) CK(cudaMemcpy(rec.data(), S->h[c].records, sizeof(double) * n * LQ_NOBS, cudaMemcpyDeviceToHost));
+  lq_internal_obs_stats(rec.data(), n, n_bins, mean, err);
+  return LQ_OK;
+}

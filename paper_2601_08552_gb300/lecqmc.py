@@ -29,7 +29,8 @@ EXPORTS = [
     "lq_sim_get_fock", "lq_sim_set_sweep_index", "lq_sim_sweep", "lq_sim_run_host", "lq_sim_sync", "lq_sim_log_weight",
     "lq_sim_tracked_weight", "lq_sim_field_ratio", "lq_sim_swap_ratio", "lq_sim_records",
     "lq_sim_clear_records", "lq_sim_stats", "lq_sim_profile", "lq_sim_chain_panel", "lq_sim_chain_info",
-    "lq_sim_device_bytes", "lq_sim_destroy", "lq_sweep_noalloc", "lq_last_error", "lq_version",
+    "lq_sim_device_bytes", "lq_sim_destroy", "lq_sim_measure", "lq_server_create", "lq_server_submit",
+    "lq_server_poll", "lq_server_stats", "lq_server_destroy", "lq_sweep_noalloc", "lq_last_error", "lq_version",
 ]
 
 
@@ -46,6 +47,24 @@ class Params(C.Structure):
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class Request(C.Structure):
+    _fields_ = [("lattice", C.c_void_p), ("params", Params), ("n_sweeps", C.c_int32), ("chain_id", C.c_uint32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_records", C.c_int32), ("obs_mean", C.c_double * 9),
+                ("obs_err", C.c_double * 9), ("log_weight", C.c_double), ("sign", C.c_int32),
+                ("counts", C.c_int64 * 4), ("queue_ms", C.c_double), ("total_ms", C.c_double),
+                ("sweep_ms_mean", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("p50_sweep_ms", C.c_double), ("p99_sweep_ms", C.c_double), ("updates_per_s", C.c_double),
+                ("busy_s", C.c_double), ("wall_s", C.c_double), ("submitted", C.c_int64), ("admitted", C.c_int64),
+                ("completed", C.c_int64), ("rejected", C.c_int64), ("active", C.c_int64), ("queued", C.c_int64),
+                ("hbm_in_use", C.c_size_t)]
 
 
 class Allocator(C.Structure):
@@ -104,6 +123,12 @@ def load(build_if_missing=True):
         "lq_sim_device_bytes": [P, C.POINTER(C.c_size_t)],
         "lq_sim_destroy": [P],
         "lq_sweep_noalloc": [P, C.POINTER(Params), u32, u32, P, P, i32, P, P, pdbl, pi32, C.POINTER(C.c_int64)],
+        "lq_sim_measure": [P, i32, i32, pdbl, pdbl],
+        "lq_server_create": [i32, C.c_size_t, i32, i32, i32, C.POINTER(P)],
+        "lq_server_submit": [P, C.POINTER(Request), C.POINTER(C.c_uint64)],
+        "lq_server_poll": [P, C.c_uint64, C.POINTER(Result)],
+        "lq_server_stats": [P, C.POINTER(ServerStats)],
+        "lq_server_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -373,6 +398,13 @@ class Sim:
         _check(_lib.lq_sim_profile(self.h, c, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return out
 
+    def measure(self, c, n_bins=16):
+        """Sign-weighted means and jackknife errors over chain c's records."""
+        mean = np.zeros(LQ_NOBS)
+        err = np.zeros(LQ_NOBS)
+        _check(_lib.lq_sim_measure(self.h, c, int(n_bins), _p(mean, C.c_double), _p(err, C.c_double)))
+        return mean, err
+
     def chain_panel(self, c, side, spin, j):
         i = self.info[c]
         m = i["n_up"] if spin == 0 else i["n_dn"]
@@ -385,3 +417,54 @@ class Sim:
         b = C.c_size_t()
         _check(_lib.lq_sim_device_bytes(self.h, C.byref(b)))
         return b.value
+
+
+def _params_struct(p):
+    return Params(float(p["U"]), float(p["beta"]), float(p["dtau"]), int(p["n_up"]), int(p["n_dn"]),
+                  int(p["n_stab"]), int(p.get("precision", LQ_FP64)), int(p.get("seed", 0)) & (2**64 - 1))
+
+
+class Server:
+    """Continuous-batching serving loop (lq_server_*)."""
+
+    def __init__(self, hbm_budget, precision=LQ_FP64, max_active=256, queue_capacity=4096, device=0):
+        load()
+        out = C.c_void_p()
+        _check(_lib.lq_server_create(int(device), int(hbm_budget), int(precision), int(max_active),
+                                     int(queue_capacity), C.byref(out)))
+        self.h = out
+        self._keep = {}
+
+    def submit(self, lattice, params, n_sweeps, chain_id=0):
+        req = Request(lattice.h.value, _params_struct(params), int(n_sweeps), int(chain_id))
+        rid = C.c_uint64()
+        _check(_lib.lq_server_submit(self.h, C.byref(req), C.byref(rid)))
+        return rid.value
+
+    def poll(self, rid):
+        """The request's result dict, or None while it runs."""
+        r = Result()
+        st = _lib.lq_server_poll(self.h, C.c_uint64(rid), C.byref(r))
+        if st == 7:
+            return None
+        _check(st)
+        return dict(status=r.status, n_records=r.n_records, obs_mean=np.array(r.obs_mean[:]),
+                    obs_err=np.array(r.obs_err[:]), log_weight=r.log_weight, sign=r.sign,
+                    counts=np.array(r.counts[:]), queue_ms=r.queue_ms, total_ms=r.total_ms,
+                    sweep_ms_mean=r.sweep_ms_mean)
+
+    def stats(self):
+        s = ServerStats()
+        _check(_lib.lq_server_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.lq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
