@@ -219,6 +219,55 @@ def profiled_traffic(kind):
     return d.get(kind)
 
 
+def serving_leg(lq, inputs, prec, rate=200.0, window_s=5.0, n_sweeps=10, seed=None):
+    """Continuous batching through lq_server_*: a seeded Poisson stream of
+    Hubbard runs of differing size, admitted by device footprint while
+    earlier requests run.  The request mix is the serving workload's shape
+    scaled down so that the leg takes seconds: N in [64, 1024], N_up = N_dn
+    in [2, 16], beta in [1, 4], n_sweeps sweeps per request."""
+    rng = np.random.default_rng(inputs.SEED0 + 5 if seed is None else seed)
+    reqs = inputs.serving_mix(rng, rate, window_s, n_range=(64, 1024), ns_range=(2, 16), beta_range=(1.0, 4.0),
+                              n_sweeps=n_sweeps)
+    lats = {}
+    srv = lq.Server(hbm_budget=64 << 30, precision=prec, max_active=304, queue_capacity=len(reqs) + 16)
+    pending, results, i = {}, [], 0
+    t0 = time.perf_counter()
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i]["t"] <= now:
+            r = reqs[i]
+            if r["lattice"] not in lats:
+                lats[r["lattice"]] = getattr(lq.Lattice, r["lattice"][0])(*r["lattice"][1:])
+            params = {k: r[k] for k in ("U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
+            params.update(precision=prec, seed=inputs.SEED0)
+            pending[srv.submit(lats[r["lattice"]], params, r["n_sweeps"], chain_id=i)] = i
+            i += 1
+        for rid in list(pending):
+            res = srv.poll(rid)
+            if res is not None:
+                results.append(res)
+                del pending[rid]
+        if now > 600:
+            raise RuntimeError("serving leg did not drain")
+        time.sleep(0.005)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    tot = [r["total_ms"] for r in results]
+    que = [r["queue_ms"] for r in results]
+    return dict(requests=len(reqs), offered_rate_per_s=len(reqs) / window_s, completed=len(results),
+                failed=sum(1 for r in results if r["status"] != 0), wall_s=wall,
+                p50_sweep_ms=st["p50_sweep_ms"], p99_sweep_ms=st["p99_sweep_ms"], updates_per_s=st["updates_per_s"],
+                unit=UNIT, request_p50_ms=float(np.percentile(tot, 50)), request_p99_ms=float(np.percentile(tot, 99)),
+                queue_p50_ms=float(np.percentile(que, 50)), queue_p99_ms=float(np.percentile(que, 99)),
+                device_busy_s=st["busy_s"], host_admit_s=st["admit_s"], host_retire_s=st["retire_s"],
+                p50_tick_ms=st["p50_tick_ms"], p99_tick_ms=st["p99_tick_ms"], launches=st["ticks"],
+                mix="Poisson %.0f/s for %.0f s; square (Lx, Ly even) or flat-band chain 50/50, N in [64, 1024], "
+                    "N_up=N_dn in [2, 16], U in [-6, 6], beta in [1, 4], dtau 0.05, QR every 8, %d sweeps each"
+                    % (rate, window_s, n_sweeps),
+                precision=prec)
+
+
 def time_steps(torch, sim, steps, stream):
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     evs[0].record(stream)
@@ -240,6 +289,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--chains", type=int, default=0, help="override the chain count (small profiling cases)")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-window", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -279,15 +330,15 @@ def main():
     L = round(spec["beta"] / spec["dtau"])
     upd_per_step = n_chains * 2 * L * N
 
-    def make(prec):
+    def make(prec, sp=spec):
         ids = [rank * n_chains + c for c in range(n_chains)]
-        s = lq.Sim([lat] * n_chains, [dict(spec, precision=prec, seed=inputs.SEED0)] * n_chains, chain_ids=ids,
+        s = lq.Sim([lat] * n_chains, [dict(sp, precision=prec, seed=inputs.SEED0)] * n_chains, chain_ids=ids,
                    stream=stream.cuda_stream)
         s.init()
         return s
 
-    def run(prec):
-        sim = make(prec)
+    def run(prec, sp=spec):
+        sim = make(prec, sp)
         for _ in range(args.warmup):
             sim.sweep(1, measure=True)
         sim.sync()
@@ -298,7 +349,7 @@ def main():
         torch.cuda.synchronize()
         props = torch.cuda.get_device_properties(local)
         bus = "%08X:%02X:%02X.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
-        clk = ClockSampler(bus) if prec == 0 else None
+        clk = ClockSampler(bus) if (prec == 0 and sp is spec) else None
         per = time_steps(torch, sim, args.steps, stream)
         clocks = clk.stop() if clk else None
         total_ms = sum(per)
@@ -376,6 +427,21 @@ def main():
             mixed[key] = d
             msim.close()
 
+    # the second run of the 32x32 gas: attractive U = -4 (charge-channel fields)
+    wa = inputs.WORKLOADS[WORKLOAD + "_attractive"]
+    spa = {k: wa[k] for k in ("lattice", "U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
+    asim, aper, atotal, _, astat, aphases = run(0, spa)
+    attractive = dict(value=world * upd_per_step * args.steps / (atotal * 1e-3), unit=UNIT, U=spa["U"],
+                      sweeps_per_s=world * n_chains * args.steps / (atotal * 1e-3),
+                      p50_ms=float(np.percentile(aper, 50)), p99_ms=float(np.percentile(aper, 99)),
+                      field_accept=float(astat[1] / max(astat[0], 1)), swap_accept=float(astat[3] / max(astat[2], 1)),
+                      phase_cycle_share=aphases, precision="FP64")
+    asim.close()
+
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = serving_leg(lq, inputs, 1, window_s=args.serving_window)
+
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -388,7 +454,7 @@ def main():
                     field_accept=float(dstat[1] / max(dstat[0], 1)),
                     swap_accept=float(dstat[3] / max(dstat[2], 1)), phase_cycle_share=phases,
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
-                    reduced_precision=mixed)
+                    reduced_precision=mixed, attractive=attractive, serving=serving)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

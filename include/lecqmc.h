@@ -218,11 +218,13 @@ lq_status lq_sim_measure(lq_sim* sim, int32_t chain, int32_t n_bins, double* hos
 /* ---- serving loop (continuous batching) -----------------------------------
  * A host thread owns one non-blocking CUDA stream on `device` and runs ticks:
  * admit queued requests first come first served while their device footprint
- * fits hbm_budget and fewer than max_active run; then one sweep of every
- * active request in ONE persistent launch (requests that arrive while others
- * run join the next launch); then retire requests that finished their sweeps.
- * All requests share the server's precision.  Device memory comes from
- * cudaMalloc (the allocator hook is not used from the server thread). */
+ * fits hbm_budget and fewer than max_active run; then ONE persistent launch
+ * over every active request, each running its remaining sweeps within the
+ * launch's time budget (see lq_server_set_tick_target); requests that arrive
+ * while others run join the next launch; then retire requests that finished
+ * their sweeps.  All requests share the server's precision.  Request arenas
+ * come from a stream-ordered memory pool owned by the server, so admission
+ * and retirement never synchronize the device. */
 typedef struct lq_server lq_server;
 typedef struct {
   const lq_lattice* lattice; /* copied at submit; the caller may destroy it */
@@ -243,10 +245,12 @@ typedef struct {
   double sweep_ms_mean;      /* mean per-sweep latency this request saw */
 } lq_result;
 typedef struct {
-  double p50_sweep_ms, p99_sweep_ms; /* per-sweep latency over all active requests and ticks */
+  double p50_sweep_ms, p99_sweep_ms; /* per-sweep latency: one sample per sweep run, the chain's own sweep time */
+  double p50_tick_ms, p99_tick_ms;   /* duration of the batched launches */
   double updates_per_s;              /* field-update attempts per second of device busy time */
-  double busy_s, wall_s;
-  int64_t submitted, admitted, completed, rejected, active, queued;
+  double busy_s, wall_s;             /* device time of the batched launches; wall time since creation */
+  double admit_s, retire_s;          /* host time spent admitting and retiring requests */
+  int64_t submitted, admitted, completed, rejected, active, queued, ticks;
   size_t hbm_in_use;
 } lq_server_info;
 /* Errors: LQ_EINVAL for a bad budget, slot count, queue capacity or precision. */
@@ -258,6 +262,12 @@ lq_status lq_server_submit(lq_server* srv, const lq_request* request, uint64_t* 
 /* LQ_ENOTFOUND until the request is done; then fills *out once and forgets it. */
 lq_status lq_server_poll(lq_server* srv, uint64_t id, lq_result* out);
 lq_status lq_server_stats(lq_server* srv, lq_server_info* out);
+/* Lower bound (ms) of the time budget of one batched launch (default 20).
+ * Within a launch each request runs its remaining sweeps while they fit in
+ * the budget, at least one; the budget is the longest expected single sweep
+ * among the active requests and at least this target.  Larger targets mean
+ * fewer launches and longer waits for newly admitted requests. */
+lq_status lq_server_set_tick_target(lq_server* srv, double ms);
 /* Finishes every admitted request, drops the queued ones, joins the thread. */
 lq_status lq_server_destroy(lq_server* srv);
 

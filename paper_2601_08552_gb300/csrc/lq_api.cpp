@@ -279,8 +279,23 @@ static size_t footprint_one(int N, int nb, int G, int L, int tw, const int ns[2]
   return b + al256(sizeof(LqChainDev)) + 4 * al256(sizeof(int) * 1026);
 }
 
+static lq_status create_impl(const lq_lattice* const* lats, const lq_params* params, int32_t n_chains,
+                             const uint32_t* chain_ids, void* stream, const lq_allocator* alloc, bool build,
+                             lq_sim** out);
+
 extern "C" lq_status lq_sim_create(const lq_lattice* const* lats, const lq_params* params, int32_t n_chains,
                                    const uint32_t* chain_ids, void* stream, const lq_allocator* alloc, lq_sim** out) {
+  return create_impl(lats, params, n_chains, chain_ids, stream, alloc, true, out);
+}
+
+lq_status lq_internal_sim_create_unbuilt(const lq_lattice* lat, const lq_params* params, uint32_t chain_id,
+                                         void* stream, const lq_allocator* alloc, lq_sim** out) {
+  return create_impl(&lat, params, 1, &chain_id, stream, alloc, false, out);
+}
+
+static lq_status create_impl(const lq_lattice* const* lats, const lq_params* params, int32_t n_chains,
+                             const uint32_t* chain_ids, void* stream, const lq_allocator* alloc, bool build,
+                             lq_sim** out) {
   if (!out || !lats || !params || n_chains < 1) return fail(LQ_EINVAL, "bad arguments to lq_sim_create");
   const int prec = params[0].precision;
   if (prec != LQ_FP64 && prec != LQ_MIXED && prec != LQ_MIXED_DW)
@@ -488,10 +503,14 @@ extern "C" lq_status lq_sim_create(const lq_lattice* const* lats, const lq_param
   int per_sm = lq::max_active_sweep_ctas(prec, smem);
   if (per_sm < 1) { lq_sim_destroy(S); return fail(LQ_EUNSUPPORTED, "shared-memory plan does not fit one CTA per SM"); }
   S->grid = std::min(n_chains, sms * per_sm);
-  S->mirror_fresh = false;
-  // build the chains for the default state
-  e = lq::launch_build(prec, S->d_chains, S->d_all, n_chains, S->M, S->Nmax, S->buf_bytes, S->grid, S->st);
-  if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "initial chain build"); }
+  if (build) {
+    // build the chains for the default state
+    S->mirror_fresh = false;
+    e = lq::launch_build(prec, S->d_chains, S->d_all, n_chains, S->M, S->Nmax, S->buf_bytes, S->grid, S->st);
+    if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "initial chain build"); }
+  } else {
+    S->mirror_fresh = true;  // the host descriptors were just uploaded
+  }
   *out = S;
   return LQ_OK;
 }
@@ -799,10 +818,13 @@ lq_sim_launch_info lq_internal_sim_info(const lq_sim* S) {
   lq_sim_launch_info i;
   i.d_chains = S->d_chains; i.n_chains = S->n_chains; i.prec = S->prec; i.M = S->M; i.Nmax = S->Nmax;
   i.buf_bytes = S->buf_bytes; i.arena_bytes = S->arena_bytes;
+  i.cost = S->n_chains > 0 ? S->info[0].cost : 0.0;
   return i;
 }
 
 void lq_internal_sim_invalidate(lq_sim* S) { S->mirror_fresh = false; }
+
+const LqChainDev* lq_internal_sim_host_desc(const lq_sim* S) { return S->h.data(); }
 
 size_t lq_internal_footprint(const lq_lattice* L, const lq_params* p) {
   const long Ll = std::lround(p->beta / p->dtau);

@@ -107,6 +107,13 @@ __device__ inline Smem carve(const SmemPlan& p, char* base) {
 #define TID ((int)threadIdx.x)
 #define FULL 0xffffffffu
 
+// Device global timer in nanoseconds.
+__device__ __forceinline__ long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
+
 // Per-phase cycle counters of a chain (thread 0, clock64), for profiling.
 enum { PH_FLIP = 0, PH_PROP = 1, PH_QR = 2, PH_BLOCKINV = 3, PH_SWAP = 4, PH_MEAS = 5 };
 // Only the outermost timer of a nest records, so the phases add up.
@@ -1485,11 +1492,12 @@ __device__ void pick_flip_warps(int* sm_ctr, Smem& sm) {
 
 template <class R>
 __global__ void __launch_bounds__(LQ_THREADS, 2)
-    sweep_kernel(LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps, int do_measure, SmemPlan plan) {
+    sweep_kernel(LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps, const int* caps,
+                 long long budget_ns, int do_measure, SmemPlan plan) {
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm = carve(plan, smem_raw);
   pick_flip_warps(queue + 1, sm);
-  __shared__ int next;
+  __shared__ int next, stop;
   for (;;) {
     if (TID == 0) next = atomicAdd(queue, 1);
     __syncthreads();
@@ -1499,12 +1507,26 @@ __global__ void __launch_bounds__(LQ_THREADS, 2)
     LqChainDev* g = chains + order[q];
     load_chain(g, sm);
     LqChainDev& C = *sm.C;
-    for (int t = 0; t < n_sweeps; ++t) {
+    // a chain runs caps[q] sweeps (n_sweeps without caps); with a budget it
+    // starts no further sweep that, judged by the one just done, would end
+    // more than budget_ns after the chain was taken
+    const int cap = caps ? caps[q] : n_sweeps;
+    const long long t_take = global_ns();
+    long long t_prev = t_take;
+    for (int t = 0; t < cap; ++t) {
       up_pass<R>(C, sm);
       swap_phase<R>(C, sm);
       down_pass<R>(C, do_measure, sm);
-      if (TID == 0) C.sweep++;
+      if (TID == 0) {
+        const long long t_now = global_ns();
+        C.sweep++;
+        C.sweep_ns_last = t_now - t_prev;
+        C.sweep_ns_sum += t_now - t_prev;
+        t_prev = t_now;
+        stop = budget_ns > 0 && (t_now - t_take) + C.sweep_ns_last > budget_ns;
+      }
       __syncthreads();
+      if (stop) break;
     }
     store_chain(g, sm);
   }
@@ -1649,16 +1671,17 @@ template <class R> static cudaError_t set_attr(const void* fn, size_t smem) {
 }
 
 cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
-                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st) {
+                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st, const int* caps,
+                         long long budget_ns) {
   SmemPlan p = plan_smem(M, Nmax, buf_bytes);
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int) * (1 + 1024), st);
   if (e != cudaSuccess) return e;
   if (prec == 0) {
     if ((e = set_attr<double>((const void*)sweep_kernel<double>, p.total)) != cudaSuccess) return e;
-    sweep_kernel<double><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, do_measure, p);
+    sweep_kernel<double><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
   } else {
     if ((e = set_attr<float>((const void*)sweep_kernel<float>, p.total)) != cudaSuccess) return e;
-    sweep_kernel<float><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, do_measure, p);
+    sweep_kernel<float><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
   }
   return cudaGetLastError();
 }

@@ -8,7 +8,8 @@
 namespace lq {
 size_t smem_bytes(int M, int Nmax, int buf_bytes);
 cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
-                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st);
+                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st,
+                         const int* caps = nullptr, long long budget_ns = 0);
 cudaError_t launch_build(int prec, LqChainDev* chains, const int* order, int n_order, int M, int Nmax, int buf_bytes,
                          int grid, cudaStream_t st);
 cudaError_t launch_clear_records(LqChainDev* chains, int n, cudaStream_t st);

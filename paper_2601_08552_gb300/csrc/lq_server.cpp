@@ -1,15 +1,21 @@
 // lq_server.cpp -- continuous-batching serving loop for simulation requests.
 //
-// A host thread owns one CUDA stream and a table of active requests, each a
-// one-chain simulation with its own device arena.  Every tick it (1) admits
-// queued requests while their device footprint fits the HBM budget and a
-// slot is free, (2) runs ONE sweep of every active request in a single
-// persistent launch over a gathered descriptor array, so requests that
-// arrive while others run join the next launch and their work overlaps on
-// the device, and (3) retires requests that have done their sweeps: their
-// records become a result (sign-weighted means and jackknife errors) and
-// their memory returns to the budget.  The tick time, taken with CUDA events
-// on the server stream, is the per-sweep latency every active request saw.
+// A host thread owns one CUDA stream, a stream-ordered memory pool and a
+// table of active requests, each a one-chain simulation with its own device
+// arena.  Every tick it (1) admits queued requests while their device
+// footprint fits the HBM budget and a slot is free, (2) runs every active
+// request in a single persistent launch over a gathered descriptor array, so
+// requests that arrive while others run join the next launch and their work
+// overlaps on the device, and (3) retires requests that have done their
+// sweeps: their records become a result (sign-weighted means and jackknife
+// errors) and their memory returns to the budget.
+//
+// Within a tick each chain runs as many of its remaining sweeps as fit in the
+// tick's time budget (at least one), so small requests are not held to one
+// sweep while a large one finishes its sweep.  The budget is the longest
+// expected single sweep among the active requests (measured on the device by
+// the kernel, or estimated from a cost model for new ones), and at least the
+// tick target.  Per-sweep latency samples are the chains' own sweep times.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,10 +52,13 @@ struct Active {
   uint64_t id;
   lq_lattice* lat;
   lq_sim* sim;
+  LqChainDev desc;  // authoritative copy of the chain descriptor between ticks
   int32_t n_sweeps, done;
   size_t footprint;
   double t_submit, t_admit;
   long long updates_per_sweep;
+  double cost;          // cost-model units per sweep
+  long long last_ns;    // measured duration of its latest sweep (0 until one ran)
   double sweep_ms_sum;
 };
 
@@ -64,6 +73,8 @@ struct lq_server {
   int device = 0, prec = 0, max_active = 0, queue_cap = 0;
   size_t budget = 0, in_use = 0;
   cudaStream_t st = nullptr;
+  cudaMemPool_t pool = nullptr;
+  lq_allocator alloc;
   std::mutex mu;
   std::condition_variable cv;
   bool stop = false;
@@ -73,33 +84,74 @@ struct lq_server {
   std::vector<Active> active;
   std::map<uint64_t, lq_result> done;
   std::map<uint64_t, int> state;  // 0 queued, 1 active, 2 done
-  // device descriptor table and order list for the gathered launch
+  // device descriptor table, order list and per-chain sweep caps of the gathered launch
   LqChainDev* d_slots = nullptr;
   int* d_order = nullptr;
+  int* d_caps = nullptr;
   int* d_queue = nullptr;
+  int dev_sms = 1;
+  double tick_target_ms = 20.0;
+  double ns_per_cost = 0.0;  // running estimate of sweep nanoseconds per cost unit
   // statistics
-  std::vector<double> tick_ms;  // per-sweep latency samples (one per active request per tick)
+  std::vector<double> sweep_ms;  // one sample per sweep: that chain's sweep time in its tick
+  std::vector<double> tick_ms;   // one sample per launch
   long long submitted = 0, admitted = 0, completed = 0, rejected = 0;
-  double updates_done = 0.0, busy_s = 0.0, t_start = 0.0;
+  double updates_done = 0.0, busy_s = 0.0, t_start = 0.0, admit_s = 0.0, retire_s = 0.0;
   std::string last_err;
 };
 
 static lq_status srv_fail(lq_status s, const std::string& msg) { return lq_internal_fail(s, msg); }
 
-static void retire(lq_server* S, Active& a) {
+// Stream-ordered device memory for the request arenas: allocation and release
+// on the server stream never synchronize the device.
+static void* srv_alloc(void* ctx, size_t bytes, void* stream) {
+  lq_server* S = (lq_server*)ctx;
+  void* p = nullptr;
+  if (cudaMallocFromPoolAsync(&p, bytes, S->pool, (cudaStream_t)stream) != cudaSuccess) return nullptr;
+  return p;
+}
+static void srv_free(void*, void* ptr, size_t, void* stream) { cudaFreeAsync(ptr, (cudaStream_t)stream); }
+
+static void finish_failed(lq_server* S, uint64_t id, size_t footprint, lq_status st) {
   lq_result r;
   std::memset(&r, 0, sizeof(r));
-  r.status = LQ_OK;
+  r.status = st;
+  std::lock_guard<std::mutex> g(S->mu);
+  S->in_use -= footprint;
+  S->done[id] = r;
+  S->state[id] = 2;
+  S->completed++;
+}
+
+static void retire_impl(lq_server* S, Active& a);
+
+static void retire(lq_server* S, Active& a) {
+  const double t0 = now_s();
+  retire_impl(S, a);
+  std::lock_guard<std::mutex> g(S->mu);
+  S->retire_s += now_s() - t0;
+}
+
+static void retire_impl(lq_server* S, Active& a) {
+  lq_result r;
+  std::memset(&r, 0, sizeof(r));
+  // hand the descriptor back to the simulation object, then read it out
+  const lq_sim_launch_info inf = lq_internal_sim_info(a.sim);
+  lq_status st = LQ_OK;
+  if (cudaMemcpyAsync(inf.d_chains, &a.desc, sizeof(LqChainDev), cudaMemcpyHostToDevice, S->st) != cudaSuccess ||
+      cudaStreamSynchronize(S->st) != cudaSuccess)
+    st = LQ_ECUDA;
+  lq_internal_sim_invalidate(a.sim);
+  if (st == LQ_OK) st = lq_sim_sync(a.sim);  // device errors of the chain (bad input, numerics)
   std::vector<double> rec((size_t)std::max(a.n_sweeps, 1) * LQ_NOBS);
   int32_t nrec = 0;
-  lq_status st = lq_sim_records(a.sim, 0, a.n_sweeps, &nrec, rec.data());
+  if (st == LQ_OK && a.n_sweeps > 0) st = lq_sim_records(a.sim, 0, a.n_sweeps, &nrec, rec.data());
   if (st == LQ_OK) {
     r.n_records = std::min(nrec, a.n_sweeps);
     lq_internal_obs_stats(rec.data(), r.n_records, std::min(r.n_records, 16), r.obs_mean, r.obs_err);
     st = lq_sim_tracked_weight(a.sim, 0, &r.log_weight, &r.sign);
   }
   if (st == LQ_OK) st = lq_sim_stats(a.sim, 0, r.counts);
-  if (st == LQ_OK) st = lq_sim_sync(a.sim);
   r.status = st;
   r.queue_ms = 1e3 * (a.t_admit - a.t_submit);
   r.total_ms = 1e3 * (now_s() - a.t_submit);
@@ -114,71 +166,119 @@ static void retire(lq_server* S, Active& a) {
 }
 
 // Admit queued requests (first come, first served; a request that does not
-// fit waits, and later ones wait behind it).
+// fit waits, and later ones wait behind it).  The new requests' fields and
+// Fock states are drawn and their QR chains built in one gathered launch each.
 static void admit(lq_server* S) {
-  for (;;) {
-    Pending p;
-    {
-      std::lock_guard<std::mutex> g(S->mu);
-      if (S->queue.empty() || (int)S->active.size() >= S->max_active) return;
-      if (S->in_use + S->queue.front().footprint > S->budget) return;
-      p = S->queue.front();
+  std::vector<Pending> take;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    size_t in_use = S->in_use;
+    while (!S->queue.empty() && (int)(S->active.size() + take.size()) < S->max_active &&
+           in_use + S->queue.front().footprint <= S->budget) {
+      take.push_back(S->queue.front());
+      in_use += S->queue.front().footprint;
       S->queue.pop_front();
-      S->in_use += p.footprint;
     }
+    S->in_use = in_use;
+  }
+  if (take.empty()) return;
+  std::vector<Active> fresh;
+  int M = 1, Nmax = 1, buf = 0;
+  for (const Pending& p : take) {
     lq_sim* sim = nullptr;
-    const lq_lattice* lp = p.lat;
-    lq_status st = lq_sim_create(&lp, &p.params, 1, &p.chain_id, S->st, nullptr, &sim);
-    if (st == LQ_OK) st = lq_sim_init(sim);
+    lq_status st = lq_internal_sim_create_unbuilt(p.lat, &p.params, p.chain_id, S->st, &S->alloc, &sim);
     if (st != LQ_OK) {
-      lq_result r;
-      std::memset(&r, 0, sizeof(r));
-      r.status = st;
-      if (sim) lq_sim_destroy(sim);
       lq_lattice_destroy(p.lat);
-      std::lock_guard<std::mutex> g(S->mu);
-      S->in_use -= p.footprint;
-      S->done[p.id] = r;
-      S->state[p.id] = 2;
-      S->completed++;
+      finish_failed(S, p.id, p.footprint, st);
       continue;
     }
+    const lq_sim_launch_info inf = lq_internal_sim_info(sim);
     Active a;
+    a.desc = *lq_internal_sim_host_desc(sim);
+    a.cost = inf.cost;
     a.id = p.id; a.lat = p.lat; a.sim = sim; a.n_sweeps = p.n_sweeps; a.done = 0; a.footprint = p.footprint;
-    a.t_submit = p.t_submit; a.t_admit = now_s();
+    a.t_submit = p.t_submit;
     a.updates_per_sweep = 2LL * (long long)std::lround(p.params.beta / p.params.dtau) * lq_lattice_get_view(p.lat).N;
+    a.last_ns = 0;
     a.sweep_ms_sum = 0.0;
+    fresh.push_back(a);
+    M = std::max(M, inf.M);
+    Nmax = std::max(Nmax, inf.Nmax);
+    buf = std::max(buf, inf.buf_bytes);
+  }
+  const int n = (int)fresh.size();
+  if (n == 0) return;
+  std::vector<LqChainDev> desc(n);
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) {
+    desc[k] = fresh[k].desc;
+    order[k] = k;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return fresh[x].cost > fresh[y].cost; });
+  const size_t smem = lq::smem_bytes(M, Nmax, buf);
+  const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, smem));
+  cudaError_t e = cudaMemcpyAsync(S->d_slots, desc.data(), sizeof(LqChainDev) * n, cudaMemcpyHostToDevice, S->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->st);
+  if (e == cudaSuccess) e = lq::launch_init(S->d_slots, S->d_order, n, std::min(n, 1024), S->st);
+  if (e == cudaSuccess)
+    e = lq::launch_build(S->prec, S->d_slots, S->d_order, n, M, Nmax, buf, std::min(n, S->dev_sms * per_sm), S->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(desc.data(), S->d_slots, sizeof(LqChainDev) * n, cudaMemcpyDeviceToHost, S->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+  const double t_admit = now_s();
+  for (int k = 0; k < n; ++k) {
+    Active& a = fresh[k];
+    a.t_admit = t_admit;
+    if (e == cudaSuccess) a.desc = desc[k];
+    a.desc.sweep_ns_sum = 0;
+    {
+      std::lock_guard<std::mutex> g(S->mu);
+      S->state[a.id] = 1;
+      S->admitted++;
+    }
+    if (e != cudaSuccess || a.desc.err) {
+      a.n_sweeps = 0;  // the build failed: report it through the simulation's own error path
+      retire(S, a);
+      continue;
+    }
     std::lock_guard<std::mutex> g(S->mu);
     S->active.push_back(a);
-    S->state[a.id] = 1;
-    S->admitted++;
   }
 }
 
-// One sweep of every active request in one launch.
+// One launch over every active request: each runs its remaining sweeps up to
+// the tick's time budget (at least one).
 static void tick(lq_server* S) {
   const int n = (int)S->active.size();
   if (n == 0) return;
   int M = 1, Nmax = 1, buf = 0;
   std::vector<LqChainDev> desc(n);
-  std::vector<int> order(n);
+  std::vector<int> order(n), caps(n);
+  std::vector<double> est(n);
+  double target_ms;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    target_ms = S->tick_target_ms;
+  }
+  long long budget_ns = std::max(1LL, (long long)(target_ms * 1e6));  // 0 would mean no budget in the kernel
   for (int k = 0; k < n; ++k) {
-    const lq_sim_launch_info inf = lq_internal_sim_info(S->active[k].sim);
-    cudaMemcpyAsync(&desc[k], inf.d_chains, sizeof(LqChainDev), cudaMemcpyDeviceToHost, S->st);
+    const Active& a = S->active[k];
+    const lq_sim_launch_info inf = lq_internal_sim_info(a.sim);
+    desc[k] = a.desc;
     M = std::max(M, inf.M);
     Nmax = std::max(Nmax, inf.Nmax);
     buf = std::max(buf, inf.buf_bytes);
+    est[k] = a.last_ns > 0 ? (double)a.last_ns : S->ns_per_cost * a.cost;
+    budget_ns = std::max(budget_ns, (long long)est[k]);
     order[k] = k;
   }
-  cudaStreamSynchronize(S->st);
-  // longest first
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return (double)desc[a].L * desc[a].N > (double)desc[b].L * desc[b].N;
+  // longest first, so the persistent CTAs take the long chains before the short ones
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return est[x] != est[y] ? est[x] > est[y] : S->active[x].cost > S->active[y].cost;
   });
+  for (int q = 0; q < n; ++q) caps[q] = S->active[order[q]].n_sweeps - S->active[order[q]].done;
   cudaMemcpyAsync(S->d_slots, desc.data(), sizeof(LqChainDev) * n, cudaMemcpyHostToDevice, S->st);
   cudaMemcpyAsync(S->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->st);
-  int dev_sms = 1;
-  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, S->device);
+  cudaMemcpyAsync(S->d_caps, caps.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->st);
   const size_t smem = lq::smem_bytes(M, Nmax, buf);
   const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, smem));
   cudaEvent_t e0, e1;
@@ -186,34 +286,45 @@ static void tick(lq_server* S) {
   cudaEventCreate(&e1);
   cudaEventRecord(e0, S->st);
   cudaError_t e = lq::launch_sweep(S->prec, S->d_slots, S->d_order, n, S->d_queue, 1, 1, M, Nmax, buf,
-                                   std::min(n, dev_sms * per_sm), S->st);
+                                   std::min(n, S->dev_sms * per_sm), S->st, S->d_caps, budget_ns);
   cudaEventRecord(e1, S->st);
   cudaMemcpyAsync(desc.data(), S->d_slots, sizeof(LqChainDev) * n, cudaMemcpyDeviceToHost, S->st);
-  cudaStreamSynchronize(S->st);
+  cudaError_t e2 = cudaStreamSynchronize(S->st);
+  if (e == cudaSuccess) e = e2;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  std::vector<double> samples;
+  double upd = 0.0, ratio_sum = 0.0;
+  int ratio_n = 0;
   for (int k = 0; k < n; ++k) {
-    const lq_sim_launch_info inf = lq_internal_sim_info(S->active[k].sim);
-    cudaMemcpyAsync(inf.d_chains, &desc[k], sizeof(LqChainDev), cudaMemcpyHostToDevice, S->st);
-    lq_internal_sim_invalidate(S->active[k].sim);
+    Active& a = S->active[k];
+    const int d = (int)(desc[k].sweep - a.desc.sweep);
+    if (d > 0) {
+      const double per_ms = 1e-6 * (double)desc[k].sweep_ns_sum / d;
+      for (int t = 0; t < d; ++t) samples.push_back(per_ms);
+      a.sweep_ms_sum += per_ms * d;
+      a.last_ns = desc[k].sweep_ns_last;
+      if (a.cost > 0) { ratio_sum += (double)desc[k].sweep_ns_last / a.cost; ++ratio_n; }
+      upd += (double)d * (double)a.updates_per_sweep;
+      a.done += d;
+    }
+    a.desc = desc[k];
+    a.desc.sweep_ns_sum = 0;
   }
-  cudaStreamSynchronize(S->st);
+  if (ratio_n) S->ns_per_cost = ratio_sum / ratio_n;
   {
     std::lock_guard<std::mutex> g(S->mu);
     S->busy_s += ms * 1e-3;
-    for (int k = 0; k < n; ++k) {
-      S->tick_ms.push_back(ms);
-      S->updates_done += (double)S->active[k].updates_per_sweep;
-    }
+    S->tick_ms.push_back(ms);
+    S->sweep_ms.insert(S->sweep_ms.end(), samples.begin(), samples.end());
+    S->updates_done += upd;
     if (e != cudaSuccess) S->last_err = cudaGetErrorString(e);
   }
   std::vector<Active> keep;
   for (Active& a : S->active) {
-    a.done++;
-    a.sweep_ms_sum += ms;
-    if (a.done >= a.n_sweeps) retire(S, a);
+    if (e != cudaSuccess || a.done >= a.n_sweeps) retire(S, a);
     else keep.push_back(a);
   }
   std::lock_guard<std::mutex> g(S->mu);
@@ -240,8 +351,12 @@ static void run_loop(lq_server* S) {
         S->queue.clear();
       }
     }
+    const double t0 = now_s();
     admit(S);
+    const double t1 = now_s();
     tick(S);
+    std::lock_guard<std::mutex> g(S->mu);
+    S->admit_s += t1 - t0;
   }
 }
 
@@ -257,7 +372,22 @@ extern "C" lq_status lq_server_create(int32_t device, size_t hbm_budget, int32_t
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_slots, sizeof(LqChainDev) * max_active);
   if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_order, sizeof(int) * max_active);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_caps, sizeof(int) * max_active);
   if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_queue, sizeof(int) * (1 + 1024));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->dev_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&S->pool, &props);
+    uint64_t keep_all = UINT64_MAX;  // keep released memory in the pool for the next request
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep_all);
+  }
+  S->alloc.ctx = S;
+  S->alloc.alloc = srv_alloc;
+  S->alloc.free = srv_free;
   if (e != cudaSuccess) {
     lq_server_destroy(S);
     return srv_fail(LQ_ECUDA, std::string("server set-up: ") + cudaGetErrorString(e));
@@ -322,12 +452,19 @@ extern "C" lq_status lq_server_stats(lq_server* S, lq_server_info* out) {
   if (!S || !out) return srv_fail(LQ_EINVAL, "bad arguments");
   std::lock_guard<std::mutex> g(S->mu);
   std::memset(out, 0, sizeof(*out));
-  std::vector<double> t = S->tick_ms;
+  std::vector<double> t = S->sweep_ms;
   if (!t.empty()) {
     std::sort(t.begin(), t.end());
     out->p50_sweep_ms = t[(size_t)(0.50 * (t.size() - 1))];
     out->p99_sweep_ms = t[(size_t)(0.99 * (t.size() - 1))];
   }
+  t = S->tick_ms;
+  if (!t.empty()) {
+    std::sort(t.begin(), t.end());
+    out->p50_tick_ms = t[(size_t)(0.50 * (t.size() - 1))];
+    out->p99_tick_ms = t[(size_t)(0.99 * (t.size() - 1))];
+  }
+  out->ticks = (int64_t)S->tick_ms.size();
   out->submitted = S->submitted;
   out->admitted = S->admitted;
   out->completed = S->completed;
@@ -337,7 +474,16 @@ extern "C" lq_status lq_server_stats(lq_server* S, lq_server_info* out) {
   out->busy_s = S->busy_s;
   out->wall_s = now_s() - S->t_start;
   out->updates_per_s = S->busy_s > 0 ? S->updates_done / S->busy_s : 0.0;
+  out->admit_s = S->admit_s;
+  out->retire_s = S->retire_s;
   out->hbm_in_use = S->in_use;
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_server_set_tick_target(lq_server* S, double ms) {
+  if (!S || !(ms >= 0.0) || !std::isfinite(ms)) return srv_fail(LQ_EINVAL, "tick target must be a finite number >= 0");
+  std::lock_guard<std::mutex> g(S->mu);
+  S->tick_target_ms = ms;
   return LQ_OK;
 }
 
@@ -354,7 +500,9 @@ extern "C" lq_status lq_server_destroy(lq_server* S) {
   if (S->st) cudaStreamSynchronize(S->st);
   cudaFree(S->d_slots);
   cudaFree(S->d_order);
+  cudaFree(S->d_caps);
   cudaFree(S->d_queue);
+  if (S->pool) cudaMemPoolDestroy(S->pool);
   if (S->st) cudaStreamDestroy(S->st);
   delete S;
   return LQ_OK;

@@ -45,3 +45,30 @@ def flatband_batch(rng, n_chains, periodic_frac=0.5):
         out.append(dict(lattice=("flatband", nc, 1.0, 1.0, 1.0, 1.0, bool(rng.random() < periodic_frac)), U=2.0,
                         beta=beta, dtau=0.05, n_up=ns, n_dn=ns, n_stab=8))
     return out
+
+
+def serving_mix(rng, rate_per_s, window_s, n_range=(256, 16384), ns_range=(4, 64), beta_range=(2.0, 20.0),
+                n_sweeps=100, dtau=0.05, n_stab=8):
+    """Poisson request stream of Hubbard runs: arrival times (s) with mean rate
+    rate_per_s over window_s, each a square lattice (Lx, Ly even, N = Lx*Ly in
+    n_range) or a flat-band chain (2 sites per cell) with equal probability,
+    N_up = N_dn uniform in ns_range (at most N/4), U uniform in [-6, 6], beta
+    uniform in beta_range rounded to a whole number of QR blocks."""
+    out, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate_per_s))
+        if t >= window_s:
+            return out
+        n_target = int(rng.integers(n_range[0], n_range[1] + 1))
+        if rng.random() < 0.5:
+            lx = max(2, 2 * int(round(np.sqrt(n_target) / 2)))
+            ly = max(2, 2 * int(round(n_target / lx / 2)))
+            lattice, N = ("square", lx, ly), lx * ly
+        else:
+            nc = max(2, n_target // 2)
+            lattice, N = ("flatband", nc, 1.0, 1.0, 1.0, 1.0, True), 2 * nc
+        ns = int(rng.integers(ns_range[0], ns_range[1] + 1))
+        ns = max(1, min(ns, N // 4))
+        blocks = max(1, int(round(rng.uniform(*beta_range) / (dtau * n_stab))))
+        out.append(dict(t=t, lattice=lattice, U=float(rng.uniform(-6.0, 6.0)), beta=blocks * n_stab * dtau,
+                        dtau=dtau, n_up=ns, n_dn=ns, n_stab=n_stab, n_sweeps=n_sweeps))

@@ -30,7 +30,8 @@ EXPORTS = [
     "lq_sim_tracked_weight", "lq_sim_field_ratio", "lq_sim_swap_ratio", "lq_sim_records",
     "lq_sim_clear_records", "lq_sim_stats", "lq_sim_profile", "lq_sim_chain_panel", "lq_sim_chain_info",
     "lq_sim_device_bytes", "lq_sim_destroy", "lq_sim_measure", "lq_server_create", "lq_server_submit",
-    "lq_server_poll", "lq_server_stats", "lq_server_destroy", "lq_sweep_noalloc", "lq_last_error", "lq_version",
+    "lq_server_poll", "lq_server_stats", "lq_server_set_tick_target", "lq_server_destroy", "lq_sweep_noalloc",
+    "lq_last_error", "lq_version",
 ]
 
 
@@ -61,9 +62,10 @@ class Result(C.Structure):
 
 
 class ServerStats(C.Structure):
-    _fields_ = [("p50_sweep_ms", C.c_double), ("p99_sweep_ms", C.c_double), ("updates_per_s", C.c_double),
-                ("busy_s", C.c_double), ("wall_s", C.c_double), ("submitted", C.c_int64), ("admitted", C.c_int64),
-                ("completed", C.c_int64), ("rejected", C.c_int64), ("active", C.c_int64), ("queued", C.c_int64),
+    _fields_ = [("p50_sweep_ms", C.c_double), ("p99_sweep_ms", C.c_double), ("p50_tick_ms", C.c_double),
+                ("p99_tick_ms", C.c_double), ("updates_per_s", C.c_double), ("busy_s", C.c_double),
+                ("wall_s", C.c_double), ("admit_s", C.c_double), ("retire_s", C.c_double), ("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("active", C.c_int64), ("queued", C.c_int64), ("ticks", C.c_int64),
                 ("hbm_in_use", C.c_size_t)]
 
 
@@ -128,6 +130,7 @@ def load(build_if_missing=True):
         "lq_server_submit": [P, C.POINTER(Request), C.POINTER(C.c_uint64)],
         "lq_server_poll": [P, C.c_uint64, C.POINTER(Result)],
         "lq_server_stats": [P, C.POINTER(ServerStats)],
+        "lq_server_set_tick_target": [P, dbl],
         "lq_server_destroy": [P],
     }
     for name, args in sig.items():
@@ -452,6 +455,9 @@ class Server:
                     obs_err=np.array(r.obs_err[:]), log_weight=r.log_weight, sign=r.sign,
                     counts=np.array(r.counts[:]), queue_ms=r.queue_ms, total_ms=r.total_ms,
                     sweep_ms_mean=r.sweep_ms_mean)
+
+    def set_tick_target(self, ms):
+        _check(_lib.lq_server_set_tick_target(self.h, float(ms)))
 
     def stats(self):
         s = ServerStats()

@@ -107,3 +107,27 @@ def test_queue_full_and_unknown_ids(lq):
         tiny = lq.Server(hbm_budget=1 << 20)
         tiny.submit(lat, params, 1)
     srv.close()  # finishes the admitted request, drops the queued ones
+
+
+def test_grouping_of_sweeps_into_launches_does_not_change_results(lq):
+    """Tick target 0 (one sweep per launch for a lone request) against 10 s
+    (every sweep in one launch): the counter-based random numbers depend on
+    (chain, sweep, slice, site) only, so the results agree."""
+    lat = lq.Lattice.flatband(10)
+    params = dict(U=2.0, beta=1.2, dtau=0.05, n_up=4, n_dn=4, n_stab=8, seed=8, precision=0)
+    out = []
+    for target in (0.0, 10000.0):
+        srv = lq.Server(hbm_budget=1 << 30)
+        srv.set_tick_target(target)
+        rid = srv.submit(lat, params, 12, chain_id=3)
+        out.append((wait(srv, [rid])[rid], srv.stats()))
+        srv.close()
+    (ra, sa), (rb, sb) = out
+    assert sa["ticks"] == 12 and sb["ticks"] == 1
+    assert np.array_equal(ra["counts"], rb["counts"])
+    assert np.max(np.abs(ra["obs_mean"] - rb["obs_mean"])) < 1e-10
+    assert abs(ra["log_weight"] - rb["log_weight"]) < 1e-10 * max(1.0, abs(ra["log_weight"]))
+    srv = lq.Server(hbm_budget=1 << 30)
+    with pytest.raises(lq.LqError):
+        srv.set_tick_target(-1.0)
+    srv.close()
