@@ -291,13 +291,15 @@ def main():
     ap.add_argument("--chains", type=int, default=0, help="override the chain count (small profiling cases)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-window", type=float, default=10.0)
+    ap.add_argument("--workload", default=WORKLOAD, choices=["gas32x32", "gas64x64"],
+                    help="gas64x64: the 64x64 mixed-precision comparison (512 chains, ~10 s per sweep)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
 
     from paper_2601_08552_gb300 import inputs
 
-    w = inputs.WORKLOADS[WORKLOAD]
+    w = inputs.WORKLOADS[args.workload]
     spec = {k: w[k] for k in ("lattice", "U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
     n_chains = args.chains or w["chains"]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -339,6 +341,9 @@ def main():
 
     def run(prec, sp=spec):
         sim = make(prec, sp)
+        # log-weights of the first chains on their seeded initial fields (identical across precisions)
+        lw0 = np.array([sim.log_weight(c)[0] for c in range(min(8, n_chains))])
+        run.lw0[prec] = lw0
         for _ in range(args.warmup):
             sim.sweep(1, measure=True)
         sim.sync()
@@ -366,6 +371,7 @@ def main():
                   enumerate(["flips", "propagation", "qr", "block_inverse", "swaps", "measure"])}
         return sim, per, total_ms, clocks, d, phases
 
+    run.lw0 = {}
     sim, per, total_ms, clocks, dstat, phases = run(0)
     value = world * upd_per_step * args.steps / (total_ms * 1e-3)
     sweeps = world * n_chains * args.steps / (total_ms * 1e-3)
@@ -424,22 +430,26 @@ def main():
                      p50_ms=float(np.percentile(mper, 50)), p99_ms=float(np.percentile(mper, 99)),
                      field_accept=float(mstat[1] / max(mstat[0], 1)), phase_cycle_share=mphases, precision=desc)
             d["speedup_vs_fp64"] = d["value"] / value
+            d["logw_max_rel_err_vs_fp64"] = float(np.max(np.abs(run.lw0[prec] - run.lw0[0]) /
+                                                         np.maximum(1.0, np.abs(run.lw0[0]))))
             mixed[key] = d
             msim.close()
 
     # the second run of the 32x32 gas: attractive U = -4 (charge-channel fields)
-    wa = inputs.WORKLOADS[WORKLOAD + "_attractive"]
-    spa = {k: wa[k] for k in ("lattice", "U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
-    asim, aper, atotal, _, astat, aphases = run(0, spa)
-    attractive = dict(value=world * upd_per_step * args.steps / (atotal * 1e-3), unit=UNIT, U=spa["U"],
-                      sweeps_per_s=world * n_chains * args.steps / (atotal * 1e-3),
-                      p50_ms=float(np.percentile(aper, 50)), p99_ms=float(np.percentile(aper, 99)),
-                      field_accept=float(astat[1] / max(astat[0], 1)), swap_accept=float(astat[3] / max(astat[2], 1)),
-                      phase_cycle_share=aphases, precision="FP64")
-    asim.close()
+    attractive = None
+    if args.workload + "_attractive" in inputs.WORKLOADS:
+        wa = inputs.WORKLOADS[args.workload + "_attractive"]
+        spa = {k: wa[k] for k in ("lattice", "U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
+        asim, aper, atotal, _, astat, aphases = run(0, spa)
+        attractive = dict(value=world * upd_per_step * args.steps / (atotal * 1e-3), unit=UNIT, U=spa["U"],
+                          sweeps_per_s=world * n_chains * args.steps / (atotal * 1e-3),
+                          p50_ms=float(np.percentile(aper, 50)), p99_ms=float(np.percentile(aper, 99)),
+                          field_accept=float(astat[1] / max(astat[0], 1)),
+                          swap_accept=float(astat[3] / max(astat[2], 1)), phase_cycle_share=aphases, precision="FP64")
+        asim.close()
 
     serving = None
-    if not args.no_serving and world == 1:
+    if not args.no_serving and world == 1 and args.workload == WORKLOAD:
         serving = serving_leg(lq, inputs, 1, window_s=args.serving_window)
 
     if rank == 0:

@@ -863,8 +863,10 @@ template <class R> struct FlipDispatch {
 template <> struct FlipDispatch<float> {
   __device__ static void run(LqChainDev& C, int l, float* a, float* b, const float* c, const float* d, uint32_t tag,
                              Smem& sm) {
+    // FP64 algebra on FP32 panels: the rows are widened once as they are
+    // staged, so the flip loop itself converts nothing
     if (C.prec == 2) flip_slice_any<float, OpsDW>(C, l, a, b, c, d, tag, sm);
-    else flip_slice_any<float, OpsF64<float> >(C, l, a, b, c, d, tag, sm);
+    else flip_slice_any<float, OpsF64<double> >(C, l, a, b, c, d, tag, sm);
   }
 };
 // ---------------------------------------------------------------------------
