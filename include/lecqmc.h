@@ -78,7 +78,7 @@ typedef enum {
 #define LQ_OBS_SPAR 8  /* S^par(q=0) = (1/(N/2)) sum_ij <S^x_i S^x_j + S^y_i S^y_j> */
 
 /* largest particle number per spin this build supports */
-#define LQ_MAX_PARTICLES 32
+#define LQ_MAX_PARTICLES 256
 
 typedef struct lq_lattice lq_lattice;
 typedef struct lq_sim lq_sim;

@@ -243,6 +243,8 @@ struct lq_sim {
   int* d_queue = nullptr;
   int* d_all = nullptr;          // 0..n-1
   int M = 1, Nmax = 1, buf_bytes = 0, grid = 1;
+  char* ws = nullptr;            // global workspace of big plans (grid x per-CTA slab)
+  size_t ws_bytes = 0;
   bool mirror_fresh = false;
 };
 
@@ -276,6 +278,8 @@ static size_t footprint_one(int N, int nb, int G, int L, int tw, const int ns[2]
     b += al256(tw * pn * PS) + al256(pn * PS) + al256(pn * 8);
   }
   b += al256((size_t)2 * N * 8) + al256((size_t)n * LQ_NS_MAX * 2 * 8) + al256((size_t)max_records * LQ_NOBS * 8);
+  const int M = std::max(std::max(ns[0], ns[1]), 1);
+  b += al256(lq::workspace_bytes(M, N, lq::staging_bytes(M, N)));  // one CTA's workspace (big plans)
   return b + al256(sizeof(LqChainDev)) + 4 * al256(sizeof(int) * 1026);
 }
 
@@ -336,7 +340,17 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   const size_t PS = prec == LQ_FP64 ? sizeof(double) : sizeof(float);
   // shared-memory staging buffer: at least one full column of the largest
   // panel, and room for a chunk of rows in the flip loop
-  S->buf_bytes = (int)std::max<size_t>((size_t)Nmax * 8, 48 * 1024);
+  S->buf_bytes = lq::staging_bytes(M, Nmax);
+  {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = lq::smem_bytes(M, Nmax, S->buf_bytes);
+    const int per_sm = lq::max_active_sweep_ctas(prec, M, smem);
+    if (per_sm < 1) { delete S; return fail(LQ_EUNSUPPORTED, "shared-memory plan does not fit one CTA per SM"); }
+    S->grid = std::min(n_chains, sms * per_sm);
+    S->ws_bytes = (size_t)S->grid * lq::workspace_bytes(M, Nmax, S->buf_bytes);
+  }
   // arena layout
   std::vector<size_t> off(n_chains);
   size_t tot = 0;
@@ -364,6 +378,8 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   const size_t desc_off = tot;
   tot += al256(sizeof(LqChainDev) * n_chains) + 3 * al256(sizeof(int) * (n_chains + 1)) +
          al256(sizeof(int) * (n_chains + 1 + 1024));
+  const size_t ws_off = tot;
+  tot += al256(S->ws_bytes);
   S->arena_bytes = tot;
   if (S->has_alloc) S->arena = (char*)S->alloc.alloc(S->alloc.ctx, tot, stream);
   else if (cudaMalloc((void**)&S->arena, tot) != cudaSuccess) S->arena = nullptr;
@@ -377,6 +393,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   S->d_single = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
   S->d_all = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
   S->d_queue = (int*)(S->arena + o2);  // [0]: chain queue, [1..1024]: per-SM CTA counters
+  S->ws = S->ws_bytes ? S->arena + ws_off : nullptr;
   // descriptors + host-side constant data (lattice tables, P = first sites)
   S->h.resize(n_chains);
   std::vector<char> stage;
@@ -496,17 +513,10 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   if (e == cudaSuccess) e = cudaMemcpy(S->d_order, ord.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(S->d_all, all.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "descriptor upload"); }
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = lq::smem_bytes(S->M, S->Nmax, S->buf_bytes);
-  int per_sm = lq::max_active_sweep_ctas(prec, smem);
-  if (per_sm < 1) { lq_sim_destroy(S); return fail(LQ_EUNSUPPORTED, "shared-memory plan does not fit one CTA per SM"); }
-  S->grid = std::min(n_chains, sms * per_sm);
   if (build) {
     // build the chains for the default state
     S->mirror_fresh = false;
-    e = lq::launch_build(prec, S->d_chains, S->d_all, n_chains, S->M, S->Nmax, S->buf_bytes, S->grid, S->st);
+    e = lq::launch_build(prec, S->d_chains, S->d_all, n_chains, S->M, S->Nmax, S->buf_bytes, S->grid, S->st, S->ws, S->ws_bytes);
     if (e != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(e, "initial chain build"); }
   } else {
     S->mirror_fresh = true;  // the host descriptors were just uploaded
@@ -518,7 +528,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
 static lq_status rebuild(lq_sim* S, const int* d_list, int n) {
   S->mirror_fresh = false;
   cudaError_t e = lq::launch_build(S->prec, S->d_chains, d_list, n, S->M, S->Nmax, S->buf_bytes,
-                                   std::min(n, S->grid), S->st);
+                                   std::min(n, S->grid), S->st, S->ws, S->ws_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "chain build");
   return LQ_OK;
 }
@@ -602,7 +612,7 @@ extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) 
   if (n_sweeps == 0) return LQ_OK;
   S->mirror_fresh = false;
   cudaError_t e = lq::launch_sweep(S->prec, S->d_chains, S->d_order, S->n_chains, S->d_queue, n_sweeps, measure,
-                                   S->M, S->Nmax, S->buf_bytes, S->grid, S->st);
+                                   S->M, S->Nmax, S->buf_bytes, S->grid, S->st, S->ws, S->ws_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   return LQ_OK;
 }
@@ -692,7 +702,7 @@ extern "C" lq_status lq_sim_field_ratio(lq_sim* S, int32_t c, int32_t l, int32_t
   if (l < 0 || l >= S->info[c].L || i < 0 || i >= S->info[c].N) return fail(LQ_EINVAL, "slice or site out of range");
   if ((st = rebuild_one(S, c)) != LQ_OK) return st;
   S->mirror_fresh = false;
-  cudaError_t e = lq::launch_field_ratio(S->prec, S->d_chains, c, l, i, S->M, S->Nmax, S->buf_bytes, S->st);
+  cudaError_t e = lq::launch_field_ratio(S->prec, S->d_chains, c, l, i, S->M, S->Nmax, S->buf_bytes, S->st, S->ws, S->ws_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "field ratio");
   if ((st = pull(S)) != LQ_OK) return st;
   if (r) *r = S->h[c].hook[0];
@@ -712,7 +722,7 @@ extern "C" lq_status lq_sim_swap_ratio(lq_sim* S, int32_t c, int32_t sg, int32_t
     if (occ[a] == j) return fail(LQ_EINVAL, "target site is occupied");
   if ((st = rebuild_one(S, c)) != LQ_OK) return st;
   S->mirror_fresh = false;
-  cudaError_t e = lq::launch_swap_ratio(S->prec, S->d_chains, c, sg, k, j, S->M, S->Nmax, S->buf_bytes, S->st);
+  cudaError_t e = lq::launch_swap_ratio(S->prec, S->d_chains, c, sg, k, j, S->M, S->Nmax, S->buf_bytes, S->st, S->ws, S->ws_bytes);
   if (e != cudaSuccess) return cuda_fail(e, "swap ratio");
   if ((st = pull(S)) != LQ_OK) return st;
   const double* h = S->h[c].hook;

@@ -12,7 +12,10 @@ static inline void lq_dw_split(double x, float out[2]) {
 }
 
 #define LQ_NOBS 9          // sign, n_up, n_dn, docc, ekin, szz_00, szz_11, szz_01, s_par
-#define LQ_NS_MAX 32       // particles per spin handled by the flip warps (one lane per column)
+#define LQ_NS_MAX 256      // particles per spin (the C ABI's LQ_MAX_PARTICLES)
+#define LQ_NS_SMALL 32     // up to this many per spin, one warp per spin flips with one lane per column and
+                           // the m x m matrices live in shared memory; above it, a four-warp group per spin
+                           // flips and those matrices live in a global workspace per CTA
 #define LQ_THREADS 256     // threads per CTA (one CTA per chain)
 #define LQ_WIN 8           // sites per field-flip window (submatrix update)
 // 8-byte elements of one spin's window: x rows, y rows (K x MP each), G (K x (K+1)), c (K)
@@ -68,7 +71,7 @@ struct LqChainDev {
   void* live[2];            // the propagated panel of the block
   void* work[2];            // one scratch panel (measurement)
   double* vec;              // 2 x N scratch vectors (particle addition)
-  double* rot;              // n x LQ_NS_MAX x 2 Givens coefficients
+  double* rot;              // n x LQ_NS_MAX x 2 Givens coefficients (row stride LQ_NS_MAX x 2)
   double* records;          // max_records x LQ_NOBS
   int max_records, nrec;
   double logw;              // tracked log|W|

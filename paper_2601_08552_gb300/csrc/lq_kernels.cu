@@ -32,9 +32,13 @@ namespace lq {
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct SmemPlan {
-  int M, MP, Nmax, buf_bytes;
-  size_t off_T0, off_T1, off_W, off_S, off_vec, off_red, off_obs, off_gx, off_ip, off_occ, off_bits, off_chain, off_win, off_buf,
-      total;
+  int M, MP, Nmax, buf_bytes, big;
+  // offsets of T0, T1, W and S are in shared memory for small plans and in
+  // the CTA's slab of the global workspace for big ones (M > LQ_NS_SMALL)
+  size_t off_T0, off_T1, off_W, off_S, off_vec, off_red, off_obs, off_gx, off_ip, off_occ, off_bits, off_chain, off_win,
+      off_buf, total;
+  size_t ws_cta;  // global workspace bytes per CTA (0 for small plans)
+  char* ws;       // the launch's workspace, grid x ws_cta bytes (set by the launcher)
 };
 
 __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
@@ -43,12 +47,16 @@ __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
   p.MP = p.M | 1;
   p.Nmax = Nmax;
   p.buf_bytes = buf_bytes;
+  p.big = p.M > LQ_NS_SMALL;
+  p.ws = nullptr;
   size_t mat = (size_t)p.M * p.MP * 8;
-  size_t o = 0;
-  p.off_T0 = o; o = al16(o + mat);
-  p.off_T1 = o; o = al16(o + mat);
-  p.off_W = o; o = al16(o + (size_t)p.M * 2 * p.MP * 8);  // Gauss-Jordan / Gram workspace
-  p.off_S = o; o = al16(o + 6 * mat);                       // six small matrices
+  size_t o = 0, g = 0;
+  size_t& om = p.big ? g : o;  // where the m x m matrices go
+  p.off_T0 = om; om = al16(om + mat);
+  p.off_T1 = om; om = al16(om + mat);
+  p.off_W = om; om = al16(om + (size_t)p.M * 2 * p.MP * 8);  // Gauss-Jordan / Gram workspace
+  p.off_S = om; om = al16(om + 6 * mat);                       // six small matrices
+  p.ws_cta = p.big ? ((g + 255) & ~(size_t)255) : 0;
   p.off_vec = o; o = al16(o + (size_t)10 * p.M * 8);
   p.off_red = o; o = al16(o + 64 * 8);
   p.off_obs = o; o = al16(o + 16 * 8);
@@ -64,6 +72,19 @@ __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
 }
 
 size_t smem_bytes(int M, int Nmax, int buf_bytes) { return plan_smem(M, Nmax, buf_bytes).total; }
+size_t workspace_bytes(int M, int Nmax, int buf_bytes) { return plan_smem(M, Nmax, buf_bytes).ws_cta; }
+int staging_bytes(int M, int Nmax) {
+  // propagation needs one panel column (N values); the flip staging of the
+  // big path needs at least one window of sites (four rows of MP per site)
+  const int MP = (M < 1 ? 1 : M) | 1;
+  size_t b = (size_t)Nmax * 8;
+  if (b < 48 * 1024) b = 48 * 1024;
+  if (M > LQ_NS_SMALL) {
+    const size_t w = (size_t)LQ_WIN * (4 * (size_t)MP * 8 + 16);
+    if (b < w) b = w;
+  }
+  return (int)b;
+}
 
 struct Smem {
   double* T[2];
@@ -84,10 +105,11 @@ struct Smem {
 
 __device__ inline Smem carve(const SmemPlan& p, char* base) {
   Smem s;
-  s.T[0] = (double*)(base + p.off_T0);
-  s.T[1] = (double*)(base + p.off_T1);
-  s.W = (double*)(base + p.off_W);
-  s.S = (double*)(base + p.off_S);
+  char* mb = p.big ? p.ws + (size_t)blockIdx.x * p.ws_cta : base;
+  s.T[0] = (double*)(mb + p.off_T0);
+  s.T[1] = (double*)(mb + p.off_T1);
+  s.W = (double*)(mb + p.off_W);
+  s.S = (double*)(mb + p.off_S);
   s.vec = (double*)(base + p.off_vec);
   s.red = (double*)(base + p.off_red);
   s.obs = (double*)(base + p.off_obs);
@@ -467,17 +489,46 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
     double* rdiag = sm.vec + 8 * sm.M;
     for (int j = TID; j < m; j += LQ_THREADS) rdiag[j] = 1.0 / W[j * MP + j];
     __syncthreads();
-    // X <- X R^{-1}, row by row (forward substitution on the row vector)
-    for (int i = TID; i < N; i += LQ_THREADS) {
-      R* row = X + (size_t)i * m;
-      double y[LQ_NS_MAX];
+    if (m <= LQ_NS_SMALL) {
+      // X <- X R^{-1}, row by row (forward substitution on the row vector)
+      for (int i = TID; i < N; i += LQ_THREADS) {
+        R* row = X + (size_t)i * m;
+        double y[LQ_NS_SMALL];
 #pragma unroll 1
-      for (int j = 0; j < m; ++j) {
-        double acc = (double)row[j];
-        for (int a = 0; a < j; ++a) acc -= y[a] * W[a * MP + j];
-        y[j] = acc * rdiag[j];
+        for (int j = 0; j < m; ++j) {
+          double acc = (double)row[j];
+          for (int a = 0; a < j; ++a) acc -= y[a] * W[a * MP + j];
+          y[j] = acc * rdiag[j];
+        }
+        for (int j = 0; j < m; ++j) row[j] = (R)y[j];
       }
-      for (int j = 0; j < m; ++j) row[j] = (R)y[j];
+    } else {
+      // R^{-1} (upper triangular) by back substitution, one column per
+      // thread; then X <- X R^{-1} with one warp per row, the row staged in
+      // shared memory
+      double* Ri = sm.S + 2 * sm.M * MP;
+      for (int j = TID; j < m; j += LQ_THREADS) {
+        Ri[j * MP + j] = rdiag[j];
+        for (int i = j - 1; i >= 0; --i) {
+          double acc = 0.0;
+          for (int k = i + 1; k <= j; ++k) acc += W[i * MP + k] * Ri[k * MP + j];
+          Ri[i * MP + j] = -acc * rdiag[i];
+        }
+      }
+      __syncthreads();
+      const int warp = TID >> 5, lane = TID & 31;
+      double* rowbuf = (double*)sm.buf + (size_t)warp * m;
+      for (int i = warp; i < N; i += LQ_THREADS / 32) {
+        R* row = X + (size_t)i * m;
+        for (int a = lane; a < m; a += 32) rowbuf[a] = (double)row[a];
+        __syncwarp();
+        for (int j = lane; j < m; j += 32) {
+          double acc = 0.0;
+          for (int a = 0; a <= j; ++a) acc = fma(rowbuf[a], Ri[a * MP + j], acc);
+          row[j] = (R)acc;
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
   }
@@ -827,11 +878,235 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
   }
 }
 
-// the smallest compile-time column bound that holds both spins' particle numbers
+__device__ __forceinline__ void bar_group(int sg) { asm volatile("bar.sync %0, 128;" ::"r"(2 + sg) : "memory"); }
+
+// ---------------------------------------------------------------------------
+// Field flips for m > 32: the same submatrix update with each spin on a group
+// of four warps (spin = warp / 4).  The window's dense parts run over the
+// group's 128 threads, each owning whole columns:
+//   X = R~_W T  (thread owns column b of X: T column b, coalesced),
+//   Y = T L~_W  (thread owns row b of T),
+//   the x/y recurrences (thread owns column b of X and of Y: no barrier),
+//   T -= sum_t (c_t y_t) x_t^T  (thread owns column b of T);
+// the serial per-site chain (ratio, the two spins' exchange, the K x K
+// block's rank-1 updates) runs on the group's first warp, as in the small path.
+// ---------------------------------------------------------------------------
 template <class R, class Ops>
+__device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag,
+                               Smem& sm) {
+  PhaseTimer pt_(PH_FLIP);
+  typedef typename Ops::V V;
+  typedef typename Ops::Row Row;
+  typedef typename Ops::U U;
+  constexpr int K = LQ_WIN, KP = LQ_WIN + 1;
+  constexpr int GE = (K * K) / 32;
+  const int N = C.N, MP = sm.MP;
+  const int m0 = C.ns[0], m1 = C.ns[1];
+  const size_t per_site = (size_t)4 * MP * sizeof(Row) + sizeof(U) + 4 + 4;
+  int cs = (int)(sm.buf_bytes / per_site);
+  if (cs > 512) cs = 512;
+  Row* rrow = (Row*)sm.buf;
+  Row* lrow = rrow + (size_t)2 * cs * MP;
+  U* uni = (U*)(lrow + (size_t)2 * cs * MP);
+  int* sf = (int*)(uni + cs);
+  int* af = sf + cs;
+  const int warp = TID >> 5, lane = TID & 31;
+  const int sg = warp >> 2, gt = TID & 127;
+  const bool leader = (warp & 3) == 0;
+  for (int i0 = 0; i0 < N; i0 += cs) {
+    const int cn = min(cs, N - i0);
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int m = s2 ? m1 : m0;
+      const R* rp = s2 ? Rp1 : Rp0;
+      const R* lp = s2 ? Lp1 : Lp0;
+      Row* rr = rrow + (size_t)s2 * cs * MP;
+      Row* ll = lrow + (size_t)s2 * cs * MP;
+      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
+        const int ii = idx / m, a = idx - ii * m;
+        rr[(size_t)ii * MP + a] = (Row)rp[(size_t)(i0 + ii) * m + a];
+        ll[(size_t)ii * MP + a] = (Row)lp[(size_t)(i0 + ii) * m + a];
+      }
+    }
+    for (int ii = TID; ii < cn; ii += LQ_THREADS) {
+      uint32_t w[4];
+      philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
+      uni[ii] = Ops::make_u(u53(w[0], w[1]));
+      sf[ii] = C.s[(size_t)l * N + i0 + ii];
+    }
+    __syncthreads();
+    {
+      const int m = sg ? m1 : m0;
+      const typename Ops::TRef T = Ops::tref(sm, sg);
+      const bool upd = m > 0 && C.lambda != 0.0;
+      const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
+      const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
+      const V d_p = Ops::delta(C, true), d_m = Ops::delta(C, false);
+      const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
+      V* Xw = (V*)sm.win + (size_t)sg * LQ_WIN_ELEMS(MP);
+      V* Yw = Xw + K * MP;
+      V* Gw = Yw + K * MP;
+      V* cw = Gw + K * KP;
+      const Row* rbase = rrow + (size_t)sg * cs * MP;
+      const Row* lbase = lrow + (size_t)sg * cs * MP;
+      typename Ops::Prod wp;
+      wp.init();
+      int wsign = 1, nacc = 0, nbad = 0;
+      for (int t0 = 0; t0 < cn; t0 += K) {
+        const int kw = min(K, cn - t0);
+        // x_t = R_t T: thread owns column b
+        for (int b = gt; b < m; b += 128) {
+          V xa[K];
+#pragma unroll
+          for (int t = 0; t < K; ++t) xa[t] = Ops::zero();
+          for (int a = 0; a < m; ++a) {
+            const V tv = T.ld(a * MP + b);
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+              if (t < kw) Ops::acc(xa[t], rbase[(size_t)(t0 + t) * MP + a], tv);
+          }
+#pragma unroll
+          for (int t = 0; t < K; ++t)
+            if (t < kw) Xw[t * MP + b] = Ops::finish(xa[t]);
+        }
+        // y_t = T L_t: thread owns row b of T
+        for (int b = gt; b < m; b += 128) {
+          V ya[K];
+#pragma unroll
+          for (int t = 0; t < K; ++t) ya[t] = Ops::zero();
+          for (int a = 0; a < m; ++a) {
+            const V tv = T.ld(b * MP + a);
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+              if (t < kw) Ops::accT(ya[t], tv, lbase[(size_t)(t0 + t) * MP + a]);
+          }
+#pragma unroll
+          for (int t = 0; t < K; ++t)
+            if (t < kw) Yw[t * MP + b] = Ops::finish(ya[t]);
+        }
+        bar_group(sg);
+        // G[u][v] = x_u . L_v
+        if (gt < K * K) {
+          const int u = gt / K, v = gt % K;
+          if (u < kw && v < kw) {
+            const Row* lr = lbase + (size_t)(t0 + v) * MP;
+            V ga = Ops::zero();
+            for (int b = 0; b < m; ++b) Ops::accT(ga, Xw[u * MP + b], lr[b]);
+            Gw[u * KP + v] = Ops::finish(ga);
+          }
+        }
+        bar_group(sg);
+        if (leader) {
+          for (int t = 0; t < kw; ++t) {
+            const int ii = t0 + t;
+            const int s = sf[ii];
+            const bool pos = sp * s > 0;
+            const V d = pos ? d_p : d_m;
+            const V g = m > 0 ? Gw[t * KP + t] : Ops::zero();
+            const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt
+            const V c = Ops::div(d, rs);       // used if accepted
+            const int par = (i0 + ii) & 1;
+            if (lane == 0) sm.gx[par * 2 + sg] = Ops::pack(rs);
+            bar_pair();
+            V r = Ops::mul(Ops::unpack(sm.gx[par * 2]), Ops::unpack(sm.gx[par * 2 + 1]));
+            if (C.charge) r = Ops::mul(r, s > 0 ? cf_p : cf_m);
+            bool neg, bad;
+            const bool acc = Ops::accept(r, uni[ii], &neg, &bad);
+            const bool flip = acc && upd;
+            if (lane == 0) cw[t] = flip ? c : Ops::zero();
+            if (flip) {
+#pragma unroll
+              for (int it = 0; it < GE; ++it) {
+                const int e = lane + 32 * it, u = e / K, v = e % K;
+                if (u > t && v > t && u < kw && v < kw)
+                  Gw[u * KP + v] = Ops::fnma(Ops::mul(c, Gw[u * KP + t]), Gw[t * KP + v], Gw[u * KP + v]);
+              }
+              Row* rw = rrow + ((size_t)sg * cs + ii) * MP;
+              const Row f = pos ? opf_p : opf_m;
+              for (int a = lane; a < m; a += 32) rw[a] *= f;
+            }
+            if (sg == 0) {
+              if (lane == 0) af[ii] = acc ? 1 : 0;
+              nbad += bad;
+              if (acc) {
+                wp.mul(r);
+                wsign = neg ? -wsign : wsign;
+                ++nacc;
+              }
+            }
+            __syncwarp();
+          }
+        }
+        bar_group(sg);
+        // x_j, y_j at their flip times (column t and row t of G are frozen
+        // once site t is done); y is stored scaled by c_j for the T update
+        for (int b = gt; b < m; b += 128) {
+          V xb[K], yb[K];
+#pragma unroll
+          for (int t = 0; t < K; ++t)
+            if (t < kw) { xb[t] = Xw[t * MP + b]; yb[t] = Yw[t * MP + b]; }
+#pragma unroll
+          for (int t = 0; t < K - 1; ++t) {
+            if (t + 1 < kw) {
+              const V ct = cw[t];
+#pragma unroll
+              for (int j = t + 1; j < K; ++j)
+                if (j < kw) {
+                  xb[j] = Ops::fnma(Ops::mul(ct, Gw[j * KP + t]), xb[t], xb[j]);
+                  yb[j] = Ops::fnma(Ops::mul(ct, Gw[t * KP + j]), yb[t], yb[j]);
+                }
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < K; ++t)
+            if (t < kw) { Xw[t * MP + b] = xb[t]; Yw[t * MP + b] = Ops::mul(cw[t], yb[t]); }
+        }
+        bar_group(sg);
+        // T <- T - sum_t (c_t y_t) x_t^T: thread owns column b
+        for (int b = gt; b < m; b += 128) {
+          V xb[K];
+#pragma unroll
+          for (int t = 0; t < K; ++t) xb[t] = (t < kw) ? Xw[t * MP + b] : Ops::zero();
+          for (int a = 0; a < m; ++a) {
+            V tv = T.ld(a * MP + b);
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+              if (t < kw) tv = Ops::fnma(Yw[t * MP + a], xb[t], tv);
+            T.st(a * MP + b, tv);
+          }
+        }
+        bar_group(sg);
+      }
+      if (sg == 0 && leader && lane == 0) {
+        C.cnt[0] += cn;
+        C.cnt[1] += nacc;
+        C.logw += wp.log_value();
+        if (wsign < 0) C.sign = -C.sign;
+        if (nbad) C.err |= LQ_ERR_NONFINITE;
+      }
+    }
+    __syncthreads();
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int m = s2 ? m1 : m0;
+      R* rp = s2 ? Rp1 : Rp0;
+      const Row* rr = rrow + (size_t)s2 * cs * MP;
+      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
+        const int ii = idx / m, a = idx - ii * m;
+        rp[(size_t)(i0 + ii) * m + a] = (R)rr[(size_t)ii * MP + a];
+      }
+    }
+    for (int ii = TID; ii < cn; ii += LQ_THREADS)
+      if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
+    __syncthreads();
+  }
+}
+
+// the smallest compile-time column bound that holds both spins' particle
+// numbers; kernels built for big plans (BIG) also take the m > 32 path
+template <class R, class Ops, bool BIG>
 __device__ void flip_slice_any(LqChainDev& C, int l, R* a, R* b, const R* c, const R* d, uint32_t tag, Smem& sm) {
   const int m = max(C.ns[0], C.ns[1]);
-  if (m <= 4) flip_slice_win<R, Ops, 4>(C, l, a, b, c, d, tag, sm);
+  if (BIG && m > LQ_NS_SMALL) flip_slice_big<R, Ops>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 4) flip_slice_win<R, Ops, 4>(C, l, a, b, c, d, tag, sm);
   else if (m <= 8) flip_slice_win<R, Ops, 8>(C, l, a, b, c, d, tag, sm);
   else if (m <= 16) flip_slice_win<R, Ops, 16>(C, l, a, b, c, d, tag, sm);
   else flip_slice_win<R, Ops, 32>(C, l, a, b, c, d, tag, sm);
@@ -855,18 +1130,18 @@ __device__ void t_to_dw(Smem& sm, int sg, int m) {
   __syncthreads();
 }
 
-template <class R> struct FlipDispatch {
+template <class R, bool BIG> struct FlipDispatch {
   __device__ static void run(LqChainDev& C, int l, R* a, R* b, const R* c, const R* d, uint32_t tag, Smem& sm) {
-    flip_slice_any<R, OpsF64<R> >(C, l, a, b, c, d, tag, sm);
+    flip_slice_any<R, OpsF64<R>, BIG>(C, l, a, b, c, d, tag, sm);
   }
 };
-template <> struct FlipDispatch<float> {
+template <bool BIG> struct FlipDispatch<float, BIG> {
   __device__ static void run(LqChainDev& C, int l, float* a, float* b, const float* c, const float* d, uint32_t tag,
                              Smem& sm) {
     // FP64 algebra on FP32 panels: the rows are widened once as they are
     // staged, so the flip loop itself converts nothing
-    if (C.prec == 2) flip_slice_any<float, OpsDW>(C, l, a, b, c, d, tag, sm);
-    else flip_slice_any<float, OpsF64<double> >(C, l, a, b, c, d, tag, sm);
+    if (C.prec == 2) flip_slice_any<float, OpsDW, BIG>(C, l, a, b, c, d, tag, sm);
+    else flip_slice_any<float, OpsF64<double>, BIG>(C, l, a, b, c, d, tag, sm);
   }
 };
 // ---------------------------------------------------------------------------
@@ -953,7 +1228,7 @@ template <class R> __device__ void log_weight(LqChainDev& C, Smem& sm, double* o
 // ---------------------------------------------------------------------------
 // Up pass: stored left panels per block, live right panel, QR at block tops.
 // ---------------------------------------------------------------------------
-template <class R> __device__ void up_pass(LqChainDev& C, Smem& sm) {
+template <class R, bool BIG> __device__ void up_pass(LqChainDev& C, Smem& sm) {
   const int N = C.N, MP = sm.MP;
   for (int j = 1; j <= C.n; ++j) {
     const int lo = bnd(C, j - 1), hi = bnd(C, j), nl = hi - lo;
@@ -973,7 +1248,7 @@ template <class R> __device__ void up_pass(LqChainDev& C, Smem& sm) {
     }
     for (int l = lo; l < hi; ++l) {
       const size_t o0 = (size_t)(l - lo) * N * C.ns[0], o1 = (size_t)(l - lo) * N * C.ns[1];
-      FlipDispatch<R>::run(C, l, (R*)C.live[0], (R*)C.live[1], (const R*)C.stored[0] + o0, (const R*)C.stored[1] + o1, 1u, sm);
+      FlipDispatch<R, BIG>::run(C, l, (R*)C.live[0], (R*)C.live[1], (const R*)C.stored[0] + o0, (const R*)C.stored[1] + o1, 1u, sm);
       for (int sg = 0; sg < 2; ++sg) {
         const int m = C.ns[sg];
         if (l + 1 < hi) {
@@ -1099,7 +1374,7 @@ template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
 // Down pass: stored right panels per block, live left panel, QR at block
 // bottoms, measurement at each boundary below a finished block.
 // ---------------------------------------------------------------------------
-template <class R> __device__ void down_pass(LqChainDev& C, int do_measure, Smem& sm) {
+template <class R, bool BIG> __device__ void down_pass(LqChainDev& C, int do_measure, Smem& sm) {
   const int N = C.N, MP = sm.MP;
   for (int sg = 0; sg < 2; ++sg) fill_P<R>(C, sg, ql_panel<R>(C, sg, C.n));
   if (TID < LQ_NOBS) sm.obs[TID] = 0.0;
@@ -1122,7 +1397,7 @@ template <class R> __device__ void down_pass(LqChainDev& C, int do_measure, Smem
     }
     for (int l = hi - 1; l >= lo; --l) {
       const size_t o0 = (size_t)(l - lo) * N * C.ns[0], o1 = (size_t)(l - lo) * N * C.ns[1];
-      FlipDispatch<R>::run(C, l, (R*)C.stored[0] + o0, (R*)C.stored[1] + o1, (const R*)C.live[0], (const R*)C.live[1], 2u, sm);
+      FlipDispatch<R, BIG>::run(C, l, (R*)C.stored[0] + o0, (R*)C.stored[1] + o1, (const R*)C.live[0], (const R*)C.live[1], 2u, sm);
       for (int sg = 0; sg < 2; ++sg) {
         const int m = C.ns[sg];
         if (l > lo) {
@@ -1173,18 +1448,20 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     int sgnrN = 1;
     for (int i = 1; i <= n; ++i) {
       const double* Vi = vr_mat(C, sg, cb, i);
-      if (lane < m) {
-        const int src_col = (lane < k) ? lane : (lane < m - 1 ? lane + 1 : k);
-        for (int r = 0; r < m; ++r) Am[r * MP + lane] = Vi[r * m + (i == 1 ? src_col : lane)];
+      for (int cc = lane; cc < m; cc += 32) {
+        const int src_col = (cc < k) ? cc : (cc < m - 1 ? cc + 1 : k);
+        for (int r = 0; r < m; ++r) Am[r * MP + cc] = Vi[r * m + (i == 1 ? src_col : cc)];
       }
       __syncwarp();
-      if (i > 1 && lane < m) {
-        for (int t = 0; t < nrot; ++t) {
-          const int q = k + t;
-          const double c = rc[t], s = rs[t];
-          const double x = Am[lane * MP + q], y = Am[lane * MP + q + 1];
-          Am[lane * MP + q] = c * x + s * y;
-          Am[lane * MP + q + 1] = -s * x + c * y;
+      if (i > 1) {
+        for (int rr = lane; rr < m; rr += 32) {
+          for (int t = 0; t < nrot; ++t) {
+            const int q = k + t;
+            const double c = rc[t], s = rs[t];
+            const double x = Am[rr * MP + q], y = Am[rr * MP + q + 1];
+            Am[rr * MP + q] = c * x + s * y;
+            Am[rr * MP + q + 1] = -s * x + c * y;
+          }
         }
       }
       __syncwarp();
@@ -1194,10 +1471,10 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
         const double r = hypot(a, b);
         const double c = (r != 0.0) ? a / r : 1.0, s = (r != 0.0) ? b / r : 0.0;
         __syncwarp();
-        if (lane < m) {
-          const double x = Am[q * MP + lane], y = Am[(q + 1) * MP + lane];
-          Am[q * MP + lane] = c * x + s * y;
-          Am[(q + 1) * MP + lane] = -s * x + c * y;
+        for (int cc = lane; cc < m; cc += 32) {
+          const double x = Am[q * MP + cc], y = Am[(q + 1) * MP + cc];
+          Am[q * MP + cc] = c * x + s * y;
+          Am[(q + 1) * MP + cc] = -s * x + c * y;
         }
         __syncwarp();
         if (lane == 0) {
@@ -1211,8 +1488,8 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
         __syncwarp();
       }
       double* Vt = vr_mat(C, sg, tb, i);
-      if (lane < m)
-        for (int r = 0; r < m; ++r) Vt[r * m + lane] = Am[r * MP + lane];
+      for (int cc = lane; cc < m; cc += 32)
+        for (int r = 0; r < m; ++r) Vt[r * m + cc] = Am[r * MP + cc];
       const double dN = Am[(m - 1) * MP + (m - 1)];
       logrN += log(fabs(dN));
       if (dN < 0) sgnrN = -sgnrN;
@@ -1220,25 +1497,25 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     }
     // M^{-1} = G_n T0 U, then the downdate of Eq. S12
     const double* T0 = sm.T[sg];
-    if (lane < m) {
-      const int src_col = (lane < k) ? lane : (lane < m - 1 ? lane + 1 : k);
-      for (int r = 0; r < m; ++r) Mi[r * MP + lane] = T0[r * MP + src_col];
+    for (int cc = lane; cc < m; cc += 32) {
+      const int src_col = (cc < k) ? cc : (cc < m - 1 ? cc + 1 : k);
+      for (int r = 0; r < m; ++r) Mi[r * MP + cc] = T0[r * MP + src_col];
     }
     __syncwarp();
     for (int t = 0; t < nrot; ++t) {
       const int q = k + t;
       const double c = rc[t], s = rs[t];
-      if (lane < m) {
-        const double x = Mi[q * MP + lane], y = Mi[(q + 1) * MP + lane];
-        Mi[q * MP + lane] = c * x + s * y;
-        Mi[(q + 1) * MP + lane] = -s * x + c * y;
+      for (int cc = lane; cc < m; cc += 32) {
+        const double x = Mi[q * MP + cc], y = Mi[(q + 1) * MP + cc];
+        Mi[q * MP + cc] = c * x + s * y;
+        Mi[(q + 1) * MP + cc] = -s * x + c * y;
       }
       __syncwarp();
     }
     const double mNN = Mi[(m - 1) * MP + (m - 1)];
-    if (lane < mr)
-      for (int b = 0; b < mr; ++b) Tp[lane * MP + b] = Mi[lane * MP + b] - Mi[lane * MP + (m - 1)] * Mi[(m - 1) * MP + b] / mNN;
-    if (lane < mr) occr[lane] = occ[(lane < k) ? lane : lane + 1];
+    for (int rr = lane; rr < mr; rr += 32)
+      for (int b = 0; b < mr; ++b) Tp[rr * MP + b] = Mi[rr * MP + b] - Mi[rr * MP + (m - 1)] * Mi[(m - 1) * MP + b] / mNN;
+    for (int rr = lane; rr < mr; rr += 32) occr[rr] = occ[(rr < k) ? rr : rr + 1];
     if (lane == 0) {
       sm.ip[11] = occ[k];
       sm.red[48] = log(fabs(mNN)) - logrN;
@@ -1313,13 +1590,13 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     const R* Qn = qr_panel<R>(C, sg, tb, n);
     double s_add = 0.0;
     if (valid) {
-      if (lane < mr) {
+      for (int rr = lane; rr < mr; rr += 32) {
         double acc = 0.0;
-        for (int b = 0; b < mr; ++b) acc += Tp[lane * MP + b] * q[occr[b]];
-        av[lane] = acc;
+        for (int b = 0; b < mr; ++b) acc += Tp[rr * MP + b] * q[occr[b]];
+        av[rr] = acc;
         double acc2 = 0.0;
-        for (int a = 0; a < mr; ++a) acc2 += (double)Qn[(size_t)j * m + a] * Tp[a * MP + lane];
-        bv[lane] = acc2;
+        for (int a = 0; a < mr; ++a) acc2 += (double)Qn[(size_t)j * m + a] * Tp[a * MP + rr];
+        bv[rr] = acc2;
       }
       __syncwarp();
       s_add = q[j];
@@ -1342,10 +1619,10 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     __syncwarp();
     if (accept) {
       double* T0 = sm.T[sg];
-      if (lane < mr) {
-        for (int b = 0; b < mr; ++b) T0[lane * MP + b] = Tp[lane * MP + b] + av[lane] * bv[b] / s_add;
-        T0[lane * MP + (m - 1)] = -av[lane] / s_add;
-        T0[(m - 1) * MP + lane] = -bv[lane] / s_add;
+      for (int rr = lane; rr < mr; rr += 32) {
+        for (int b = 0; b < mr; ++b) T0[rr * MP + b] = Tp[rr * MP + b] + av[rr] * bv[b] / s_add;
+        T0[rr * MP + (m - 1)] = -av[rr] / s_add;
+        T0[(m - 1) * MP + rr] = -bv[rr] / s_add;
       }
       if (lane == 0) {
         T0[(m - 1) * MP + (m - 1)] = 1.0 / s_add;
@@ -1492,8 +1769,8 @@ __device__ void pick_flip_warps(int* sm_ctr, Smem& sm) {
   __syncthreads();
 }
 
-template <class R>
-__global__ void __launch_bounds__(LQ_THREADS, 2)
+template <class R, bool BIG>
+__global__ void __launch_bounds__(LQ_THREADS, BIG ? 1 : 2)
     sweep_kernel(LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps, const int* caps,
                  long long budget_ns, int do_measure, SmemPlan plan) {
   extern __shared__ __align__(16) char smem_raw[];
@@ -1516,9 +1793,9 @@ __global__ void __launch_bounds__(LQ_THREADS, 2)
     const long long t_take = global_ns();
     long long t_prev = t_take;
     for (int t = 0; t < cap; ++t) {
-      up_pass<R>(C, sm);
+      up_pass<R, BIG>(C, sm);
       swap_phase<R>(C, sm);
-      down_pass<R>(C, do_measure, sm);
+      down_pass<R, BIG>(C, do_measure, sm);
       if (TID == 0) {
         const long long t_now = global_ns();
         C.sweep++;
@@ -1639,10 +1916,10 @@ __global__ void __launch_bounds__(LQ_THREADS, 2) field_ratio_kernel(LqChainDev* 
     int s1;
     inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
     double part = 0.0;
-    if (TID < m) {
+    for (int b = TID; b < m; b += LQ_THREADS) {
       double x = 0.0;
-      for (int a = 0; a < m; ++a) x += (double)X[(size_t)i * m + a] * sm.T[sg][a * MP + TID];
-      part = x * (double)Z[(size_t)i * m + TID];
+      for (int a = 0; a < m; ++a) x += (double)X[(size_t)i * m + a] * sm.T[sg][a * MP + b];
+      part += x * (double)Z[(size_t)i * m + b];
     }
     const double gg = cta_sum(part, sm);
     r *= 1.0 + delta_of(C, sg, s) * gg;
@@ -1672,26 +1949,45 @@ template <class R> static cudaError_t set_attr(const void* fn, size_t smem) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+static const void* sweep_fn(int prec, int big) {
+  if (prec == 0) return big ? (const void*)sweep_kernel<double, true> : (const void*)sweep_kernel<double, false>;
+  return big ? (const void*)sweep_kernel<float, true> : (const void*)sweep_kernel<float, false>;
+}
+
+// Big plans keep their m x m matrices in the caller's workspace: grid slabs of ws_cta bytes.
+static cudaError_t bind_ws(SmemPlan& p, void* ws, size_t ws_bytes, int grid) {
+  if (!p.big) return cudaSuccess;
+  if (!ws || (size_t)grid * p.ws_cta > ws_bytes || ((uintptr_t)ws & 255)) return cudaErrorInvalidValue;
+  p.ws = (char*)ws;
+  return cudaSuccess;
+}
+
 cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
-                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st, const int* caps,
-                         long long budget_ns) {
+                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st, void* ws,
+                         size_t ws_bytes, const int* caps, long long budget_ns) {
   SmemPlan p = plan_smem(M, Nmax, buf_bytes);
-  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int) * (1 + 1024), st);
+  cudaError_t e = bind_ws(p, ws, ws_bytes, grid);
   if (e != cudaSuccess) return e;
-  if (prec == 0) {
-    if ((e = set_attr<double>((const void*)sweep_kernel<double>, p.total)) != cudaSuccess) return e;
-    sweep_kernel<double><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
-  } else {
-    if ((e = set_attr<float>((const void*)sweep_kernel<float>, p.total)) != cudaSuccess) return e;
-    sweep_kernel<float><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
-  }
+  e = cudaMemsetAsync(queue, 0, sizeof(int) * (1 + 1024), st);
+  if (e != cudaSuccess) return e;
+  const void* fn = sweep_fn(prec, p.big);
+  if ((e = set_attr<double>(fn, p.total)) != cudaSuccess) return e;
+  if (prec == 0 && !p.big)
+    sweep_kernel<double, false><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
+  else if (prec == 0)
+    sweep_kernel<double, true><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
+  else if (!p.big)
+    sweep_kernel<float, false><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
+  else
+    sweep_kernel<float, true><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_build(int prec, LqChainDev* chains, const int* order, int n_order, int M, int Nmax, int buf_bytes,
-                         int grid, cudaStream_t st) {
+                         int grid, cudaStream_t st, void* ws, size_t ws_bytes) {
   SmemPlan p = plan_smem(M, Nmax, buf_bytes);
-  cudaError_t e;
+  cudaError_t e = bind_ws(p, ws, ws_bytes, grid);
+  if (e != cudaSuccess) return e;
   if (prec == 0) {
     if ((e = set_attr<double>((const void*)build_kernel<double>, p.total)) != cudaSuccess) return e;
     build_kernel<double><<<grid, LQ_THREADS, p.total, st>>>(chains, order, n_order, p);
@@ -1713,9 +2009,10 @@ cudaError_t launch_init(LqChainDev* chains, const int* order, int n_order, int g
 }
 
 cudaError_t launch_field_ratio(int prec, LqChainDev* chains, int c, int l, int i, int M, int Nmax, int buf_bytes,
-                               cudaStream_t st) {
+                               cudaStream_t st, void* ws, size_t ws_bytes) {
   SmemPlan p = plan_smem(M, Nmax, buf_bytes);
-  cudaError_t e;
+  cudaError_t e = bind_ws(p, ws, ws_bytes, 1);
+  if (e != cudaSuccess) return e;
   if (prec == 0) {
     if ((e = set_attr<double>((const void*)field_ratio_kernel<double>, p.total)) != cudaSuccess) return e;
     field_ratio_kernel<double><<<1, LQ_THREADS, p.total, st>>>(chains, c, l, i, p);
@@ -1727,9 +2024,10 @@ cudaError_t launch_field_ratio(int prec, LqChainDev* chains, int c, int l, int i
 }
 
 cudaError_t launch_swap_ratio(int prec, LqChainDev* chains, int c, int sg, int k, int j, int M, int Nmax,
-                              int buf_bytes, cudaStream_t st) {
+                              int buf_bytes, cudaStream_t st, void* ws, size_t ws_bytes) {
   SmemPlan p = plan_smem(M, Nmax, buf_bytes);
-  cudaError_t e;
+  cudaError_t e = bind_ws(p, ws, ws_bytes, 1);
+  if (e != cudaSuccess) return e;
   if (prec == 0) {
     if ((e = set_attr<double>((const void*)swap_ratio_kernel<double>, p.total)) != cudaSuccess) return e;
     swap_ratio_kernel<double><<<1, LQ_THREADS, p.total, st>>>(chains, c, sg, k, j, p);
@@ -1743,9 +2041,9 @@ cudaError_t launch_swap_ratio(int prec, LqChainDev* chains, int c, int sg, int k
 }  // namespace lq
 
 namespace lq {
-int max_active_sweep_ctas(int prec, size_t smem) {
+int max_active_sweep_ctas(int prec, int M, size_t smem) {
   int n = 0;
-  const void* fn = prec == 0 ? (const void*)sweep_kernel<double> : (const void*)sweep_kernel<float>;
+  const void* fn = sweep_fn(prec, M > LQ_NS_SMALL);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, LQ_THREADS, smem) != cudaSuccess) return 0;
   return n;

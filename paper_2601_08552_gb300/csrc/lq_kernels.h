@@ -6,17 +6,23 @@
 #include "lq_device.h"
 
 namespace lq {
+// Dynamic shared memory of one CTA, global workspace per CTA (nonzero only
+// when M > LQ_NS_SMALL: then every launch needs grid x workspace_bytes of
+// 256-byte aligned device memory in ws), and the staging buffer size the
+// plan wants for M particles per spin and Nmax sites.
 size_t smem_bytes(int M, int Nmax, int buf_bytes);
+size_t workspace_bytes(int M, int Nmax, int buf_bytes);
+int staging_bytes(int M, int Nmax);
 cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
-                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st,
-                         const int* caps = nullptr, long long budget_ns = 0);
+                         int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st, void* ws,
+                         size_t ws_bytes, const int* caps = nullptr, long long budget_ns = 0);
 cudaError_t launch_build(int prec, LqChainDev* chains, const int* order, int n_order, int M, int Nmax, int buf_bytes,
-                         int grid, cudaStream_t st);
+                         int grid, cudaStream_t st, void* ws, size_t ws_bytes);
 cudaError_t launch_clear_records(LqChainDev* chains, int n, cudaStream_t st);
 cudaError_t launch_init(LqChainDev* chains, const int* order, int n_order, int grid, cudaStream_t st);
 cudaError_t launch_field_ratio(int prec, LqChainDev* chains, int c, int l, int i, int M, int Nmax, int buf_bytes,
-                               cudaStream_t st);
+                               cudaStream_t st, void* ws, size_t ws_bytes);
 cudaError_t launch_swap_ratio(int prec, LqChainDev* chains, int c, int sg, int k, int j, int M, int Nmax,
-                              int buf_bytes, cudaStream_t st);
-int max_active_sweep_ctas(int prec, size_t smem);
+                              int buf_bytes, cudaStream_t st, void* ws, size_t ws_bytes);
+int max_active_sweep_ctas(int prec, int M, size_t smem);
 }  // namespace lq

@@ -98,6 +98,10 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
     o_st[sg] = take(tw * pn * PS); o_live[sg] = take(pn * PS); o_work[sg] = take(pn * 8);
   }
   const size_t o_vec = take((size_t)2 * N * 8), o_rot = take((size_t)n * LQ_NS_MAX * 2 * 8);
+  const int M = std::max(std::max(ns[0], ns[1]), 1);
+  const int buf_bytes = lq::staging_bytes(M, N);
+  const size_t ws_bytes = lq::workspace_bytes(M, N, buf_bytes);  // one CTA's slab (big plans only)
+  const size_t o_ws = take(ws_bytes);
   if (o > (size_t)LQ_NOALLOC_SCRATCH_BYTES)
     return lq_internal_fail(LQ_EUNSUPPORTED, "lq_sweep_noalloc: this chain needs " + std::to_string(o) +
                                                  " scratch bytes, more than LQ_NOALLOC_SCRATCH_BYTES (" +
@@ -168,11 +172,11 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   LqChainDev* dchain = (LqChainDev*)(base + o_desc);
   const int* dorder = (const int*)(base + o_order);
   int* dqueue = (int*)(base + o_queue);
-  const int M = std::max(1, std::max(ns[0], ns[1]));
-  const int buf_bytes = (int)std::max<size_t>((size_t)N * 8, 48 * 1024);
-  e = lq::launch_build(p->precision, dchain, dorder, 1, M, N, buf_bytes, 1, st);
+  void* ws = ws_bytes ? (void*)(base + o_ws) : nullptr;
+  e = lq::launch_build(p->precision, dchain, dorder, 1, M, N, buf_bytes, 1, st, ws, ws_bytes);
   if (e == cudaSuccess && n_sweeps > 0)
-    e = lq::launch_sweep(p->precision, dchain, dorder, 1, dqueue, n_sweeps, dev_records ? 1 : 0, M, N, buf_bytes, 1, st);
+    e = lq::launch_sweep(p->precision, dchain, dorder, 1, dqueue, n_sweeps, dev_records ? 1 : 0, M, N, buf_bytes, 1, st,
+                         ws, ws_bytes);
   if (e != cudaSuccess) return lq_internal_fail(LQ_ECUDA, std::string("lq_sweep_noalloc launch: ") + cudaGetErrorString(e));
   if (host_log_weight || host_sign || host_counts4) {
     LqChainDev out;

@@ -89,6 +89,8 @@ struct lq_server {
   int* d_order = nullptr;
   int* d_caps = nullptr;
   int* d_queue = nullptr;
+  char* d_ws = nullptr;  // workspace of big plans for the gathered launches (grown on demand)
+  size_t ws_cap = 0;
   int dev_sms = 1;
   double tick_target_ms = 20.0;
   double ns_per_cost = 0.0;  // running estimate of sweep nanoseconds per cost unit
@@ -111,6 +113,20 @@ static void* srv_alloc(void* ctx, size_t bytes, void* stream) {
   return p;
 }
 static void srv_free(void*, void* ptr, size_t, void* stream) { cudaFreeAsync(ptr, (cudaStream_t)stream); }
+
+// Workspace for a gathered launch of `grid` CTAs (stream-ordered, from the pool).
+static cudaError_t ensure_ws(lq_server* S, size_t bytes) {
+  if (bytes <= S->ws_cap) return cudaSuccess;
+  if (S->d_ws) cudaFreeAsync(S->d_ws, S->st);
+  S->d_ws = nullptr;
+  S->ws_cap = 0;
+  void* p = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, S->pool, S->st);
+  if (e != cudaSuccess) return e;
+  S->d_ws = (char*)p;
+  S->ws_cap = bytes;
+  return cudaSuccess;
+}
 
 static void finish_failed(lq_server* S, uint64_t id, size_t footprint, lq_status st) {
   lq_result r;
@@ -216,12 +232,14 @@ static void admit(lq_server* S) {
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return fresh[x].cost > fresh[y].cost; });
   const size_t smem = lq::smem_bytes(M, Nmax, buf);
-  const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, smem));
+  const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, M, smem));
   cudaError_t e = cudaMemcpyAsync(S->d_slots, desc.data(), sizeof(LqChainDev) * n, cudaMemcpyHostToDevice, S->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->st);
+  const int grid = std::min(n, S->dev_sms * per_sm);
+  if (e == cudaSuccess) e = ensure_ws(S, (size_t)grid * lq::workspace_bytes(M, Nmax, buf));
   if (e == cudaSuccess) e = lq::launch_init(S->d_slots, S->d_order, n, std::min(n, 1024), S->st);
   if (e == cudaSuccess)
-    e = lq::launch_build(S->prec, S->d_slots, S->d_order, n, M, Nmax, buf, std::min(n, S->dev_sms * per_sm), S->st);
+    e = lq::launch_build(S->prec, S->d_slots, S->d_order, n, M, Nmax, buf, grid, S->st, S->d_ws, S->ws_cap);
   if (e == cudaSuccess) e = cudaMemcpyAsync(desc.data(), S->d_slots, sizeof(LqChainDev) * n, cudaMemcpyDeviceToHost, S->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
   const double t_admit = now_s();
@@ -280,13 +298,16 @@ static void tick(lq_server* S) {
   cudaMemcpyAsync(S->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->st);
   cudaMemcpyAsync(S->d_caps, caps.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->st);
   const size_t smem = lq::smem_bytes(M, Nmax, buf);
-  const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, smem));
+  const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, M, smem));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  const int grid = std::min(n, S->dev_sms * per_sm);
+  cudaError_t e = ensure_ws(S, (size_t)grid * lq::workspace_bytes(M, Nmax, buf));
   cudaEventRecord(e0, S->st);
-  cudaError_t e = lq::launch_sweep(S->prec, S->d_slots, S->d_order, n, S->d_queue, 1, 1, M, Nmax, buf,
-                                   std::min(n, S->dev_sms * per_sm), S->st, S->d_caps, budget_ns);
+  if (e == cudaSuccess)
+    e = lq::launch_sweep(S->prec, S->d_slots, S->d_order, n, S->d_queue, 1, 1, M, Nmax, buf, grid, S->st, S->d_ws,
+                         S->ws_cap, S->d_caps, budget_ns);
   cudaEventRecord(e1, S->st);
   cudaMemcpyAsync(desc.data(), S->d_slots, sizeof(LqChainDev) * n, cudaMemcpyDeviceToHost, S->st);
   cudaError_t e2 = cudaStreamSynchronize(S->st);
@@ -497,6 +518,7 @@ extern "C" lq_status lq_server_destroy(lq_server* S) {
     S->cv.notify_one();
     S->worker.join();
   }
+  if (S->d_ws && S->st) cudaFreeAsync(S->d_ws, S->st);
   if (S->st) cudaStreamSynchronize(S->st);
   cudaFree(S->d_slots);
   cudaFree(S->d_order);
