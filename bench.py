@@ -268,6 +268,29 @@ def serving_leg(lq, inputs, prec, rate=200.0, window_s=5.0, n_sweeps=10, seed=No
                 precision=prec)
 
 
+# ---------------------------------------------------------------------------
+# multi-rank helpers (one process per GPU; chains are independent, so ranks
+# share nothing but the timing reduction)
+# ---------------------------------------------------------------------------
+def rank_chain_ids(rank, n_chains):
+    """Philox chain words of this rank's chains: disjoint across ranks."""
+    return [rank * n_chains + c for c in range(n_chains)]
+
+
+def max_over_ranks(torch, dist, x, device):
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, units_per_rank_step, steps, max_ms):
+    """Whole-job rate: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank_step * steps / (max_ms * 1e-3)
+
+
 def time_steps(torch, sim, steps, stream):
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     evs[0].record(stream)
@@ -333,7 +356,7 @@ def main():
     upd_per_step = n_chains * 2 * L * N
 
     def make(prec, sp=spec):
-        ids = [rank * n_chains + c for c in range(n_chains)]
+        ids = rank_chain_ids(rank, n_chains)
         s = lq.Sim([lat] * n_chains, [dict(sp, precision=prec, seed=inputs.SEED0)] * n_chains, chain_ids=ids,
                    stream=stream.cuda_stream)
         s.init()
@@ -357,11 +380,7 @@ def main():
         clk = ClockSampler(bus) if (prec == 0 and sp is spec) else None
         per = time_steps(torch, sim, args.steps, stream)
         clocks = clk.stop() if clk else None
-        total_ms = sum(per)
-        if dist is not None:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(torch, dist, sum(per), "cuda")
         sim.sync()
         st1 = sum(sim.stats(c) for c in range(n_chains))
         d = st1 - st0
@@ -373,7 +392,7 @@ def main():
 
     run.lw0 = {}
     sim, per, total_ms, clocks, dstat, phases = run(0)
-    value = world * upd_per_step * args.steps / (total_ms * 1e-3)
+    value = aggregate_rate(world, upd_per_step, args.steps, total_ms)
     sweeps = world * n_chains * args.steps / (total_ms * 1e-3)
     flops = algorithmic_fp64_flops(spec, n_chains, dstat[1], dstat[0], lat.n_bonds, 0)
     kern_ms = total_ms / args.steps
@@ -405,11 +424,7 @@ def main():
         ho, ho_out = ho_out, ho
         if k > 0:
             e2e_times.append(dt)
-    e2e_s = max(sum(e2e_times), 1e-12)
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(torch, dist, max(sum(e2e_times), 1e-12), "cuda")
     e2e = dict(value=world * upd_per_step * len(e2e_times) / e2e_s, unit=UNIT,
                h2d_bytes_per_step=int(hf.numel() + 4 * ho.numel()),
                d2h_bytes_per_step=int(hf.numel() + 4 * ho.numel() + 8 * rec.numel()),
