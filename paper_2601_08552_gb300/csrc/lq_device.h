@@ -18,8 +18,9 @@ static inline void lq_dw_split(double x, float out[2]) {
                            // flips and those matrices live in a global workspace per CTA
 #define LQ_THREADS 256     // threads per CTA (one CTA per chain)
 #define LQ_WIN 8           // sites per field-flip window (submatrix update)
-// 8-byte elements of one spin's window: x rows, y rows (K x MP each), G (K x (K+1)), c (K)
-#define LQ_WIN_ELEMS(MP) (2 * LQ_WIN * (MP) + LQ_WIN * (LQ_WIN + 1) + LQ_WIN)
+// 8-byte elements of one spin's window: x rows, y rows (K x MP each), G (K x (K+1)), c (K),
+// c-scaled G factors of the x/y recurrences (K x K)
+#define LQ_WIN_ELEMS(MP) (2 * LQ_WIN * (MP) + LQ_WIN * (LQ_WIN + 1) + LQ_WIN + LQ_WIN * LQ_WIN)
 
 // Error bits a kernel may set in LqChainDev::err.
 #define LQ_ERR_SINGULAR 1  // a Gram / overlap matrix had a zero pivot

@@ -80,7 +80,7 @@ int staging_bytes(int M, int Nmax) {
   size_t b = (size_t)Nmax * 8;
   if (b < 48 * 1024) b = 48 * 1024;
   if (M > LQ_NS_SMALL) {
-    const size_t w = (size_t)LQ_WIN * (4 * (size_t)MP * 8 + 16);
+    const size_t w = (size_t)LQ_WIN * (4 * (size_t)MP * 8 + 32);
     if (b < w) b = w;
   }
   return (int)b;
@@ -595,11 +595,19 @@ template <class RowT> struct OpsF64 {
     double m;
     long long e;
     __device__ void init() { m = 1.0; e = 0; }
-    __device__ void mul(V r) {
-      m *= fabs(r);
+    __device__ void mul_pos(double x) {
+      m *= x;
       const long long bits = __double_as_longlong(m);
       e += ((bits >> 52) & 0x7ff) - 1022;
       m = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1022LL << 52));
+    }
+    __device__ void mul(V r) { mul_pos(fabs(r)); }
+    // multiply by the product held by lane (lane ^ o)
+    __device__ void combine_xor(int o) {
+      const double om = __shfl_xor_sync(FULL, m, o);
+      const long long oe = __shfl_xor_sync(FULL, e, o);
+      mul_pos(om);
+      e += oe;
     }
     __device__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
   };
@@ -655,14 +663,21 @@ struct OpsDW {
     dw m;
     long long e;
     __device__ void init() { m = dw{1.f, 0.f}; e = 0; }
-    __device__ void mul(V r) {
-      m = dw_mul(m, r.h < 0.f ? dw_neg(r) : r);
+    __device__ void mul_pos(dw x) {
+      m = dw_mul(m, x);
       // exact rescale by a power of two: keep m.h in [0.5, 1)
       const int ex = ((__float_as_int(m.h) >> 23) & 0xff) - 126;
       const float sc = __int_as_float((127 - ex) << 23);
       m.h *= sc;
       m.l *= sc;
       e += ex;
+    }
+    __device__ void mul(V r) { mul_pos(r.h < 0.f ? dw_neg(r) : r); }
+    __device__ void combine_xor(int o) {
+      const dw om = dw_shfl_xor(m, o);
+      const long long oe = __shfl_xor_sync(FULL, e, o);
+      mul_pos(om);
+      e += oe;
     }
     __device__ double log_value() const { return log((double)m.h + (double)m.l) + (double)e * 0.69314718055994530942; }
   };
@@ -699,14 +714,16 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
   constexpr int XU = XE < 2 ? XE : 2, TU = TE < 2 ? TE : 2;  // unroll of the per-lane element loops
   const int N = C.N, MP = sm.MP;
   const int m0 = C.ns[0], m1 = C.ns[1];
-  const size_t per_site = (size_t)4 * MP * sizeof(Row) + sizeof(U) + 4 + 4;
+  const size_t per_site = (size_t)4 * MP * sizeof(Row) + 8 + sizeof(U) + 4 + 4;
   int cs = (int)(sm.buf_bytes / per_site);
   if (cs > 512) cs = 512;
   Row* rrow = (Row*)sm.buf;
   Row* lrow = rrow + (size_t)2 * cs * MP;
-  U* uni = (U*)(lrow + (size_t)2 * cs * MP);
+  double* racc = (double*)(lrow + (size_t)2 * cs * MP);  // accepted ratios (packed), multiplied per chunk
+  U* uni = (U*)(racc + cs);
   int* sf = (int*)(uni + cs);
   int* af = sf + cs;
+  const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
   const int warp = TID >> 5, lane = TID & 31;
   const int role = (warp == sm.ip[14]) ? 0 : (warp == sm.ip[15]) ? 1 : -1;
   for (int i0 = 0; i0 < N; i0 += cs) {
@@ -737,17 +754,15 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
       const typename Ops::TRef T = Ops::tref(sm, sg);
       const bool upd = m > 0 && C.lambda != 0.0;
       const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
-      const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
       const V d_p = Ops::delta(C, true), d_m = Ops::delta(C, false);
       const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
       V* Xw = (V*)sm.win + (size_t)sg * LQ_WIN_ELEMS(MP);
       V* Yw = Xw + K * MP;
       V* Gw = Yw + K * MP;
       V* cw = Gw + K * KP;
+      V* CG = cw + K;  // c_t G[j][t] (j > t) and c_t G[t][j] (t < j)
       const Row* rbase = rrow + (size_t)sg * cs * MP;
       const Row* lbase = lrow + (size_t)sg * cs * MP;
-      typename Ops::Prod wp;
-      wp.init();
       int wsign = 1, nacc = 0, nbad = 0;
       for (int t0 = 0; t0 < cn; t0 += K) {
         const int kw = min(K, cn - t0);
@@ -802,45 +817,62 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
           const bool flip = acc && upd;
           if (lane == 0) cw[t] = flip ? c : Ops::zero();
           if (flip) {
+            // c G[u][t] once per row u (lane u), then G[u][v] -= (c G[u][t]) G[t][v];
+            // column t is not written at this step, so the factors are current
+            const V cu = Ops::mul(c, Gw[(lane & (K - 1)) * KP + t]);
 #pragma unroll
             for (int it = 0; it < GE; ++it) {
               const int e = lane + 32 * it, u = e / K, v = e % K;
-              if (u > t && v > t && u < kw && v < kw)
-                Gw[u * KP + v] = Ops::fnma(Ops::mul(c, Gw[u * KP + t]), Gw[t * KP + v], Gw[u * KP + v]);
-            }
-            if (lane < m) {
-              Row* rw = rrow + ((size_t)sg * cs + ii) * MP;
-              rw[lane] *= pos ? opf_p : opf_m;
+              const V cuu = Ops::from_lane(cu, u);
+              if (u > t && v > t && u < kw && v < kw) Gw[u * KP + v] = Ops::fnma(cuu, Gw[t * KP + v], Gw[u * KP + v]);
             }
           }
           if (sg == 0) {
-            if (lane == 0) af[ii] = acc ? 1 : 0;
+            if (lane == 0) {
+              af[ii] = acc ? 1 : 0;
+              racc[ii] = Ops::pack(r);
+            }
             nbad += bad;
             if (acc) {
-              wp.mul(r);
               wsign = neg ? -wsign : wsign;
               ++nacc;
             }
           }
           __syncwarp();
         }
+        // c-scaled factors of the recurrences: CG[j][t] = c_t G[j][t] (j > t),
+        // CG[t][j] = c_t G[t][j] (t < j)
+#pragma unroll
+        for (int it = 0; it < GE; ++it) {
+          const int e = lane + 32 * it, u = e / K, v = e % K;
+          V val = Ops::zero();
+          if (u > v && u < kw) val = Ops::mul(cw[v], Gw[u * KP + v]);
+          else if (u < v && v < kw) val = Ops::mul(cw[u], Gw[u * KP + v]);
+          CG[u * K + v] = val;
+        }
+        __syncwarp();
         // the window's x_j, y_j at their flip times: column t and row t of the
         // block are frozen once site t is done, so the recurrences
         //   x_j -= c_t G[j][t] x_t,  y_j -= c_t G[t][j] y_t  (j > t)
         // run here, t ascending, parallel over (j, b)
         for (int t = 0; t + 1 < kw; ++t) {
-          const V ct = cw[t];
 #pragma unroll XU
           for (int it = 0; it < XE; ++it) {
             const int e = lane + 32 * it, j = e / MT, b = e % MT;
             if (e < K * MT && j > t && j < kw && b < m) {
-              Xw[j * MP + b] = Ops::fnma(Ops::mul(ct, Gw[j * KP + t]), Xw[t * MP + b], Xw[j * MP + b]);
-              Yw[j * MP + b] = Ops::fnma(Ops::mul(ct, Gw[t * KP + j]), Yw[t * MP + b], Yw[j * MP + b]);
+              Xw[j * MP + b] = Ops::fnma(CG[j * K + t], Xw[t * MP + b], Xw[j * MP + b]);
+              Yw[j * MP + b] = Ops::fnma(CG[t * K + j], Yw[t * MP + b], Yw[j * MP + b]);
             }
           }
           __syncwarp();
         }
-        // T <- T - sum_t c_t y_t x_t^T   (element (a, b), b = lane % MT)
+        // y_t <- c_t y_t, then T <- T - sum_t (c_t y_t) x_t^T  (element (a, b), b = lane % MT)
+#pragma unroll XU
+        for (int it = 0; it < XE; ++it) {
+          const int e = lane + 32 * it, t = e / MT, b = e % MT;
+          if (e < K * MT && t < kw && b < m) Yw[t * MP + b] = Ops::mul(cw[t], Yw[t * MP + b]);
+        }
+        __syncwarp();
 #pragma unroll TU
         for (int it = 0; it < TE; ++it) {
           const int e = lane + 32 * it, a = e / MT, b = e % MT;
@@ -848,28 +880,43 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
             V tv = T.ld(a * MP + b);
 #pragma unroll
             for (int t = 0; t < K; ++t)
-              if (t < kw) tv = Ops::fnma(Ops::mul(cw[t], Yw[t * MP + a]), Xw[t * MP + b], tv);
+              if (t < kw) tv = Ops::fnma(Yw[t * MP + a], Xw[t * MP + b], tv);
             T.st(a * MP + b, tv);
           }
         }
         __syncwarp();
       }
-      if (sg == 0 && lane == 0) {
-        C.cnt[0] += cn;
-        C.cnt[1] += nacc;
-        C.logw += wp.log_value();
-        if (wsign < 0) C.sign = -C.sign;
-        if (nbad) C.err |= LQ_ERR_NONFINITE;
+      if (sg == 0) {
+        // product of the chunk's accepted ratios, lane-parallel
+        typename Ops::Prod wp;
+        wp.init();
+        for (int ii = lane; ii < cn; ii += 32)
+          if (af[ii]) wp.mul(Ops::unpack(racc[ii]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wp.combine_xor(o);
+        if (lane == 0) {
+          C.cnt[0] += cn;
+          C.cnt[1] += nacc;
+          C.logw += wp.log_value();
+          if (wsign < 0) C.sign = -C.sign;
+          if (nbad) C.err |= LQ_ERR_NONFINITE;
+        }
       }
     }
     __syncthreads();
+    // rows back to the panel; accepted sites scale their row by 1 + Delta_sigma
     for (int sg = 0; sg < 2; ++sg) {
       const int m = sg ? m1 : m0;
+      const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
       R* rp = sg ? Rp1 : Rp0;
       const Row* rr = rrow + (size_t)sg * cs * MP;
       for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
         const int a = TID % MT;
-        if (a < m) rp[(size_t)(i0 + ii) * m + a] = (R)rr[(size_t)ii * MP + a];
+        if (a < m) {
+          Row v = rr[(size_t)ii * MP + a];
+          if (af[ii]) v *= (sp * sf[ii] > 0) ? opf_p : opf_m;
+          rp[(size_t)(i0 + ii) * m + a] = (R)v;
+        }
       }
     }
     for (int ii = TID; ii < cn; ii += LQ_THREADS)
@@ -902,14 +949,16 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
   constexpr int GE = (K * K) / 32;
   const int N = C.N, MP = sm.MP;
   const int m0 = C.ns[0], m1 = C.ns[1];
-  const size_t per_site = (size_t)4 * MP * sizeof(Row) + sizeof(U) + 4 + 4;
+  const size_t per_site = (size_t)4 * MP * sizeof(Row) + 8 + sizeof(U) + 4 + 4;
   int cs = (int)(sm.buf_bytes / per_site);
   if (cs > 512) cs = 512;
   Row* rrow = (Row*)sm.buf;
   Row* lrow = rrow + (size_t)2 * cs * MP;
-  U* uni = (U*)(lrow + (size_t)2 * cs * MP);
+  double* racc = (double*)(lrow + (size_t)2 * cs * MP);
+  U* uni = (U*)(racc + cs);
   int* sf = (int*)(uni + cs);
   int* af = sf + cs;
+  const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
   const int warp = TID >> 5, lane = TID & 31;
   const int sg = warp >> 2, gt = TID & 127;
   const bool leader = (warp & 3) == 0;
@@ -939,7 +988,6 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
       const typename Ops::TRef T = Ops::tref(sm, sg);
       const bool upd = m > 0 && C.lambda != 0.0;
       const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
-      const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
       const V d_p = Ops::delta(C, true), d_m = Ops::delta(C, false);
       const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
       V* Xw = (V*)sm.win + (size_t)sg * LQ_WIN_ELEMS(MP);
@@ -948,8 +996,6 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
       V* cw = Gw + K * KP;
       const Row* rbase = rrow + (size_t)sg * cs * MP;
       const Row* lbase = lrow + (size_t)sg * cs * MP;
-      typename Ops::Prod wp;
-      wp.init();
       int wsign = 1, nacc = 0, nbad = 0;
       for (int t0 = 0; t0 < cn; t0 += K) {
         const int kw = min(K, cn - t0);
@@ -1020,15 +1066,14 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
                 if (u > t && v > t && u < kw && v < kw)
                   Gw[u * KP + v] = Ops::fnma(Ops::mul(c, Gw[u * KP + t]), Gw[t * KP + v], Gw[u * KP + v]);
               }
-              Row* rw = rrow + ((size_t)sg * cs + ii) * MP;
-              const Row f = pos ? opf_p : opf_m;
-              for (int a = lane; a < m; a += 32) rw[a] *= f;
             }
             if (sg == 0) {
-              if (lane == 0) af[ii] = acc ? 1 : 0;
+              if (lane == 0) {
+                af[ii] = acc ? 1 : 0;
+                racc[ii] = Ops::pack(r);
+              }
               nbad += bad;
               if (acc) {
-                wp.mul(r);
                 wsign = neg ? -wsign : wsign;
                 ++nacc;
               }
@@ -1076,22 +1121,34 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
         }
         bar_group(sg);
       }
-      if (sg == 0 && leader && lane == 0) {
-        C.cnt[0] += cn;
-        C.cnt[1] += nacc;
-        C.logw += wp.log_value();
-        if (wsign < 0) C.sign = -C.sign;
-        if (nbad) C.err |= LQ_ERR_NONFINITE;
+      if (sg == 0 && leader) {
+        typename Ops::Prod wp;
+        wp.init();
+        for (int ii = lane; ii < cn; ii += 32)
+          if (af[ii]) wp.mul(Ops::unpack(racc[ii]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wp.combine_xor(o);
+        if (lane == 0) {
+          C.cnt[0] += cn;
+          C.cnt[1] += nacc;
+          C.logw += wp.log_value();
+          if (wsign < 0) C.sign = -C.sign;
+          if (nbad) C.err |= LQ_ERR_NONFINITE;
+        }
       }
     }
     __syncthreads();
+    // rows back to the panel; accepted sites scale their row by 1 + Delta_sigma
     for (int s2 = 0; s2 < 2; ++s2) {
       const int m = s2 ? m1 : m0;
+      const int sp2 = C.charge ? 1 : (s2 == 0 ? 1 : -1);
       R* rp = s2 ? Rp1 : Rp0;
       const Row* rr = rrow + (size_t)s2 * cs * MP;
       for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
         const int ii = idx / m, a = idx - ii * m;
-        rp[(size_t)(i0 + ii) * m + a] = (R)rr[(size_t)ii * MP + a];
+        Row v = rr[(size_t)ii * MP + a];
+        if (af[ii]) v *= (sp2 * sf[ii] > 0) ? opf_p : opf_m;
+        rp[(size_t)(i0 + ii) * m + a] = (R)v;
       }
     }
     for (int ii = TID; ii < cn; ii += LQ_THREADS)
