@@ -293,6 +293,34 @@ def aggregate_rate(world, units_per_rank_step, steps, max_ms):
     return world * units_per_rank_step * steps / (max_ms * 1e-3)
 
 
+def uneven_leg(lq, inputs, torch, stream, prec=0, n_chains=608, steps=2, warmup=1):
+    """Hundreds of flat-band chains of uneven N, N_sigma and beta advancing in
+    one persistent launch per plan class.  The paper-shaped batch (cells
+    U[64, 512], beta U[4, 40]) costs minutes per sweep, so the leg draws
+    cells U[16, 128] and beta U[1, 4] with the same filling law (N_sigma
+    from 2 to 48, both plan classes present)."""
+    rng = np.random.default_rng(inputs.SEED0 + 4)
+    specs = inputs.flatband_batch(rng, n_chains, cells=(16, 128), beta_range=(1.0, 4.0))
+    lats = [lq.Lattice.flatband(*sp["lattice"][1:]) for sp in specs]
+    params = [dict({k: sp[k] for k in ("U", "beta", "dtau", "n_up", "n_dn", "n_stab")}, precision=prec,
+                   seed=inputs.SEED0) for sp in specs]
+    sim = lq.Sim(lats, params, stream=stream.cuda_stream)
+    sim.init()
+    for _ in range(warmup):
+        sim.sweep(1, measure=True)
+    per = time_steps(torch, sim, steps, stream)
+    upd = sum(2 * round(p["beta"] / p["dtau"]) * L.N for p, L in zip(params, lats))
+    ns = np.array([p["n_up"] for p in params])
+    Ns = np.array([L.N for L in lats])
+    sim.close()
+    return dict(chains=n_chains, value=upd * steps / (sum(per) * 1e-3), unit=UNIT,
+                sweeps_per_s=n_chains * steps / (sum(per) * 1e-3), ms_per_sweep=float(np.mean(per)),
+                n_sigma_range=[int(ns.min()), int(ns.max())], chains_above_32=int((ns > 32).sum()),
+                N_range=[int(Ns.min()), int(Ns.max())], precision="FP64",
+                mix="BCL flat-band chains, cells U[16, 128], filling U[1/4, 3/4] of the flat band split by spin, "
+                    "beta U[1, 4], dtau 0.05, U=2, half periodic")
+
+
 def time_steps(torch, sim, steps, stream):
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     evs[0].record(stream)
@@ -315,6 +343,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--chains", type=int, default=0, help="override the chain count (small profiling cases)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--serving-window", type=float, default=10.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=["gas32x32", "gas64x64"],
                     help="gas64x64: the 64x64 mixed-precision comparison (512 chains, ~10 s per sweep)")
@@ -465,6 +494,10 @@ def main():
                           swap_accept=float(astat[3] / max(astat[2], 1)), phase_cycle_share=aphases, precision="FP64")
         asim.close()
 
+    uneven = None
+    if not args.no_uneven and args.workload == WORKLOAD:
+        uneven = uneven_leg(lq, inputs, torch, stream)
+
     serving = None
     if not args.no_serving and world == 1 and args.workload == WORKLOAD:
         serving = serving_leg(lq, inputs, 1, window_s=args.serving_window)
@@ -481,7 +514,8 @@ def main():
                     field_accept=float(dstat[1] / max(dstat[0], 1)),
                     swap_accept=float(dstat[3] / max(dstat[2], 1)), phase_cycle_share=phases,
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
-                    reduced_precision=mixed, attractive=attractive, serving=serving)
+                    reduced_precision=mixed, attractive=attractive, uneven_flatband=uneven,
+                    serving=serving)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

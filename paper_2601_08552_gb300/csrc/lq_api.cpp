@@ -243,6 +243,12 @@ struct lq_sim {
   int* d_queue = nullptr;
   int* d_all = nullptr;          // 0..n-1
   int M = 1, Nmax = 1, buf_bytes = 0, grid = 1;
+  // sweeps run one launch per plan class: chains with at most LQ_NS_SMALL
+  // particles per spin (shared-memory plan), then the larger ones (global
+  // workspace); d_order holds the small class first, each by decreasing cost
+  struct PlanClass {
+    int n = 0, off = 0, M = 1, Nmax = 1, buf = 0, grid = 1;
+  } cls[2];
   char* ws = nullptr;            // global workspace of big plans (grid x per-CTA slab)
   size_t ws_bytes = 0;
   bool mirror_fresh = false;
@@ -508,7 +514,31 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   // order: decreasing cost (longest chains first)
   std::vector<int> ord(n_chains), all(n_chains);
   for (int c = 0; c < n_chains; ++c) ord[c] = all[c] = c;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return info[a].cost > info[b].cost; });
+  auto big_of = [&](int c) { return std::max(info[c].ns[0], info[c].ns[1]) > LQ_NS_SMALL; };
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    if (big_of(a) != big_of(b)) return !big_of(a);
+    return info[a].cost > info[b].cost;
+  });
+  {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int k = 0; k < 2; ++k) {
+      lq_sim::PlanClass& pc = S->cls[k];
+      pc.off = k ? S->cls[0].n : 0;
+      for (int c = 0; c < n_chains; ++c) {
+        if (big_of(c) != (k == 1)) continue;
+        pc.n++;
+        pc.M = std::max(pc.M, std::max(info[c].ns[0], info[c].ns[1]));
+        pc.Nmax = std::max(pc.Nmax, info[c].N);
+      }
+      if (!pc.n) continue;
+      pc.buf = lq::staging_bytes(pc.M, pc.Nmax);
+      const int per_sm = lq::max_active_sweep_ctas(prec, pc.M, lq::smem_bytes(pc.M, pc.Nmax, pc.buf));
+      if (per_sm < 1) { lq_sim_destroy(S); return fail(LQ_EUNSUPPORTED, "shared-memory plan does not fit one CTA per SM"); }
+      pc.grid = std::min(pc.n, sms * per_sm);
+    }
+  }
   e = cudaMemcpy(S->d_chains, S->h.data(), sizeof(LqChainDev) * n_chains, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(S->d_order, ord.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(S->d_all, all.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice);
@@ -611,8 +641,13 @@ extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) 
   if (!S || n_sweeps < 0) return fail(LQ_EINVAL, "bad arguments to lq_sim_sweep");
   if (n_sweeps == 0) return LQ_OK;
   S->mirror_fresh = false;
-  cudaError_t e = lq::launch_sweep(S->prec, S->d_chains, S->d_order, S->n_chains, S->d_queue, n_sweeps, measure,
-                                   S->M, S->Nmax, S->buf_bytes, S->grid, S->st, S->ws, S->ws_bytes);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    const lq_sim::PlanClass& pc = S->cls[k];
+    if (pc.n)
+      e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + pc.off, pc.n, S->d_queue, n_sweeps, measure, pc.M,
+                           pc.Nmax, pc.buf, pc.grid, S->st, S->ws, S->ws_bytes);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   return LQ_OK;
 }

@@ -263,51 +263,66 @@ static void admit(lq_server* S) {
   }
 }
 
-// One launch over every active request: each runs its remaining sweeps up to
-// the tick's time budget (at least one).
+// One launch over every active request of each plan class (at most
+// LQ_NS_SMALL particles per spin, then the larger ones): each request runs
+// its remaining sweeps up to its class's time budget (at least one).
 static void tick(lq_server* S) {
   const int n = (int)S->active.size();
   if (n == 0) return;
-  int M = 1, Nmax = 1, buf = 0;
   std::vector<LqChainDev> desc(n);
   std::vector<int> order(n), caps(n);
   std::vector<double> est(n);
+  std::vector<char> big(n);
   double target_ms;
   {
     std::lock_guard<std::mutex> g(S->mu);
     target_ms = S->tick_target_ms;
   }
-  long long budget_ns = std::max(1LL, (long long)(target_ms * 1e6));  // 0 would mean no budget in the kernel
   for (int k = 0; k < n; ++k) {
     const Active& a = S->active[k];
-    const lq_sim_launch_info inf = lq_internal_sim_info(a.sim);
     desc[k] = a.desc;
-    M = std::max(M, inf.M);
-    Nmax = std::max(Nmax, inf.Nmax);
-    buf = std::max(buf, inf.buf_bytes);
+    big[k] = std::max(a.desc.ns[0], a.desc.ns[1]) > LQ_NS_SMALL;
     est[k] = a.last_ns > 0 ? (double)a.last_ns : S->ns_per_cost * a.cost;
-    budget_ns = std::max(budget_ns, (long long)est[k]);
     order[k] = k;
   }
-  // longest first, so the persistent CTAs take the long chains before the short ones
+  // small class first, each longest first, so the persistent CTAs take the
+  // long chains before the short ones
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (big[x] != big[y]) return !big[x];
     return est[x] != est[y] ? est[x] > est[y] : S->active[x].cost > S->active[y].cost;
   });
   for (int q = 0; q < n; ++q) caps[q] = S->active[order[q]].n_sweeps - S->active[order[q]].done;
   cudaMemcpyAsync(S->d_slots, desc.data(), sizeof(LqChainDev) * n, cudaMemcpyHostToDevice, S->st);
   cudaMemcpyAsync(S->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->st);
   cudaMemcpyAsync(S->d_caps, caps.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->st);
-  const size_t smem = lq::smem_bytes(M, Nmax, buf);
-  const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, M, smem));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int grid = std::min(n, S->dev_sms * per_sm);
-  cudaError_t e = ensure_ws(S, (size_t)grid * lq::workspace_bytes(M, Nmax, buf));
   cudaEventRecord(e0, S->st);
-  if (e == cudaSuccess)
-    e = lq::launch_sweep(S->prec, S->d_slots, S->d_order, n, S->d_queue, 1, 1, M, Nmax, buf, grid, S->st, S->d_ws,
-                         S->ws_cap, S->d_caps, budget_ns);
+  cudaError_t e = cudaSuccess;
+  for (int cls = 0, q0 = 0; cls < 2 && e == cudaSuccess; ++cls) {
+    int q1 = q0;
+    int M = 1, Nmax = 1, buf = 0;
+    long long budget_ns = std::max(1LL, (long long)(target_ms * 1e6));  // 0 would mean no budget in the kernel
+    while (q1 < n && (int)big[order[q1]] == cls) {
+      const lq_sim_launch_info inf = lq_internal_sim_info(S->active[order[q1]].sim);
+      M = std::max(M, inf.M);
+      Nmax = std::max(Nmax, inf.Nmax);
+      buf = std::max(buf, inf.buf_bytes);
+      budget_ns = std::max(budget_ns, (long long)est[order[q1]]);
+      ++q1;
+    }
+    if (q1 > q0) {
+      const size_t smem = lq::smem_bytes(M, Nmax, buf);
+      const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, M, smem));
+      const int grid = std::min(q1 - q0, S->dev_sms * per_sm);
+      e = ensure_ws(S, (size_t)grid * lq::workspace_bytes(M, Nmax, buf));
+      if (e == cudaSuccess)
+        e = lq::launch_sweep(S->prec, S->d_slots, S->d_order + q0, q1 - q0, S->d_queue, 1, 1, M, Nmax, buf, grid, S->st,
+                             S->d_ws, S->ws_cap, S->d_caps + q0, budget_ns);
+    }
+    q0 = q1;
+  }
   cudaEventRecord(e1, S->st);
   cudaMemcpyAsync(desc.data(), S->d_slots, sizeof(LqChainDev) * n, cudaMemcpyDeviceToHost, S->st);
   cudaError_t e2 = cudaStreamSynchronize(S->st);

@@ -33,15 +33,17 @@ WORKLOADS = {
 }
 
 
-def flatband_batch(rng, n_chains, periodic_frac=0.5):
-    """Uneven flat-band chains: cells U[64, 512], filling U[1/4, 3/4] of the flat
-    band split evenly by spin, beta U[4, 40], dtau 0.05, U = 2."""
+def flatband_batch(rng, n_chains, periodic_frac=0.5, cells=(64, 512), beta_range=(4.0, 40.0)):
+    """Uneven flat-band chains: cells uniform in `cells` (U[64, 512] in the
+    paper-shaped workload), filling U[1/4, 3/4] of the flat band split evenly
+    by spin, beta uniform in beta_range (U[4, 40]), dtau 0.05, U = 2; half of
+    the chains periodic."""
     out = []
     for _ in range(n_chains):
-        nc = int(rng.integers(64, 513))
+        nc = int(rng.integers(cells[0], cells[1] + 1))
         f = rng.uniform(0.25, 0.75)
         ns = max(1, int(round(f * nc / 2)))
-        beta = float(np.round(rng.uniform(4.0, 40.0) / 0.05) * 0.05)
+        beta = float(np.round(rng.uniform(*beta_range) / 0.05) * 0.05)
         out.append(dict(lattice=("flatband", nc, 1.0, 1.0, 1.0, 1.0, bool(rng.random() < periodic_frac)), U=2.0,
                         beta=beta, dtau=0.05, n_up=ns, n_dn=ns, n_stab=8))
     return out

@@ -131,3 +131,24 @@ def test_grouping_of_sweeps_into_launches_does_not_change_results(lq):
     with pytest.raises(lq.LqError):
         srv.set_tick_target(-1.0)
     srv.close()
+
+
+def test_large_request_alone_and_in_mix(lq):
+    """A request with more than 32 particles per spin runs in its own launch
+    of each tick (the large plan) beside small requests: same result alone
+    and in the mix."""
+    lat = lq.Lattice.chain(96)
+    params = dict(U=4.0, beta=0.6, dtau=0.1, n_up=40, n_dn=33, n_stab=3, seed=17, precision=0)
+    srv = lq.Server(hbm_budget=1 << 30)
+    rid = srv.submit(lat, params, 3, chain_id=5)
+    ra = wait(srv, [rid])[rid]
+    srv.close()
+    srv = lq.Server(hbm_budget=1 << 30)
+    ids = [srv.submit(L, dict(p, precision=0), ns, chain_id=cid) for L, p, ns, cid in request_mix(lq)]
+    rid2 = srv.submit(lat, params, 3, chain_id=5)
+    res = wait(srv, ids + [rid2])
+    srv.close()
+    rb = res[rid2]
+    assert ra["status"] == 0 and rb["status"] == 0 and all(r["status"] == 0 for r in res.values())
+    assert np.array_equal(ra["counts"], rb["counts"])
+    assert np.max(np.abs(ra["obs_mean"] - rb["obs_mean"])) < 1e-10
