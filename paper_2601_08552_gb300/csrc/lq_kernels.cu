@@ -32,14 +32,18 @@ namespace lq {
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct SmemPlan {
-  int M, MP, Nmax, buf_bytes, big;
-  // offsets of T0, T1, W and S are in shared memory for small plans and in
-  // the CTA's slab of the global workspace for big ones (M > LQ_NS_SMALL)
+  int M, MP, Nmax, buf_bytes, big, s_global;
+  // offsets of T0, T1 and W are in shared memory for small plans and in the
+  // CTA's slab of the global workspace for big ones (M > LQ_NS_SMALL); the
+  // four scratch matrices S stay in shared memory while they fit there
   size_t off_T0, off_T1, off_W, off_S, off_vec, off_red, off_obs, off_gx, off_ip, off_occ, off_bits, off_chain, off_win,
       off_buf, total;
   size_t ws_cta;  // global workspace bytes per CTA (0 for small plans)
   char* ws;       // the launch's workspace, grid x ws_cta bytes (set by the launcher)
 };
+
+// largest dynamic shared memory a plan may take (the opt-in limit is 227 KB)
+#define LQ_SMEM_CAP (220 * 1024)
 
 __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
   SmemPlan p;
@@ -49,14 +53,12 @@ __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
   p.buf_bytes = buf_bytes;
   p.big = p.M > LQ_NS_SMALL;
   p.ws = nullptr;
-  size_t mat = (size_t)p.M * p.MP * 8;
+  const size_t mat = (size_t)p.M * p.MP * 8;
   size_t o = 0, g = 0;
-  size_t& om = p.big ? g : o;  // where the m x m matrices go
+  size_t& om = p.big ? g : o;  // where T and the Gauss-Jordan workspace go
   p.off_T0 = om; om = al16(om + mat);
   p.off_T1 = om; om = al16(om + mat);
   p.off_W = om; om = al16(om + (size_t)p.M * 2 * p.MP * 8);  // Gauss-Jordan / Gram workspace
-  p.off_S = om; om = al16(om + 6 * mat);                       // six small matrices
-  p.ws_cta = p.big ? ((g + 255) & ~(size_t)255) : 0;
   p.off_vec = o; o = al16(o + (size_t)10 * p.M * 8);
   p.off_red = o; o = al16(o + 64 * 8);
   p.off_obs = o; o = al16(o + 16 * 8);
@@ -67,6 +69,12 @@ __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
   p.off_chain = o; o = al16(o + sizeof(LqChainDev));
   p.off_win = o; o = al16(o + (size_t)2 * LQ_WIN_ELEMS(p.MP) * 8);
   p.off_buf = o; o = al16(o + (size_t)buf_bytes);
+  // four scratch matrices (swap, QR and measurement work): shared memory
+  // unless a big plan runs out of it
+  p.s_global = p.big && o + 4 * mat > LQ_SMEM_CAP;
+  size_t& os = p.s_global ? g : o;
+  p.off_S = os; os = al16(os + 4 * mat);
+  p.ws_cta = p.big ? ((g + 255) & ~(size_t)255) : 0;
   p.total = o;
   return p;
 }
@@ -109,7 +117,7 @@ __device__ inline Smem carve(const SmemPlan& p, char* base) {
   s.T[0] = (double*)(mb + p.off_T0);
   s.T[1] = (double*)(mb + p.off_T1);
   s.W = (double*)(mb + p.off_W);
-  s.S = (double*)(mb + p.off_S);
+  s.S = (double*)((p.s_global ? mb : base) + p.off_S);
   s.vec = (double*)(base + p.off_vec);
   s.red = (double*)(base + p.off_red);
   s.obs = (double*)(base + p.off_obs);
@@ -938,6 +946,47 @@ __device__ __forceinline__ void bar_group(int sg) { asm volatile("bar.sync %0, 1
 // the serial per-site chain (ratio, the two spins' exchange, the K x K
 // block's rank-1 updates) runs on the group's first warp, as in the small path.
 // ---------------------------------------------------------------------------
+// x_t = R_t T and y_t = T L_t for the KT window sites tlo.. (KT a compile-time
+// count, so no FP64 instruction issues for a site the thread does not own):
+// the calling thread owns column b of X (T column b) and row b of T.
+template <class Ops, int KT>
+__device__ __forceinline__ void window_xy(const typename Ops::TRef& T, const typename Ops::Row* rbase,
+                                          const typename Ops::Row* lbase, typename Ops::V* Xw, typename Ops::V* Yw,
+                                          int t0, int tlo, int kw, int m, int MP, int b0, int bstep) {
+  typedef typename Ops::V V;
+  const int nt = min(KT, kw - tlo);
+  if (nt <= 0) return;
+  for (int b = b0; b < m; b += bstep) {
+    V xa[KT], ya[KT];
+#pragma unroll
+    for (int t = 0; t < KT; ++t) { xa[t] = Ops::zero(); ya[t] = Ops::zero(); }
+    if (nt == KT) {
+      for (int a = 0; a < m; ++a) {
+        const V tc = T.ld(a * MP + b), tr = T.ld(b * MP + a);
+#pragma unroll
+        for (int t = 0; t < KT; ++t) {
+          Ops::acc(xa[t], rbase[(size_t)(t0 + tlo + t) * MP + a], tc);
+          Ops::accT(ya[t], tr, lbase[(size_t)(t0 + tlo + t) * MP + a]);
+        }
+      }
+    } else {  // ragged last window of a chunk
+      for (int a = 0; a < m; ++a) {
+        const V tc = T.ld(a * MP + b), tr = T.ld(b * MP + a);
+        for (int t = 0; t < nt; ++t) {
+          Ops::acc(xa[t], rbase[(size_t)(t0 + tlo + t) * MP + a], tc);
+          Ops::accT(ya[t], tr, lbase[(size_t)(t0 + tlo + t) * MP + a]);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < KT; ++t)
+      if (t < nt) {
+        Xw[(tlo + t) * MP + b] = Ops::finish(xa[t]);
+        Yw[(tlo + t) * MP + b] = Ops::finish(ya[t]);
+      }
+  }
+}
+
 template <class R, class Ops>
 __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag,
                                Smem& sm) {
@@ -999,45 +1048,33 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
       int wsign = 1, nacc = 0, nbad = 0;
       for (int t0 = 0; t0 < cn; t0 += K) {
         const int kw = min(K, cn - t0);
-        // x_t = R_t T: thread owns column b
-        for (int b = gt; b < m; b += 128) {
-          V xa[K];
-#pragma unroll
-          for (int t = 0; t < K; ++t) xa[t] = Ops::zero();
-          for (int a = 0; a < m; ++a) {
-            const V tv = T.ld(a * MP + b);
-#pragma unroll
-            for (int t = 0; t < K; ++t)
-              if (t < kw) Ops::acc(xa[t], rbase[(size_t)(t0 + t) * MP + a], tv);
-          }
-#pragma unroll
-          for (int t = 0; t < K; ++t)
-            if (t < kw) Xw[t * MP + b] = Ops::finish(xa[t]);
-        }
-        // y_t = T L_t: thread owns row b of T
-        for (int b = gt; b < m; b += 128) {
-          V ya[K];
-#pragma unroll
-          for (int t = 0; t < K; ++t) ya[t] = Ops::zero();
-          for (int a = 0; a < m; ++a) {
-            const V tv = T.ld(b * MP + a);
-#pragma unroll
-            for (int t = 0; t < K; ++t)
-              if (t < kw) Ops::accT(ya[t], tv, lbase[(size_t)(t0 + t) * MP + a]);
-          }
-#pragma unroll
-          for (int t = 0; t < K; ++t)
-            if (t < kw) Yw[t * MP + b] = Ops::finish(ya[t]);
-        }
+        // x_t = R_t T (thread owns column b) and y_t = T L_t (thread owns row b
+        // of T).  With m <= 64 the group's two halves take the window's first
+        // and last K/2 sites, so every thread works.
+        const int TG = m <= 64 ? 2 : 1, KT = K / TG;
+        const int bstep = 128 / TG, tg = gt / bstep, tlo = tg * KT;
+        if (TG == 2)
+          window_xy<Ops, K / 2>(T, rbase, lbase, Xw, Yw, t0, tlo, kw, m, MP, gt % bstep, bstep);
+        else
+          window_xy<Ops, K>(T, rbase, lbase, Xw, Yw, t0, tlo, kw, m, MP, gt % bstep, bstep);
         bar_group(sg);
-        // G[u][v] = x_u . L_v
+        // G[u][v] = x_u . L_v (four partial sums: the m-long chain is latency bound)
         if (gt < K * K) {
           const int u = gt / K, v = gt % K;
           if (u < kw && v < kw) {
             const Row* lr = lbase + (size_t)(t0 + v) * MP;
-            V ga = Ops::zero();
-            for (int b = 0; b < m; ++b) Ops::accT(ga, Xw[u * MP + b], lr[b]);
-            Gw[u * KP + v] = Ops::finish(ga);
+            const V* xr = Xw + u * MP;
+            V g0 = Ops::zero(), g1 = Ops::zero(), g2 = Ops::zero(), g3 = Ops::zero();
+            int b = 0;
+            for (; b + 3 < m; b += 4) {
+              Ops::accT(g0, xr[b], lr[b]);
+              Ops::accT(g1, xr[b + 1], lr[b + 1]);
+              Ops::accT(g2, xr[b + 2], lr[b + 2]);
+              Ops::accT(g3, xr[b + 3], lr[b + 3]);
+            }
+            for (; b < m; ++b) Ops::accT(g0, xr[b], lr[b]);
+            Gw[u * KP + v] = Ops::add(Ops::add(Ops::finish(g0), Ops::finish(g1)),
+                                      Ops::add(Ops::finish(g2), Ops::finish(g3)));
           }
         }
         bar_group(sg);
@@ -1083,40 +1120,48 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
         }
         bar_group(sg);
         // x_j, y_j at their flip times (column t and row t of G are frozen
-        // once site t is done); y is stored scaled by c_j for the T update
-        for (int b = gt; b < m; b += 128) {
-          V xb[K], yb[K];
+        // once site t is done); y is stored scaled by c_j for the T update.
+        // A thread owns column b of X and of Y (with m <= 64 one half of the
+        // group takes X, the other Y).
+        for (int b = gt % bstep; b < m; b += bstep) {
 #pragma unroll
-          for (int t = 0; t < K; ++t)
-            if (t < kw) { xb[t] = Xw[t * MP + b]; yb[t] = Yw[t * MP + b]; }
-#pragma unroll
-          for (int t = 0; t < K - 1; ++t) {
-            if (t + 1 < kw) {
-              const V ct = cw[t];
-#pragma unroll
-              for (int j = t + 1; j < K; ++j)
-                if (j < kw) {
-                  xb[j] = Ops::fnma(Ops::mul(ct, Gw[j * KP + t]), xb[t], xb[j]);
-                  yb[j] = Ops::fnma(Ops::mul(ct, Gw[t * KP + j]), yb[t], yb[j]);
-                }
-            }
-          }
-#pragma unroll
-          for (int t = 0; t < K; ++t)
-            if (t < kw) { Xw[t * MP + b] = xb[t]; Yw[t * MP + b] = Ops::mul(cw[t], yb[t]); }
-        }
-        bar_group(sg);
-        // T <- T - sum_t (c_t y_t) x_t^T: thread owns column b
-        for (int b = gt; b < m; b += 128) {
-          V xb[K];
-#pragma unroll
-          for (int t = 0; t < K; ++t) xb[t] = (t < kw) ? Xw[t * MP + b] : Ops::zero();
-          for (int a = 0; a < m; ++a) {
-            V tv = T.ld(a * MP + b);
+          for (int xy = 0; xy < 2; ++xy) {
+            if (TG == 2 && xy != tg) continue;
+            V* Wm = xy ? Yw : Xw;
+            V v[K];
 #pragma unroll
             for (int t = 0; t < K; ++t)
-              if (t < kw) tv = Ops::fnma(Yw[t * MP + a], xb[t], tv);
-            T.st(a * MP + b, tv);
+              if (t < kw) v[t] = Wm[t * MP + b];
+#pragma unroll
+            for (int t = 0; t < K - 1; ++t) {
+              if (t + 1 < kw) {
+                const V ct = cw[t];
+#pragma unroll
+                for (int j = t + 1; j < K; ++j)
+                  if (j < kw) v[j] = Ops::fnma(Ops::mul(ct, xy ? Gw[t * KP + j] : Gw[j * KP + t]), v[t], v[j]);
+              }
+            }
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+              if (t < kw) Wm[t * MP + b] = xy ? Ops::mul(cw[t], v[t]) : v[t];
+          }
+        }
+        bar_group(sg);
+        // T <- T - sum_t (c_t y_t) x_t^T: thread owns column b (with m <= 64,
+        // one half of the rows each)
+        {
+          const int ah = (m + TG - 1) / TG, alo = tg * ah, ahi = min(m, alo + ah);
+          for (int b = gt % bstep; b < m; b += bstep) {
+            V xb[K];
+#pragma unroll
+            for (int t = 0; t < K; ++t) xb[t] = (t < kw) ? Xw[t * MP + b] : Ops::zero();
+            for (int a = alo; a < ahi; ++a) {
+              V tv = T.ld(a * MP + b);
+#pragma unroll
+              for (int t = 0; t < K; ++t)
+                if (t < kw) tv = Ops::fnma(Yw[t * MP + a], xb[t], tv);
+              T.st(a * MP + b, tv);
+            }
           }
         }
         bar_group(sg);
@@ -1331,7 +1376,7 @@ template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
   const R* QRb[2];
   double* A[2];
   int sgn = 1;
-  double* Ms = sm.S;  // Ms + k*M*MP, k = 0..5
+  double* Ms = sm.S;  // Ms + k*M*MP, k = 0..3
   for (int sg = 0; sg < 2; ++sg) {
     const int m = C.ns[sg];
     QLb[sg] = ql_panel<R>(C, sg, jb);
