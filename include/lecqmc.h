@@ -198,7 +198,9 @@ lq_status lq_sim_clear_records(lq_sim* sim);
 lq_status lq_sim_stats(lq_sim* sim, int32_t chain, int64_t* host_counts4);
 /* SM cycles chain c spent, summed over its sweeps, per phase: field flips,
  * slice propagation, QR restabilization, block-start Gram and inverse,
- * particle-hole swaps, measurement, and two unused slots (host array of 8). */
+ * particle-hole swaps, measurement; then two parts of the swap cycles: the
+ * removal (Givens rotations, M^-1, downdate, rotated Q panels) and the
+ * addition (vector propagation and Gram-Schmidt) (host array of 8). */
 lq_status lq_sim_profile(lq_sim* sim, int32_t chain, int64_t* host_cycles8);
 /* Test hook: panel j of the right (side 0) or left (side 1) chain of a spin,
  * as FP64 host arrays Q (N x N_sigma) and V (N_sigma x N_sigma, nullable). */

@@ -80,7 +80,8 @@ struct LqChainDev {
   int err;
   long long cnt[4];         // field attempts, field accepts, swap attempts, swap accepts
   double hook[8];           // test-hook outputs
-  long long prof[8];        // cycles per phase: flips, propagation, QR, block inverse, swaps, measurement
+  long long prof[8];        // cycles per phase: flips, propagation, QR, block inverse, swaps, measurement;
+                            // then two parts of the swaps: removal (with Q streaming), addition
   long long sweep_ns_last;  // wall time of the chain's most recent sweep (device global timer)
   long long sweep_ns_sum;   // summed wall time of its sweeps (the caller may reset it)
 };

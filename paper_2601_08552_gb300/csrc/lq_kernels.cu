@@ -1544,6 +1544,8 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
   int* occr = sm.occ2;               // reduced column order (sites), then the new order
   const int* occ = C.occ[sg];
   double* rot = C.rot;
+  // sub-phase cycles of the swap (thread 0): removal into prof[6], addition into prof[7]
+  long long tsub = (TID == 0) ? clock64() : 0;
   // --- removal: retriangulate V_i U (i = 1) and V_i G_{i-1}^T (i > 1) -----
   if (warp == 0) {
     double logrN = 0.0;
@@ -1647,6 +1649,11 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     }
   }
   __syncthreads();
+  if (TID == 0) {
+    const long long t1 = clock64();
+    C.prof[6] += t1 - tsub;
+    tsub = t1;
+  }
   // --- addition of site j on the reduced chain ------------------------------
   double* q = C.vec;
   double* w = C.vec + N;
@@ -1687,6 +1694,7 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     logrho += log(rho);
     __syncthreads();
   }
+  if (TID == 0) C.prof[7] += clock64() - tsub;
   // --- Schur complement s (Eq. S7), ratio, Metropolis, commit ---------------
   if (warp == 0) {
     const R* Qn = qr_panel<R>(C, sg, tb, n);
