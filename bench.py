@@ -430,7 +430,7 @@ def main():
     achieved = flops / (kern_ms * 1e-3) / 1e12
     roofline = dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
                     frac=achieved / FP64_PEAK_TFLOPS, traffic=profiled_traffic("fp64_bytes_per_launch"),
-                    kernel="lq::sweep_kernel<double>", flops_per_launch=flops,
+                    kernel="lq::sweep_kernel<double, false>", flops_per_launch=flops,
                     peak_source="GB300 dense FP64 1.25 TFLOP/s (pool recipe table); 1.19 measured by FMA loop")
 
     # end to end through the C ABI on pinned host buffers
