@@ -293,7 +293,7 @@ def aggregate_rate(world, units_per_rank_step, steps, max_ms):
     return world * units_per_rank_step * steps / (max_ms * 1e-3)
 
 
-def uneven_leg(lq, inputs, torch, stream, prec=0, n_chains=608, steps=2, warmup=1):
+def uneven_leg(lq, inputs, torch, stream, prec=0, n_chains=608, steps=2, warmup=1, autotune=True):
     """Hundreds of flat-band chains of uneven N, N_sigma and beta advancing in
     one persistent launch per plan class.  The paper-shaped batch (cells
     U[64, 512], beta U[4, 40]) costs minutes per sweep, so the leg draws
@@ -306,6 +306,7 @@ def uneven_leg(lq, inputs, torch, stream, prec=0, n_chains=608, steps=2, warmup=
                    seed=inputs.SEED0) for sp in specs]
     sim = lq.Sim(lats, params, stream=stream.cuda_stream)
     sim.init()
+    bufs = sim.autotune(1 if autotune else 0)
     for _ in range(warmup):
         sim.sweep(1, measure=True)
     per = time_steps(torch, sim, steps, stream)
@@ -316,7 +317,7 @@ def uneven_leg(lq, inputs, torch, stream, prec=0, n_chains=608, steps=2, warmup=
     return dict(chains=n_chains, value=upd * steps / (sum(per) * 1e-3), unit=UNIT,
                 sweeps_per_s=n_chains * steps / (sum(per) * 1e-3), ms_per_sweep=float(np.mean(per)),
                 n_sigma_range=[int(ns.min()), int(ns.max())], chains_above_32=int((ns > 32).sum()),
-                N_range=[int(Ns.min()), int(Ns.max())], precision="FP64",
+                N_range=[int(Ns.min()), int(Ns.max())], precision="FP64", staging_bytes_per_class=list(bufs),
                 mix="BCL flat-band chains, cells U[16, 128], filling U[1/4, 3/4] of the flat band split by spin, "
                     "beta U[1, 4], dtau 0.05, U=2, half periodic")
 
@@ -344,6 +345,7 @@ def main():
     ap.add_argument("--chains", type=int, default=0, help="override the chain count (small profiling cases)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-window", type=float, default=10.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=["gas32x32", "gas64x64"],
                     help="gas64x64: the 64x64 mixed-precision comparison (512 chains, ~10 s per sweep)")
@@ -398,6 +400,8 @@ def main():
         # log-weights of the first chains on their seeded initial fields (identical across precisions)
         lw0 = np.array([sim.log_weight(c)[0] for c in range(min(8, n_chains))])
         run.lw0[prec] = lw0
+        # the autotuner's timed candidates are ordinary (unmeasured) sweeps: part of the warm-up
+        run.tuned[prec] = sim.autotune(0 if args.no_autotune else 1)
         for _ in range(args.warmup):
             sim.sweep(1, measure=True)
         sim.sync()
@@ -422,6 +426,7 @@ def main():
         return sim, per, total_ms, clocks, d, phases
 
     run.lw0 = {}
+    run.tuned = {}
     sim, per, total_ms, clocks, dstat, phases = run(0)
     value = aggregate_rate(world, upd_per_step, args.steps, total_ms)
     sweeps = world * n_chains * args.steps / (total_ms * 1e-3)
@@ -496,7 +501,7 @@ def main():
 
     uneven = None
     if not args.no_uneven and args.workload == WORKLOAD:
-        uneven = uneven_leg(lq, inputs, torch, stream)
+        uneven = uneven_leg(lq, inputs, torch, stream, autotune=not args.no_autotune)
 
     serving = None
     if not args.no_serving and world == 1 and args.workload == WORKLOAD:
@@ -509,6 +514,9 @@ def main():
                     config=dict(workload=workload_desc(spec, n_chains), chains_per_gpu=n_chains, N=N, L=L,
                                 n_up=spec["n_up"], n_dn=spec["n_dn"], n_stab=spec["n_stab"], U=spec["U"],
                                 l2="device state %.1f GB per GPU >> 129 MB L2; no flush" % (bytes_dev / 1e9),
+                                staging_bytes=run.tuned.get(0, (0, 0))[0],
+                                autotune="staging buffer picked by lq_sim_autotune (1 sweep per candidate, warm-up)"
+                                if not args.no_autotune else "off",
                                 parallelism="independent chains, %d per GPU" % n_chains),
                     sweeps_per_s=sweeps, p50_ms=float(np.percentile(per, 50)), p99_ms=float(np.percentile(per, 99)),
                     field_accept=float(dstat[1] / max(dstat[0], 1)),

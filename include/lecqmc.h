@@ -166,6 +166,20 @@ lq_status lq_sim_set_sweep_index(lq_sim* sim, uint32_t sweep);
  * chain, longest chains first).  measure != 0 appends one record per sweep.
  * Asynchronous on the stream. */
 lq_status lq_sim_sweep(lq_sim* sim, int32_t n_sweeps, int32_t measure);
+/* Autotune the batched launch (build-side tuning, no counterpart in the
+ * paper).  A sweep runs one persistent launch per plan class: the chains with
+ * at most 32 particles per spin, then the larger ones.  For each class this
+ * times sweeps_per_candidate sweeps (without measurement) under each feasible
+ * size of the shared-memory staging buffer, which sets the propagation's
+ * column chunks, the flip loop's chunk of sites and the CTAs per SM, and keeps
+ * the fastest for later sweeps.  The timed sweeps are ordinary sweeps of the
+ * chains of that class (they advance its chains; use them as warm-up), so a
+ * class's chains advance by sweeps_per_candidate times the number of
+ * candidates tried.  Choices are cached per (precision, class, N_sigma, N,
+ * chain-count bucket) for the process; with sweeps_per_candidate = 0 only a
+ * cached choice is applied.  host_buf2 (nullable) receives the staging bytes
+ * chosen for the two classes (0 for an empty class).  Synchronous. */
+lq_status lq_sim_autotune(lq_sim* sim, int32_t sweeps_per_candidate, int32_t* host_buf2);
 /* One stateless batch call on host buffers: upload every chain's fields
  * (host_fields: chains concatenated, each L x N) and Fock state (host_occ:
  * each chain's n_up then n_dn sites), rebuild the QR chains, run n_sweeps

@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -649,6 +652,100 @@ extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) 
                            pc.Nmax, pc.buf, pc.grid, S->st, S->ws, S->ws_bytes);
   }
   if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+  return LQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the batched launch: per plan class, the shared-memory staging
+// buffer (it sets the propagation's column chunks, the flip loop's chunk of
+// sites, and through the shared memory per CTA the CTAs per SM).  Candidates
+// are timed on real sweeps of that class (without measurement), and the
+// choice is cached per (precision, class, N_sigma, N, chain-count bucket).
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
+int chain_bucket(int n) {
+  int b = 0;
+  while ((1 << b) < n) ++b;
+  return b;
+}
+}  // namespace
+
+extern "C" lq_status lq_sim_autotune(lq_sim* S, int32_t sweeps_per_candidate, int32_t* host_buf2) {
+  if (!S || sweeps_per_candidate < 0) return fail(LQ_EINVAL, "bad arguments to lq_sim_autotune");
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  S->mirror_fresh = false;
+  for (int k = 0; k < 2; ++k) {
+    lq_sim::PlanClass& pc = S->cls[k];
+    if (host_buf2) host_buf2[k] = pc.n ? pc.buf : 0;
+    if (!pc.n) continue;
+    const auto key = std::make_tuple(S->prec, k, pc.M, pc.Nmax, chain_bucket(pc.n));
+    const int need = lq::staging_min_bytes(pc.M, pc.Nmax);
+    // a feasible (grid, fits) for a candidate buffer
+    auto feasible = [&](int buf, int* grid) {
+      if (buf < need) return false;
+      const size_t smem = lq::smem_bytes(pc.M, pc.Nmax, buf);
+      if (smem > 227 * 1024) return false;
+      const int per_sm = lq::max_active_sweep_ctas(S->prec, pc.M, smem);
+      if (per_sm < 1) return false;
+      *grid = std::min(pc.n, sms * per_sm);
+      return (size_t)(*grid) * lq::workspace_bytes(pc.M, pc.Nmax, buf) <= S->ws_bytes;
+    };
+    {
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      int grid = 0;
+      if (it != g_tune_cache.end() && feasible(it->second, &grid)) {
+        pc.buf = it->second;
+        pc.grid = grid;
+        if (host_buf2) host_buf2[k] = pc.buf;
+        continue;
+      }
+    }
+    if (sweeps_per_candidate == 0) continue;
+    std::vector<int> cand = {pc.buf, 32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024, 128 * 1024, 160 * 1024, 200 * 1024};
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    int best_buf = pc.buf, best_grid = pc.grid;
+    bool have = false;
+    for (int buf : cand) {
+      int grid = 0;
+      if (!feasible(buf, &grid)) continue;
+      cudaError_t e = cudaEventRecord(e0, S->st);
+      if (e == cudaSuccess)
+        e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + pc.off, pc.n, S->d_queue, sweeps_per_candidate, 0,
+                             pc.M, pc.Nmax, buf, grid, S->st, S->ws, S->ws_bytes);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, S->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e, "autotune sweep");
+      }
+      if (!have || ms < best_ms) {
+        best_ms = ms;
+        best_buf = buf;
+        best_grid = grid;
+        have = true;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pc.buf = best_buf;
+    pc.grid = best_grid;
+    if (host_buf2) host_buf2[k] = pc.buf;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = pc.buf;
+  }
   return LQ_OK;
 }
 

@@ -81,6 +81,18 @@ __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
 
 size_t smem_bytes(int M, int Nmax, int buf_bytes) { return plan_smem(M, Nmax, buf_bytes).total; }
 size_t workspace_bytes(int M, int Nmax, int buf_bytes) { return plan_smem(M, Nmax, buf_bytes).ws_cta; }
+int staging_min_bytes(int M, int Nmax) {
+  // one panel column (N values) for the propagation; for big plans one window
+  // of sites for the flip staging
+  const int MP = (M < 1 ? 1 : M) | 1;
+  size_t b = (size_t)Nmax * 8;
+  if (b < 16 * 1024) b = 16 * 1024;
+  if (M > LQ_NS_SMALL) {
+    const size_t w = (size_t)LQ_WIN * (4 * (size_t)MP * 8 + 32);
+    if (b < w) b = w;
+  }
+  return (int)b;
+}
 int staging_bytes(int M, int Nmax) {
   // propagation needs one panel column (N values); the flip staging of the
   // big path needs at least one window of sites (four rows of MP per site)

@@ -13,6 +13,7 @@ namespace lq {
 size_t smem_bytes(int M, int Nmax, int buf_bytes);
 size_t workspace_bytes(int M, int Nmax, int buf_bytes);
 int staging_bytes(int M, int Nmax);
+int staging_min_bytes(int M, int Nmax);  // the smallest staging buffer a plan can run with
 cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
                          int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st, void* ws,
                          size_t ws_bytes, const int* caps = nullptr, long long budget_ns = 0);

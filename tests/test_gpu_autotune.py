@@ -1,0 +1,82 @@
+"""Autotuner of the batched launch (lq_sim_autotune).
+
+The tuner times real sweeps under candidate staging-buffer sizes and keeps
+the fastest.  The staging size changes only how work is chunked, so after
+tuning every chain still follows the oracle's trajectory: the tuning sweeps
+are ordinary sweeps of the chains of each plan class."""
+import numpy as np
+import pytest
+
+from oracle import OracleSim, lattices
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [
+    dict(lattice=("square", 4, 4), U=4.0, beta=0.8, dtau=0.1, n_up=3, n_dn=2, n_stab=4),
+    dict(lattice=("chain", 96), U=4.0, beta=0.4, dtau=0.1, n_up=40, n_dn=33, n_stab=2),
+    dict(lattice=("flatband", 10), U=2.0, beta=0.6, dtau=0.1, n_up=4, n_dn=4, n_stab=3),
+]
+
+
+@pytest.fixture(scope="module")
+def lq():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2601_08552_gb300 as p
+
+    p.load()
+    return p
+
+
+def build(lq, seed):
+    lats, params, oracles = [], [], []
+    for c, spec in enumerate(SPECS):
+        lat = getattr(lattices, spec["lattice"][0])(*spec["lattice"][1:])
+        oracles.append(OracleSim(lat, spec["U"], spec["beta"], spec["dtau"], spec["n_up"], spec["n_dn"],
+                                 spec["n_stab"], seed=seed, chain=c))
+        lats.append(getattr(lq.Lattice, spec["lattice"][0])(*spec["lattice"][1:]))
+        params.append(dict(spec, precision=0, seed=seed))
+    sim = lq.Sim(lats, params)
+    sim.init()
+    return sim, oracles
+
+
+def test_autotune_keeps_the_trajectory(lq):
+    sim, oracles = build(lq, 31)
+    bufs = sim.autotune(1)
+    assert bufs[0] > 0 and bufs[1] > 0
+    sim.sync()
+    for c, o in enumerate(oracles):
+        L, N = o.L, o.N
+        done = int(sim.stats(c)[0]) // (2 * L * N)  # field attempts -> sweeps the tuner ran
+        assert done >= 1
+        o.sweep(done)
+        assert np.array_equal(sim.get_fields(c), o.get_fields())
+        assert np.array_equal(sim.stats(c), o.stats())
+    sim.sweep(2)
+    sim.sync()
+    for c, o in enumerate(oracles):
+        o.sweep(2)
+        assert np.array_equal(sim.get_fields(c), o.get_fields())
+        assert np.array_equal(sim.stats(c), o.stats())
+        lt, st = sim.tracked_weight(c)
+        lo, so = o.tracked()
+        assert st == so and abs(lt - lo) < 1e-9 * max(1.0, abs(lo))
+        rg = sim.records(c)
+        ro = o.records()[-2:]
+        assert np.max(np.abs(rg - ro)) < 1e-10 * max(1.0, float(np.max(np.abs(ro))))
+
+
+def test_autotune_cache(lq):
+    sim, _ = build(lq, 32)
+    first = sim.autotune(1)
+    sim2, _ = build(lq, 33)
+    sim2.sync()
+    before = sim2.stats(0).copy()
+    again = sim2.autotune(0)  # cached: applies the choice without sweeping
+    sim2.sync()
+    assert again == first
+    assert np.array_equal(sim2.stats(0), before)
+    with pytest.raises(lq.LqError):
+        sim2.autotune(-1)
