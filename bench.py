@@ -322,6 +322,22 @@ def uneven_leg(lq, inputs, torch, stream, prec=0, n_chains=608, steps=2, warmup=
                     "beta U[1, 4], dtau 0.05, U=2, half periodic")
 
 
+def observable_deviation(a, b):
+    """Chain-mean observables of two runs from the same seeded states: the
+    largest |difference| over the measured observables in units of the
+    combined standard error across chains (the FP64 run as reference)."""
+    from paper_2601_08552_gb300 import OBS_NAMES
+
+    ma, mb = a.mean(axis=0), b.mean(axis=0)
+    se = np.sqrt(a.var(axis=0, ddof=1) / len(a) + b.var(axis=0, ddof=1) / len(b))
+    dev = {}
+    for k, name in enumerate(OBS_NAMES):
+        if se[k] > 0:
+            dev[name] = float(abs(ma[k] - mb[k]) / se[k])
+    return dict(max_sigma=max(dev.values()) if dev else 0.0, sigma=dev,
+                max_rel=float(np.max(np.abs(ma - mb) / np.maximum(np.abs(mb), 1e-300))))
+
+
 def time_steps(torch, sim, steps, stream):
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     evs[0].record(stream)
@@ -423,10 +439,13 @@ def main():
         tot = max(float(pr[:6].sum()), 1.0)
         phases = {k: round(float(pr[i]) / tot, 4) for i, k in
                   enumerate(["flips", "propagation", "qr", "block_inverse", "swaps", "measure"])}
+        # per-chain means of the measured observables (warm-up and timed sweeps)
+        run.obs[(prec, sp is spec)] = np.stack([sim.records(c).mean(axis=0) for c in range(n_chains)])
         return sim, per, total_ms, clocks, d, phases
 
     run.lw0 = {}
     run.tuned = {}
+    run.obs = {}
     sim, per, total_ms, clocks, dstat, phases = run(0)
     value = aggregate_rate(world, upd_per_step, args.steps, total_ms)
     sweeps = world * n_chains * args.steps / (total_ms * 1e-3)
@@ -483,6 +502,7 @@ def main():
             d["speedup_vs_fp64"] = d["value"] / value
             d["logw_max_rel_err_vs_fp64"] = float(np.max(np.abs(run.lw0[prec] - run.lw0[0]) /
                                                          np.maximum(1.0, np.abs(run.lw0[0]))))
+            d["observables_vs_fp64"] = observable_deviation(run.obs[(prec, True)], run.obs[(0, True)])
             mixed[key] = d
             msim.close()
 
