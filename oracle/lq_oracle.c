@@ -115,6 +115,12 @@ typedef struct {
   int want_corr;
   double *corr_nn, *corr_ss;
   long long ncorr;
+  /* Fock-swap proposal: 0 uniform over empty sites, 1 empty nearest neighbour
+   * of the removed particle's site (neighbours = distinct bond partners,
+   * ascending, in nb_off / nb_site), 2 as 1 without the Hastings factor (a
+   * deliberately wrong sampler for the tests) */
+  int swap_mode;
+  int *nb_off, *nb_site;
 } orc_sim;
 
 static double* dalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
@@ -360,6 +366,22 @@ orc_sim* orc_create(int N, int nb, const int* bi, const int* bj, const double* k
     S->QL[sg] = dalloc((S->n + 1) * panel(S, sg));
     S->VL[sg] = dalloc((S->n + 1) * sq(S, sg));
   }
+  /* neighbour lists: each site's distinct bond partners, ascending */
+  S->nb_off = (int*)calloc(N + 1, sizeof(int));
+  S->nb_site = (int*)calloc(2 * (size_t)(nb ? nb : 1), sizeof(int));
+  {
+    char* seen = (char*)calloc(N, 1);
+    for (int i = 0; i < N; ++i) {
+      S->nb_off[i + 1] = S->nb_off[i];
+      for (int b = 0; b < nb; ++b) {
+        int o = bi[b] == i ? bj[b] : (bj[b] == i ? bi[b] : -1);
+        if (o >= 0 && o != i) seen[o] = 1;
+      }
+      for (int o = 0; o < N; ++o)
+        if (seen[o]) { S->nb_site[S->nb_off[i + 1]++] = o; seen[o] = 0; }
+    }
+    free(seen);
+  }
   S->max_records = max_records;
   S->records = dalloc((size_t)(max_records > 0 ? max_records : 1) * NOBS);
   S->want_corr = want_corr;
@@ -370,6 +392,7 @@ orc_sim* orc_create(int N, int nb, const int* bi, const int* bj, const double* k
 void orc_destroy(orc_sim* S) {
   if (!S) return;
   free(S->bi); free(S->bj); free(S->kb); free(S->eps); free(S->sub); free(S->fam_of);
+  free(S->nb_off); free(S->nb_site);
   free(S->bc); free(S->bs); free(S->ceps); free(S->bnd); free(S->s);
   for (int sg = 0; sg < 2; ++sg) { free(S->occ[sg]); free(S->QR[sg]); free(S->VR[sg]); free(S->QL[sg]); free(S->VL[sg]); }
   free(S->records); free(S->corr_nn); free(S->corr_ss);
@@ -1061,13 +1084,43 @@ static void swap_phase(orc_sim* S) {
       ctr[3] = 1u;
       orc_philox(ctr, S->key, w2);
       int k = (int)(u53(w[0], w[1]) * (double)m);
-      int jidx = (int)(u53(w[2], w[3]) * (double)(S->N - m));
       double u = u53(w2[0], w2[1]);
-      int j = jth_empty(S, sg, jidx);
+      int j;
+      double log_hastings = 0.0;
+      if (S->swap_mode == 0) {
+        int jidx = (int)(u53(w[2], w[3]) * (double)(S->N - m));
+        j = jth_empty(S, sg, jidx);
+      } else {
+        /* target: uniform among the empty neighbours E(i) of i = occ[k]; the
+         * reverse move picks i among the empty neighbours E'(j) of j after the
+         * move, so the Metropolis-Hastings factor is |E(i)| / |E'(j)| */
+        int i = S->occ[sg][k], ne = 0;
+        char* occd = (char*)calloc(S->N, 1);
+        for (int a = 0; a < m; ++a) occd[S->occ[sg][a]] = 1;
+        for (int t = S->nb_off[i]; t < S->nb_off[i + 1]; ++t) ne += !occd[S->nb_site[t]];
+        if (ne == 0) {  /* no move: a rejected attempt */
+          free(occd);
+          S->cnt[2]++;
+          continue;
+        }
+        int jidx = (int)(u53(w[2], w[3]) * (double)ne);
+        j = -1;
+        for (int t = S->nb_off[i], c = 0; t < S->nb_off[i + 1]; ++t)
+          if (!occd[S->nb_site[t]]) { if (c == jidx) { j = S->nb_site[t]; break; } ++c; }
+        occd[i] = 0;
+        occd[j] = 1;
+        int ne2 = 0;
+        for (int t = S->nb_off[j]; t < S->nb_off[j + 1]; ++t) ne2 += !occd[S->nb_site[t]];
+        free(occd);
+        /* mode 2 leaves the factor out on purpose: the tests use it to show
+         * that the ED comparison detects a missing Hastings correction */
+        log_hastings = (S->swap_mode == 2) ? 0.0 : log((double)ne) - log((double)ne2);
+      }
       swap_trial tr;
       swap_core(S, sg, k, j, T0, &tr);
       S->cnt[2]++;
-      int accept = tr.valid && (tr.logabs >= 0.0 || u < exp(tr.logabs));
+      const double lacc = tr.logabs + log_hastings;
+      int accept = tr.valid && (lacc >= 0.0 || u < exp(lacc));
       if (accept) {
         S->cnt[3]++;
         memcpy(S->QR[sg], tr.Q, sizeof(double) * (S->n + 1) * pn);
@@ -1185,3 +1238,4 @@ void orc_info(const orc_sim* S, int* ints, double* dbl) {
 void orc_get_families(const orc_sim* S, int* fam) { memcpy(fam, S->fam_of, sizeof(int) * S->nb); }
 
 void orc_set_sweep(orc_sim* S, uint32_t sweep) { S->sweep = sweep; }
+void orc_set_swap_mode(orc_sim* S, int mode) { S->swap_mode = mode; }

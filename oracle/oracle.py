@@ -72,6 +72,7 @@ def _load():
     lib.orc_stats.argtypes = [P, C.POINTER(C.c_longlong)]
     lib.orc_info.argtypes = [P, ip, dp]
     lib.orc_get_families.argtypes = [P, ip]
+    lib.orc_set_swap_mode.argtypes = [P, C.c_int]
     lib.orc_set_sweep.argtypes = [P, C.c_uint32]
     _lib = lib
     return lib
@@ -94,7 +95,7 @@ class OracleSim:
     """One chain of the oracle.  ``lat`` is a dict from ``oracle.lattices``."""
 
     def __init__(self, lat, U, beta, dtau, n_up, n_dn, n_stab, seed=0, chain=0,
-                 max_records=100000, want_corr=False, init="seed"):
+                 max_records=100000, want_corr=False, init="seed", swap_mode=0):
         lib = _load()
         self.lib = lib
         self.lat = lat
@@ -116,6 +117,7 @@ class OracleSim:
         self.N, self.L, self.tw, self.n, self.G, self.n_up, self.n_dn, self.charge = [int(x) for x in ints[:8]]
         self.lam = float(dbl[0])
         self.ns = (self.n_up, self.n_dn)
+        lib.orc_set_swap_mode(self.h, int(swap_mode))  # 0 uniform target, 1 empty nearest neighbour
         if init == "seed":
             lib.orc_init_from_seed(self.h)
         else:

@@ -240,12 +240,22 @@ def test_ed_canonical_free_trace():
     assert abs(ed.Z - Z) < 1e-10 * abs(Z)
 
 
-def _mc_vs_ed(lat, U, beta, dtau, nu, nd, tw, nsweep, names, seed, nsig=5.0, chains=1):
+def _mc_records(lat, U, beta, dtau, nu, nd, tw, nsweep, seed, chains=1, swap_mode=0):
+    recs = []
+    for c in range(chains):
+        o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=seed, chain=c, max_records=nsweep, swap_mode=swap_mode)
+        o.sweep(nsweep // 10, measure=False)
+        o.sweep(nsweep)
+        recs.append(o.records())
+    return np.concatenate(recs)
+
+
+def _mc_vs_ed(lat, U, beta, dtau, nu, nd, tw, nsweep, names, seed, nsig=5.0, chains=1, swap_mode=0):
     L = int(round(beta / dtau))
     ed = exact.TrotterED(lat, U, dtau, L, nu, nd).observables()
     recs = []
     for c in range(chains):
-        o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=seed, chain=c, max_records=nsweep)
+        o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=seed, chain=c, max_records=nsweep, swap_mode=swap_mode)
         o.sweep(nsweep // 10, measure=False)
         o.sweep(nsweep)
         recs.append(o.records())
@@ -271,3 +281,28 @@ def test_mc_matches_trotter_ed_free_fermions():
 
 def test_mc_matches_trotter_ed_flatband():
     _mc_vs_ed(lattices.flatband(3), 2.0, 2.0, 0.1, 2, 1, 5, 10000, ["docc", "ekin", "szz_00", "szz_11"], seed=4)
+
+
+# Nearest-neighbour Fock-swap proposals (target uniform among the empty
+# neighbours of the removed particle's site, Metropolis-Hastings factor
+# |E(i)| / |E'(j)|).  Open chains make the neighbour counts uneven (the end
+# sites have one neighbour), so a wrong factor biases the density profile and
+# with it the kinetic energy.
+def test_mc_matches_trotter_ed_nearest_neighbour_swaps_free():
+    _mc_vs_ed(lattices.chain(7, 1.0, False), 0.0, 2.0, 0.1, 2, 2, 5, 20000, ["ekin", "szz_00", "s_par"], seed=3,
+              swap_mode=1)
+
+
+def test_mc_matches_trotter_ed_nearest_neighbour_swaps_repulsive():
+    _mc_vs_ed(lattices.chain(6, 1.0, False), 4.0, 1.0, 0.1, 2, 1, 5, 20000, ["docc", "ekin", "szz_00", "s_par"],
+              seed=1, swap_mode=1)
+
+
+def test_missing_hastings_factor_is_detected():
+    """Planted mistake: the same proposal without the Hastings factor (oracle
+    mode 2) must miss the exact kinetic energy by many standard errors."""
+    lat = lattices.chain(7, 1.0, False)
+    ed = exact.TrotterED(lat, 0.0, 0.1, 20, 2, 2).observables()
+    recs = _mc_records(lat, 0.0, 2.0, 0.1, 2, 2, 5, 20000, seed=3, swap_mode=2)
+    est, err = jackknife_ratio(recs, OBS_NAMES.index("ekin"))
+    assert abs(est - ed["ekin"]) > 10.0 * err
