@@ -130,7 +130,19 @@ typedef struct {
   int32_t n_stab;  /* tau_w: slices between QR restabilizations */
   int32_t precision; /* LQ_FP64, LQ_MIXED or LQ_MIXED_DW */
   uint64_t seed;   /* Philox4x32-10 key */
+  int32_t swap_mode; /* Fock-swap target: LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR (0 = uniform) */
 } lq_params;
+
+/* Fock-swap proposals.  A swap removes the particle of a uniformly drawn
+ * occupied column k and adds one at a target site j.  UNIFORM draws j
+ * uniformly among the empty sites.  NEIGHBOUR draws j uniformly among the
+ * empty nearest neighbours E(i) of the removed particle's site i (distinct
+ * bond partners; no move if there is none) and accepts with the
+ * Metropolis-Hastings factor |E(i)| / |E'(j)|, E'(j) being the empty
+ * neighbours of j after the move.  The paper fixes the weight ratio of a
+ * Fock-state move, not its proposal law. */
+#define LQ_SWAP_UNIFORM 0
+#define LQ_SWAP_NEIGHBOUR 1
 
 /* optional device allocator (e.g. a framework's caching allocator); stream is
  * the cudaStream_t the memory is used on.  NULL -> cudaMalloc/cudaFree. */

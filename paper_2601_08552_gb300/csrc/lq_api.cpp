@@ -47,6 +47,8 @@ struct lq_lattice {
   // family-sorted copies (read by the allocation-free entry point)
   std::vector<int> fam_off, sorted_i, sorted_j;
   std::vector<double> sorted_k;
+  // each site's distinct bond partners, ascending (nearest-neighbour swaps)
+  std::vector<int> nb_off, nb_site;
 };
 
 // each bond, in order, goes to the lowest family where neither site is used
@@ -98,6 +100,18 @@ static lq_status make_lattice(int N, const std::vector<int>& bi, const std::vect
     L->sorted_j.push_back(L->bj[order[t]]);
     L->sorted_k.push_back(L->kb[order[t]]);
   }
+  std::vector<std::vector<int>> adj(N);
+  for (int b = 0; b < nb; ++b) {
+    adj[L->bi[b]].push_back(L->bj[b]);
+    adj[L->bj[b]].push_back(L->bi[b]);
+  }
+  L->nb_off.assign(N + 1, 0);
+  for (int i = 0; i < N; ++i) {
+    std::sort(adj[i].begin(), adj[i].end());
+    adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
+    L->nb_off[i + 1] = L->nb_off[i] + (int)adj[i].size();
+    L->nb_site.insert(L->nb_site.end(), adj[i].begin(), adj[i].end());
+  }
   *out = L;
   return LQ_OK;
 }
@@ -107,6 +121,7 @@ lq_lattice_view lq_lattice_get_view(const lq_lattice* L) {
   v.N = L->N; v.nb = (int)L->bi.size(); v.G = L->G; v.has_eps = L->has_eps;
   v.fam_off = L->fam_off.data(); v.sorted_i = L->sorted_i.data(); v.sorted_j = L->sorted_j.data();
   v.sorted_k = L->sorted_k.data(); v.eps = L->eps.data(); v.sub = L->sub.data();
+  v.nb_off = L->nb_off.data(); v.nb_site = L->nb_site.data();
   return v;
 }
 
@@ -278,7 +293,8 @@ static size_t footprint_one(int N, int nb, int G, int L, int tw, const int ns[2]
   const size_t PS = prec == LQ_FP64 ? sizeof(double) : sizeof(float);
   const int n = (L + tw - 1) / tw;
   size_t b = al256((G + 1) * 4) + 3 * al256(nb * 4) + 3 * al256(nb * 8) + 2 * al256(nb * 4) + 3 * al256(N * 8) +
-             al256(N * 4) + al256(N * 4) + al256((size_t)L * N);
+             al256(N * 4) + al256(N * 4) + al256((size_t)(N + 1) * 4) + al256((size_t)std::max(2 * nb, 1) * 4) +
+             al256((size_t)L * N);
   for (int sg = 0; sg < 2; ++sg) {
     const size_t pn = (size_t)N * ns[sg], qn = (size_t)ns[sg] * ns[sg];
     b += al256(std::max(ns[sg], 1) * 4);
@@ -326,6 +342,8 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     if (Ll < 1 || std::fabs(Lf - (double)Ll) > 1e-9 * std::max(1.0, Lf) || Ll > (1 << 24) - 1)
       return fail(LQ_EINVAL, "beta/dtau must be a positive integer");
     if (p.n_stab < 1) return fail(LQ_EINVAL, "n_stab must be >= 1");
+    if (p.swap_mode != LQ_SWAP_UNIFORM && p.swap_mode != LQ_SWAP_NEIGHBOUR)
+      return fail(LQ_EINVAL, "swap_mode must be LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR");
     if (p.n_up < 0 || p.n_dn < 0 || p.n_up > Lt->N || p.n_dn > Lt->N)
       return fail(LQ_EINVAL, "particle numbers must be in [0, N]");
     if (p.n_up > LQ_MAX_PARTICLES || p.n_dn > LQ_MAX_PARTICLES)
@@ -366,7 +384,8 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   auto lat_bytes = [&](int c) {
     const ChainHost& ci = info[c];
     return al256((ci.G + 1) * 4) + 3 * al256(ci.nb * 4) + 3 * al256(ci.nb * 8) + 2 * al256(ci.nb * 4) +
-           3 * al256(ci.N * 8) + al256(ci.N * 4) + al256(ci.N * 4);
+           3 * al256(ci.N * 8) + al256(ci.N * 4) + al256(ci.N * 4) + al256((size_t)(ci.N + 1) * 4) +
+           al256((size_t)std::max(2 * ci.nb, 1) * 4);
   };
   const int max_records = 1 << 16;
   auto chain_bytes = [&](int c) {
@@ -449,6 +468,8 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     (void)take(ci.N * 8);
     float* d_cef = (float*)take(ci.N * 4);
     int* d_sub = (int*)take(ci.N * 4);
+    int* d_nbo = (int*)take((size_t)(ci.N + 1) * 4);
+    int* d_nbs = (int*)take((size_t)std::max(2 * ci.nb, 1) * 4);
     std::vector<cudaError_t> es;
     es.push_back(up(d_fo, fo.data(), fo.size() * 4));
     if (ci.nb) {
@@ -459,6 +480,8 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     }
     es.push_back(up(d_ce, ce.data(), ci.N * 8)); es.push_back(up(d_ep, ep.data(), ci.N * 8));
     es.push_back(up(d_cef, cef.data(), ci.N * 4)); es.push_back(up(d_sub, Lt->sub.data(), ci.N * 4));
+    es.push_back(up(d_nbo, Lt->nb_off.data(), (size_t)(ci.N + 1) * 4));
+    if (!Lt->nb_site.empty()) es.push_back(up(d_nbs, Lt->nb_site.data(), Lt->nb_site.size() * 4));
     // the staging vectors must outlive the async copies
     for (cudaError_t ee : es)
       if (ee != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(ee, "lattice upload"); }
@@ -471,9 +494,12 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     D.lat.cepsf = Lt->has_eps ? d_cef : nullptr;
     D.lat.eps = Lt->has_eps ? d_ep : nullptr;
     D.lat.sub = d_sub;
+    D.lat.nb_off = d_nbo;
+    D.lat.nb_site = d_nbs;
     D.N = ci.N; D.L = ci.L; D.tw = ci.tw; D.n = ci.n; D.ns[0] = ci.ns[0]; D.ns[1] = ci.ns[1];
     D.charge = p.U < 0;
     D.prec = prec;
+    D.swap_mode = p.swap_mode;
     D.lambda = std::acosh(std::exp(p.dtau * std::fabs(p.U) / 2.0));
     D.dfac_p = std::exp(D.lambda); D.dfac_m = std::exp(-D.lambda);
     D.delta_p = std::expm1(-2.0 * D.lambda); D.delta_m = std::expm1(2.0 * D.lambda);

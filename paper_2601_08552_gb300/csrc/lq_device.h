@@ -44,6 +44,8 @@ struct LqLatticeDev {
   const float* cepsf;
   const double* eps;        // onsite eps_i, or nullptr
   const int* sub;           // sublattice label 0/1
+  const int* nb_off;        // N + 1 offsets into nb_site
+  const int* nb_site;       // each site's distinct bond partners, ascending
 };
 
 struct LqChainDev {
@@ -59,6 +61,7 @@ struct LqChainDev {
   double opd_p, opd_m;      // 1 + delta_p, 1 + delta_m (row factor of an accepted flip)
   float dw_delta_p[2], dw_delta_m[2], dw_cfac_p[2], dw_cfac_m[2];  // double-word forms (LQ_MIXED_DW)
   uint32_t key0, key1, chain_id, sweep;
+  int swap_mode;            // LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR
   // configuration
   int8_t* s;                // L x N fields, row = slice
   int* occ[2];              // ordered occupied sites (columns of P)

@@ -21,6 +21,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "../../include/lecqmc.h"
 #include "lq_device.h"
 #include "lq_kernels.h"
 
@@ -1538,7 +1539,8 @@ template <class R, bool BIG> __device__ void down_pass(LqChainDev& C, int do_mea
 // sm.T[sg].  commit: 1 Metropolis with uniform u, 0 only report (hook).
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int commit, Smem& sm) {
+__device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int commit, Smem& sm,
+                             double log_hastings = 0.0) {
   const int N = C.N, m = C.ns[sg], n = C.n, MP = sm.MP, M = sm.M;
   const int cb = C.cur[sg], tb = cb ^ 1;
   const size_t pn = (size_t)N * m;
@@ -1731,7 +1733,8 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     const int sgn_add = (s_add < 0) ? -1 : 1;
     const double logabs = valid ? log_rem + log_add : -INFINITY;
     const int sgn = sgn_rem * sgn_add;
-    const int accept = commit && valid && (logabs >= 0.0 || u < exp(logabs));
+    const double lacc = logabs + log_hastings;  // Metropolis-Hastings: weight ratio times the proposal ratio
+    const int accept = commit && valid && (lacc >= 0.0 || u < exp(lacc));
     if (lane == 0) {
       C.hook[0] = logabs; C.hook[1] = sgn; C.hook[2] = log_rem; C.hook[3] = sgn_rem;
       C.hook[4] = log_add; C.hook[5] = sgn_add;
@@ -1826,18 +1829,53 @@ template <class R> __device__ void swap_phase(LqChainDev& C, Smem& sm) {
         philox(C.chain_id, C.sweep, c2, 0u, C.key0, C.key1, w);
         philox(C.chain_id, C.sweep, c2, 1u, C.key0, C.key1, w2);
         const int k = (int)(u53(w[0], w[1]) * (double)m);
-        const int jidx = (int)(u53(w[2], w[3]) * (double)(C.N - m));
+        double lh = 0.0;
+        int j;
+        if (C.swap_mode == LQ_SWAP_NEIGHBOUR) {
+          // target uniform among the empty neighbours E(i) of i = occ[k];
+          // the reverse move draws i among the empty neighbours E'(j) of j
+          // after the move, so the proposal ratio is |E(i)| / |E'(j)|
+          const int i = C.occ[sg][k];
+          const int* nbs = C.lat.nb_site;
+          const int t0 = C.lat.nb_off[i], t1 = C.lat.nb_off[i + 1];
+          int ne = 0;
+          for (int t = t0; t < t1; ++t) ne += !((sm.bits[nbs[t] >> 5] >> (nbs[t] & 31)) & 1u);
+          j = -2;  // no empty neighbour: no move
+          if (ne > 0) {
+            const int jidx = (int)(u53(w[2], w[3]) * (double)ne);
+            for (int t = t0, c = 0; t < t1; ++t)
+              if (!((sm.bits[nbs[t] >> 5] >> (nbs[t] & 31)) & 1u)) {
+                if (c == jidx) { j = nbs[t]; break; }
+                ++c;
+              }
+            int ne2 = 0;
+            for (int t = C.lat.nb_off[j]; t < C.lat.nb_off[j + 1]; ++t) {
+              const int o = nbs[t];
+              ne2 += (o == i) || !((sm.bits[o >> 5] >> (o & 31)) & 1u);
+            }
+            lh = log((double)ne) - log((double)ne2);
+          }
+        } else {
+          const int jidx = (int)(u53(w[2], w[3]) * (double)(C.N - m));
+          j = jth_empty(sm, C.N, jidx);
+        }
         sm.ip[4] = k;
-        sm.ip[5] = jth_empty(sm, C.N, jidx);
+        sm.ip[5] = j;
         sm.red[50] = u53(w2[0], w2[1]);
+        sm.red[51] = lh;
       }
       __syncthreads();
+      if (sm.ip[5] == -2) {  // nearest-neighbour proposal with no empty neighbour: a rejected attempt
+        if (TID == 0) C.cnt[2]++;
+        __syncthreads();
+        continue;
+      }
       if (sm.ip[5] < 0) {  // cannot happen for jidx < N - m; never index with it
         if (TID == 0) sm.C->err |= LQ_ERR_NONFINITE;
         __syncthreads();
         continue;
       }
-      swap_attempt<R>(C, sg, sm.ip[4], sm.ip[5], sm.red[50], 1, sm);
+      swap_attempt<R>(C, sg, sm.ip[4], sm.ip[5], sm.red[50], 1, sm, sm.red[51]);
     }
   }
 }

@@ -14,6 +14,8 @@ struct lq_lattice_view {
   const double* sorted_k;
   const double* eps;       // N onsite terms
   const int* sub;          // N sublattice labels
+  const int* nb_off;       // N + 1 offsets into nb_site
+  const int* nb_site;      // each site's distinct bond partners, ascending
 };
 
 lq_lattice_view lq_lattice_get_view(const lq_lattice* L);

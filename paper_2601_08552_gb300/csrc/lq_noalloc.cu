@@ -62,6 +62,8 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
     return lq_internal_fail(LQ_EINVAL, "beta/dtau must be a positive integer");
   if (p->n_stab < 1 || p->n_up < 0 || p->n_dn < 0 || p->n_up > v.N || p->n_dn > v.N)
     return lq_internal_fail(LQ_EINVAL, "n_stab must be >= 1 and particle numbers in [0, N]");
+  if (p->swap_mode != LQ_SWAP_UNIFORM && p->swap_mode != LQ_SWAP_NEIGHBOUR)
+    return lq_internal_fail(LQ_EINVAL, "swap_mode must be LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR");
   if (p->n_up > LQ_MAX_PARTICLES || p->n_dn > LQ_MAX_PARTICLES)
     return lq_internal_fail(LQ_EUNSUPPORTED, "at most LQ_MAX_PARTICLES particles per spin");
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -89,6 +91,7 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   const size_t o_fo = take((G + 1) * 4), o_bi = take(nb * 4), o_bj = take(nb * 4), o_bk = take(nb * 8);
   const size_t o_bc = take(nb * 8), o_bs = take(nb * 8), o_bcf = take(nb * 4), o_bsf = take(nb * 4);
   const size_t o_eps = take(N * 8), o_ce = take(N * 8), o_cef = take(N * 4), o_sub = take(N * 4);
+  const size_t o_nbo = take((size_t)(N + 1) * 4), o_nbs = take((size_t)std::max(2 * nb, 1) * 4);
   size_t o_QR[2][2], o_VR[2][2], o_QL[2], o_VL[2], o_st[2], o_live[2], o_work[2];
   for (int sg = 0; sg < 2; ++sg) {
     const size_t pn = (size_t)N * ns[sg], qn = (size_t)ns[sg] * ns[sg];
@@ -116,6 +119,8 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   if (e == cudaSuccess) e = up(o_bk, v.sorted_k, nb * 8);
   if (e == cudaSuccess) e = up(o_eps, v.eps, N * 8);
   if (e == cudaSuccess) e = up(o_sub, v.sub, N * 4);
+  if (e == cudaSuccess) e = up(o_nbo, v.nb_off, (size_t)(N + 1) * 4);
+  if (e == cudaSuccess) e = up(o_nbs, v.nb_site, (size_t)v.nb_off[N] * 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_order, 0, sizeof(int), st);
   if (e != cudaSuccess) return lq_internal_fail(LQ_ECUDA, std::string("lq_sweep_noalloc upload: ") + cudaGetErrorString(e));
   noalloc_tables_kernel<<<(std::max(nb, N) + 255) / 256, 256, 0, st>>>(
@@ -139,9 +144,12 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   D.lat.cepsf = v.has_eps ? (const float*)(base + o_cef) : nullptr;
   D.lat.eps = v.has_eps ? (const double*)(base + o_eps) : nullptr;
   D.lat.sub = (const int*)(base + o_sub);
+  D.lat.nb_off = (const int*)(base + o_nbo);
+  D.lat.nb_site = (const int*)(base + o_nbs);
   D.N = N; D.L = L; D.tw = tw; D.n = n; D.ns[0] = ns[0]; D.ns[1] = ns[1];
   D.charge = p->U < 0;
   D.prec = p->precision;
+  D.swap_mode = p->swap_mode;
   D.lambda = std::acosh(std::exp(p->dtau * std::fabs(p->U) / 2.0));
   D.dfac_p = std::exp(D.lambda); D.dfac_m = std::exp(-D.lambda);
   D.delta_p = std::expm1(-2.0 * D.lambda); D.delta_m = std::expm1(2.0 * D.lambda);

@@ -15,9 +15,11 @@ from . import build as _build
 LQ_FP64 = 0
 LQ_MIXED = 1
 LQ_MIXED_DW = 2
+LQ_SWAP_UNIFORM = 0
+LQ_SWAP_NEIGHBOUR = 1
 LQ_NOBS = 9
 OBS_NAMES = ["sign", "n_up", "n_dn", "docc", "ekin", "szz_00", "szz_11", "szz_01", "s_par"]
-LQ_MAX_PARTICLES = 32
+LQ_MAX_PARTICLES = 256
 
 _STATUS = {0: "LQ_OK", 1: "LQ_EINVAL", 2: "LQ_ENOMEM", 3: "LQ_ECUDA", 4: "LQ_ENUMERIC", 5: "LQ_ETIMEOUT",
            6: "LQ_EBUSY", 7: "LQ_ENOTFOUND", 8: "LQ_EUNSUPPORTED"}
@@ -44,7 +46,8 @@ class LqError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("U", C.c_double), ("beta", C.c_double), ("dtau", C.c_double), ("n_up", C.c_int32),
-                ("n_dn", C.c_int32), ("n_stab", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64)]
+                ("n_dn", C.c_int32), ("n_stab", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64),
+                ("swap_mode", C.c_int32)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -227,9 +230,7 @@ def sweep_noalloc(lattice, params, chain_id, sweep_index, dev_fields, dev_occ, n
     load()
     import torch
 
-    p = Params(float(params["U"]), float(params["beta"]), float(params["dtau"]), int(params["n_up"]),
-               int(params["n_dn"]), int(params["n_stab"]), int(params.get("precision", LQ_FP64)),
-               int(params.get("seed", 0)) & (2**64 - 1))
+    p = _params_struct(params)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     lw, sg = C.c_double(), C.c_int32()
@@ -278,8 +279,7 @@ class Sim:
         lh = (C.c_void_p * n)(*[l.h.value for l in lattices])
         pp = (Params * n)()
         for c, p in enumerate(params):
-            pp[c] = Params(float(p["U"]), float(p["beta"]), float(p["dtau"]), int(p["n_up"]), int(p["n_dn"]),
-                           int(p["n_stab"]), int(p.get("precision", LQ_FP64)), int(p.get("seed", 0)) & (2**64 - 1))
+            pp[c] = _params_struct(p)
         ids = None
         if chain_ids is not None:
             ids = (C.c_uint32 * n)(*[int(x) for x in chain_ids])
@@ -433,7 +433,8 @@ class Sim:
 
 def _params_struct(p):
     return Params(float(p["U"]), float(p["beta"]), float(p["dtau"]), int(p["n_up"]), int(p["n_dn"]),
-                  int(p["n_stab"]), int(p.get("precision", LQ_FP64)), int(p.get("seed", 0)) & (2**64 - 1))
+                  int(p["n_stab"]), int(p.get("precision", LQ_FP64)), int(p.get("seed", 0)) & (2**64 - 1),
+                  int(p.get("swap_mode", LQ_SWAP_UNIFORM)))
 
 
 class Server:
