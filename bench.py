@@ -440,7 +440,8 @@ def main():
         phases = {k: round(float(pr[i]) / tot, 4) for i, k in
                   enumerate(["flips", "propagation", "qr", "block_inverse", "swaps", "measure"])}
         # per-chain means of the measured observables (warm-up and timed sweeps)
-        run.obs[(prec, sp is spec)] = np.stack([sim.records(c).mean(axis=0) for c in range(n_chains)])
+        if sp is spec:
+            run.obs[prec] = np.stack([sim.records(c).mean(axis=0) for c in range(n_chains)])
         return sim, per, total_ms, clocks, d, phases
 
     run.lw0 = {}
@@ -502,7 +503,7 @@ def main():
             d["speedup_vs_fp64"] = d["value"] / value
             d["logw_max_rel_err_vs_fp64"] = float(np.max(np.abs(run.lw0[prec] - run.lw0[0]) /
                                                          np.maximum(1.0, np.abs(run.lw0[0]))))
-            d["observables_vs_fp64"] = observable_deviation(run.obs[(prec, True)], run.obs[(0, True)])
+            d["observables_vs_fp64"] = observable_deviation(run.obs[prec], run.obs[0])
             mixed[key] = d
             msim.close()
 
@@ -523,6 +524,19 @@ def main():
     if not args.no_uneven and args.workload == WORKLOAD:
         uneven = uneven_leg(lq, inputs, torch, stream, autotune=not args.no_autotune)
 
+    # nearest-neighbour Fock-swap proposals on the same workload (FP64)
+    neighbour = None
+    if args.workload == WORKLOAD:
+        spn = dict(spec, swap_mode=1)
+        nsim, nper, ntotal, _, nstat, nphases = run(0, spn)
+        neighbour = dict(value=world * upd_per_step * args.steps / (ntotal * 1e-3), unit=UNIT,
+                         swap_accept=float(nstat[3] / max(nstat[2], 1)),
+                         swap_accept_uniform=float(dstat[3] / max(dstat[2], 1)),
+                         field_accept=float(nstat[1] / max(nstat[0], 1)), phase_cycle_share=nphases,
+                         proposal="target uniform among the empty nearest neighbours, Metropolis-Hastings factor",
+                         precision="FP64")
+        nsim.close()
+
     serving = None
     if not args.no_serving and world == 1 and args.workload == WORKLOAD:
         serving = serving_leg(lq, inputs, 1, window_s=args.serving_window)
@@ -542,7 +556,7 @@ def main():
                     field_accept=float(dstat[1] / max(dstat[0], 1)),
                     swap_accept=float(dstat[3] / max(dstat[2], 1)), phase_cycle_share=phases,
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
-                    reduced_precision=mixed, attractive=attractive, uneven_flatband=uneven,
+                    reduced_precision=mixed, attractive=attractive, neighbour_swaps=neighbour, uneven_flatband=uneven,
                     serving=serving)
         print(json.dumps(line), flush=True)
     if dist is not None:
