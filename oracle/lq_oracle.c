@@ -11,12 +11,12 @@
  *   - canonical weight det[P^T B_s(beta,0) P], Eq. (1);
  *   - B(beta,0) = prod_l B_l with B_l = e^{-dtau K} e^{-dtau V(s_l)}, the Trotter
  *     form of the propagator written in the constrained-path section
- *     (U(s) = prod e^{-dtau H0} e^{-dtau H_I}, SM Sec. V);
+ *     (U(s) = prod e^{-dtau H0} e^{-dtau H_I}, SM Sec. VI);
  *   - stabilized QR chain B_i Q_{i-1} = Q_i V_i every tau_w slices (SM Sec. I.A,
  *     the "subsequent stabilization steps"), B_i the product of the tau_w
  *     slices of block i;
  *   - field flips with the Sherman-Morrison update of (L R)^{-1}: the ratio
- *     det(U_L^T (1+Delta_i) U_R) / det(U_L^T U_R) of SM Sec. V;
+ *     det(U_L^T (1+Delta_i) U_R) / det(U_L^T U_R) of SM Sec. VI;
  *   - particle removal: permutation U, Givens retriangulation G_i of V_i U
  *     (i = 1) and V_i G_{i-1}^T (i > 1), Q_i' = Q_i G_i^T, ratio 1/(s r_Ne)
  *     with 1/s = [M^{-1}]_{Ne,Ne}, M^{-1} = G_n (P^T Q)^{-1} U (Eq. S10) and

@@ -4,11 +4,11 @@
 // One CTA owns one Markov chain for a whole sweep (persistent over a queue of
 // chains, longest first).  Inside a CTA:
 //   * slice propagation (B_l = e^{-dtau K} e^{-dtau V(s_l)}, Eq. 1 and the
-//     Trotter form of SM Sec. V) streams column chunks of an N x N_sigma panel
+//     Trotter form of SM Sec. VI) streams column chunks of an N x N_sigma panel
 //     through shared memory and applies the checkerboard families there;
 //   * restabilization every tau_w slices (B_i Q_{i-1} = Q_i V_i, SM Sec. I.A)
 //     is CholeskyQR2 with FP64 Gram matrices and a positive diagonal;
-//   * field flips (the Sherman-Morrison ratio of SM Sec. V) run on two warps,
+//   * field flips (the Sherman-Morrison ratio of SM Sec. VI) run on two warps,
 //     one per spin, exchanging the two g values through shared memory once
 //     per site, so two resident chains per SM keep all four FP64 pipes busy;
 //   * particle-hole swaps: removal by permutation + Givens retriangulation

@@ -3,7 +3,7 @@
 * Sign in the dilute limit (main text, Fig. 2): <sign> of the 2D repulsive
   Hubbard gas at fixed particle number and temperature as the linear size L
   grows (density N_e / L^2 falls).
-* Flat-band ferromagnetism (main text, Fig. 4; SM Sec. IV): the BCL chain
+* Flat-band ferromagnetism (main text, Fig. 4; SM Secs. IV-V): the BCL chain
   at half filling of its flat lowest band (N_e = number of cells,
   N_up = N_dn), where the in-plane S^par(q=0) grows as T -> 0 and the
   A1-sublattice S^zz(q=0) tends to 1/16 (SM Eq. S33).  With S^z_tot = 0 in
