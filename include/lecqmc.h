@@ -238,6 +238,17 @@ lq_status lq_sim_chain_info(const lq_sim* sim, int32_t chain, int32_t* info6);
 lq_status lq_sim_device_bytes(const lq_sim* sim, size_t* bytes);
 lq_status lq_sim_destroy(lq_sim* sim);
 
+/* Numeric health check (build-side, no counterpart in the paper): rebuild
+ * every chain's QR chains from its fields and Fock state, compare the fresh
+ * log|W| and sign with the tracked ones (the running sum of accepted log|r|),
+ * and keep the rebuilt chains, so the check also resynchronizes.  A chain
+ * drifted if |fresh - tracked| / max(1, |fresh|) > tol or the signs differ.
+ * host_max_rel / host_n_bad (nullable) receive the largest relative drift and
+ * the number of drifted chains.  Errors: LQ_ENUMERIC when a chain drifted
+ * (after resynchronizing it) or a device error flag is set; LQ_EINVAL for a
+ * negative tol.  Synchronous; costs about one QR-chain build per chain. */
+lq_status lq_sim_check_drift(lq_sim* sim, double tol, double* host_max_rel, int32_t* host_n_bad);
+
 /* Sign-weighted means <sign O>/<sign> over chain c's per-sweep records and
  * their jackknife errors over n_bins bins (host arrays of LQ_NOBS; index 0
  * holds the mean sign and a zero error). */

@@ -854,6 +854,35 @@ extern "C" lq_status lq_sim_tracked_weight(lq_sim* S, int32_t c, double* la, int
   return LQ_OK;
 }
 
+// Numeric health check: rebuild every chain's QR chains from its fields and
+// Fock state (the state is fully reconstructible from them), compare the fresh
+// log|W| and sign with the tracked ones, and keep the rebuilt chains.
+extern "C" lq_status lq_sim_check_drift(lq_sim* S, double tol, double* host_max_rel, int32_t* host_n_bad) {
+  if (!S || !(tol >= 0.0)) return fail(LQ_EINVAL, "bad arguments to lq_sim_check_drift");
+  lq_status st = pull(S);
+  if (st != LQ_OK) return st;
+  std::vector<double> lw(S->n_chains);
+  std::vector<int> sg(S->n_chains);
+  for (int c = 0; c < S->n_chains; ++c) { lw[c] = S->h[c].logw; sg[c] = S->h[c].sign; }
+  if ((st = rebuild(S, S->d_all, S->n_chains)) != LQ_OK) return st;
+  if ((st = pull(S)) != LQ_OK) return st;
+  double worst = 0.0;
+  int bad = 0;
+  for (int c = 0; c < S->n_chains; ++c) {
+    const double fresh = S->h[c].logw;
+    const double rel = std::fabs(fresh - lw[c]) / std::max(1.0, std::fabs(fresh));
+    const bool off = !(rel <= tol) || S->h[c].sign != sg[c];
+    worst = std::max(worst, std::isfinite(rel) ? rel : INFINITY);
+    bad += off;
+  }
+  if (host_max_rel) *host_max_rel = worst;
+  if (host_n_bad) *host_n_bad = bad;
+  if (bad)
+    return fail(LQ_ENUMERIC, std::to_string(bad) + " chain(s) drifted beyond the tolerance (largest relative drift " +
+                                 std::to_string(worst) + "); their chains were rebuilt from fields and Fock states");
+  return lq_sim_sync(S);
+}
+
 extern "C" lq_status lq_sim_field_ratio(lq_sim* S, int32_t c, int32_t l, int32_t i, double* r) {
   lq_status st = check_chain(S, c);
   if (st != LQ_OK) return st;

@@ -32,7 +32,8 @@ EXPORTS = [
     "lq_sim_log_weight",
     "lq_sim_tracked_weight", "lq_sim_field_ratio", "lq_sim_swap_ratio", "lq_sim_records",
     "lq_sim_clear_records", "lq_sim_stats", "lq_sim_profile", "lq_sim_chain_panel", "lq_sim_chain_info",
-    "lq_sim_device_bytes", "lq_sim_destroy", "lq_sim_measure", "lq_server_create", "lq_server_submit",
+    "lq_sim_device_bytes", "lq_sim_destroy", "lq_sim_measure", "lq_sim_check_drift", "lq_server_create",
+    "lq_server_submit",
     "lq_server_poll", "lq_server_stats", "lq_server_set_tick_target", "lq_server_destroy", "lq_sweep_noalloc",
     "lq_last_error", "lq_version",
 ]
@@ -131,6 +132,7 @@ def load(build_if_missing=True):
         "lq_sim_destroy": [P],
         "lq_sweep_noalloc": [P, C.POINTER(Params), u32, u32, P, P, i32, P, P, pdbl, pi32, C.POINTER(C.c_int64)],
         "lq_sim_measure": [P, i32, i32, pdbl, pdbl],
+        "lq_sim_check_drift": [P, dbl, pdbl, pi32],
         "lq_server_create": [i32, C.c_size_t, i32, i32, i32, C.POINTER(P)],
         "lq_server_submit": [P, C.POINTER(Request), C.POINTER(C.c_uint64)],
         "lq_server_poll": [P, C.c_uint64, C.POINTER(Result)],
@@ -345,6 +347,14 @@ class Sim:
 
     def sweep(self, n=1, measure=True):
         _check(_lib.lq_sim_sweep(self.h, int(n), int(bool(measure))))
+
+    def check_drift(self, tol=1e-8):
+        """Rebuild every chain from its fields and Fock state and compare the
+        fresh log|W| with the tracked one; returns (largest relative drift,
+        number of drifted chains) or raises LqError (LQ_ENUMERIC) on drift."""
+        worst, bad = C.c_double(), C.c_int32()
+        _check(_lib.lq_sim_check_drift(self.h, float(tol), C.byref(worst), C.byref(bad)))
+        return worst.value, bad.value
 
     def autotune(self, sweeps_per_candidate=1):
         """Time each plan class's candidate staging buffers on real (unmeasured)

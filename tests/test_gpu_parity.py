@@ -197,3 +197,28 @@ def test_full_size_gas32x32_sampled(lq):
         lt, st = sim.tracked_weight(c)
         lo, so = o.tracked()
         assert st == so and abs(lt - lo) < 1e-9 * abs(lo)
+
+
+def test_check_drift_resynchronizes(lq):
+    """lq_sim_check_drift rebuilds the chains from fields and Fock states:
+    after sweeps the drift is at round-off, the tracked weight then equals a
+    fresh log|W|, and the rebuilt chains continue on the oracle's trajectory."""
+    o, sim = make(lq, CASES["square4x4"], seed=11, chain=3)
+    sim.init()
+    o.sweep(3)
+    sim.sweep(3)
+    sim.sync()
+    worst, bad = sim.check_drift(1e-9)
+    assert bad == 0 and worst < 1e-9
+    # the rebuilt (fresh) weight against the oracle's tracked one, which the
+    # oracle pins tie to a fresh brute-force weight after sweeps
+    lt, st = sim.tracked_weight(0)
+    lo, so = o.tracked()
+    assert st == so and abs(lt - lo) < 1e-9 * max(1.0, abs(lo))
+    o.sweep(2)
+    sim.sweep(2)
+    sim.sync()
+    assert np.array_equal(sim.get_fields(0), o.get_fields())
+    assert np.array_equal(sim.stats(0), o.stats())
+    with pytest.raises(lq.LqError):
+        sim.check_drift(-1.0)
