@@ -32,7 +32,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "HS field updates/sec & sweeps/sec vs plain FP64 same GPU; p50/p99 sweep latency"
 UNIT = "field-updates/s"
-FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64 (CUDA cores), the pool recipe's figure
+# GB300 dense FP64 on the CUDA cores: one FP64 warp instruction per 64 cycles per sub-partition
+# (tests/fp64_cost_probe.cu) = 0.5 FMA/cycle x 4 sub-partitions x 152 SMs x 2.07 GHz x 2 flops
+# = 1.26 TFLOP/s, NVIDIA's nominal 1.25; an FMA loop sustains 1.19
+FP64_PEAK_TFLOPS = 1.25
 WORKLOAD = "gas32x32"
 
 
@@ -462,7 +465,8 @@ def main():
     roofline = dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
                     frac=achieved / FP64_PEAK_TFLOPS, traffic=profiled_traffic("fp64_bytes_per_launch"),
                     kernel="lq::sweep_kernel<double, false>", flops_per_launch=flops,
-                    peak_source="GB300 dense FP64 1.25 TFLOP/s (pool recipe table); 1.19 measured by FMA loop")
+                    peak_source="GB300 dense FP64: 0.5 FMA/cycle/sub-partition x 4 x 152 SMs x 2.07 GHz x 2 = 1.26 TFLOP/s "
+                                "(nominal 1.25); an FMA loop sustains 1.19")
 
     # end to end through the C ABI on pinned host buffers
     n_occ = spec["n_up"] + spec["n_dn"]

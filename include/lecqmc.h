@@ -47,7 +47,7 @@ typedef enum {
   LQ_ETIMEOUT = 5,    /* a bounded device wait gave up */
   LQ_EBUSY = 6,       /* a queue is full */
   LQ_ENOTFOUND = 7,   /* no such request / result not ready */
-  LQ_EUNSUPPORTED = 8 /* a size outside what this build supports */
+  LQ_EUNSUPPORTED = 8 /* a size outside what the library supports */
 } lq_status;
 
 /* precision modes.
@@ -77,7 +77,7 @@ typedef enum {
 #define LQ_OBS_SZZ01 7
 #define LQ_OBS_SPAR 8  /* S^par(q=0) = (1/(N/2)) sum_ij <S^x_i S^x_j + S^y_i S^y_j> */
 
-/* largest particle number per spin this build supports */
+/* largest particle number per spin the library supports */
 #define LQ_MAX_PARTICLES 256
 
 typedef struct lq_lattice lq_lattice;

@@ -27,7 +27,7 @@
  *   - particle-hole swap = removal followed by addition, Metropolis on the
  *     product ratio (main text, "Canonical sampling").
  *
- * Readings where the paper is silent (each one is also listed in the design doc):
+ * Readings where the paper is silent:
  *   - B_i is the product of the slices of block i only (the text's
  *     "B_s(i tau_w, 0)" contradicts B_i Q_{i-1} = Q_i V_i);
  *   - Hirsch discrete HS: U > 0 spin channel, cosh(lambda) = e^{dtau U/2},
