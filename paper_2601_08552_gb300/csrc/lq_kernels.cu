@@ -8,15 +8,24 @@
 //     through shared memory and applies the checkerboard families there;
 //   * restabilization every tau_w slices (B_i Q_{i-1} = Q_i V_i, SM Sec. I.A)
 //     is CholeskyQR2 with FP64 Gram matrices and a positive diagonal;
-//   * field flips (the Sherman-Morrison ratio of SM Sec. VI) run on two warps,
-//     one per spin, exchanging the two g values through shared memory once
-//     per site, so two resident chains per SM keep all four FP64 pipes busy;
+//   * field flips (the Sherman-Morrison ratio of SM Sec. VI) run as a
+//     submatrix update over windows of K sites: the window's dense products
+//     are batched, and the serial chain of a site is its diagonal block
+//     element, the ratio and a K x K rank-1 update.  Up to 32 particles per
+//     spin one warp per spin does it (the spins exchange their factors through
+//     shared memory once per site, and two resident chains per SM put the four
+//     flip warps on four FP64 pipes); above 32 a four-warp group per spin
+//     shares the window's dense work and the m x m matrices sit in a global
+//     workspace per CTA;
 //   * particle-hole swaps: removal by permutation + Givens retriangulation
 //     (Eqs. S9-S12), addition by propagating one vector and orthogonalising
-//     it twice against each Q_i (Eqs. S1-S8, Eq. 4);
+//     it twice against each Q_i (Eqs. S1-S8, Eq. 4); the target is uniform
+//     over the empty sites or over the empty nearest neighbours (with the
+//     Metropolis-Hastings factor);
 //   * equal-time measurements at the block boundaries of the down pass.
-// Panels are FP64 (LQ_FP64) or FP32 (LQ_MIXED); the N_sigma x N_sigma algebra,
-// QR, log-det factors and all ratios stay FP64 in both.
+// Panels are FP64 (LQ_FP64) or FP32 (LQ_MIXED, LQ_MIXED_DW); QR, log-det
+// factors and inverses stay FP64 in all modes, and the flip algebra is FP64
+// except in LQ_MIXED_DW (double-word FP32).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
