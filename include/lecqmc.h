@@ -162,20 +162,28 @@ typedef struct {
 lq_status lq_sim_create(const lq_lattice* const* lattices, const lq_params* params, int32_t n_chains,
                         const uint32_t* chain_ids, void* cuda_stream, const lq_allocator* alloc, lq_sim** out);
 /* Draw fields (uniform +-1) and Fock states (Fisher-Yates, sorted) from each
- * chain's seed on the device, then build the QR chains.  Asynchronous. */
+ * chain's seed on the device, then build the right and left QR chains
+ * (B_i Q_{i-1} = Q_i V_i, SM Sec. I.A).  Asynchronous. */
 lq_status lq_sim_init(lq_sim* sim);
-/* Fields of one chain from a host array (L x N, row = slice, values +-1);
- * rebuilds that chain's QR chains.  Errors: LQ_EINVAL for a value != +-1. */
+/* Hubbard-Stratonovich fields s of Eq. 1 for one chain from a host array
+ * (L x N, row = slice, values +-1); rebuilds that chain's QR chains.
+ * Errors: LQ_EINVAL for a value != +-1. */
 lq_status lq_sim_set_fields(lq_sim* sim, int32_t chain, const int8_t* host_s);
 lq_status lq_sim_get_fields(lq_sim* sim, int32_t chain, int8_t* host_s);
-/* Ordered occupied sites (the columns of P) of one chain; rebuilds its chains.
- * Errors: LQ_EINVAL for a repeated or out-of-range site. */
+/* The Fock state eta of Eq. 1: ordered occupied sites (the columns of P_eta)
+ * of one chain; rebuilds its chains.  Errors: LQ_EINVAL for a repeated or
+ * out-of-range site. */
 lq_status lq_sim_set_fock(lq_sim* sim, int32_t chain, const int32_t* host_occ_up, const int32_t* host_occ_dn);
 lq_status lq_sim_get_fock(lq_sim* sim, int32_t chain, int32_t* host_occ_up, int32_t* host_occ_dn);
 /* Set the sweep counter of every chain (the Philox counter word). */
 lq_status lq_sim_set_sweep_index(lq_sim* sim, uint32_t sweep);
-/* n_sweeps sweeps of every chain in one persistent launch (one CTA per
- * chain, longest chains first).  measure != 0 appends one record per sweep.
+/* n_sweeps sweeps of every chain, one persistent launch per plan class (one
+ * CTA per chain, longest chains first).  A sweep samples the weight of Eq. 1:
+ * an up pass of field updates (the fast-update ratio of SM Sec. VI, run as a
+ * submatrix update), N_up then N_dn Fock-state swaps (ratio of Eq. 2 by the
+ * QR update: removal Eqs. S9-S12, addition Eqs. S1-S8), and a down pass of
+ * field updates with equal-time measurements at the block boundaries.
+ * measure != 0 appends one record (LQ_NOBS sign-weighted means) per sweep.
  * Asynchronous on the stream. */
 lq_status lq_sim_sweep(lq_sim* sim, int32_t n_sweeps, int32_t measure);
 /* Autotune the batched launch (build-side tuning, no counterpart in the
@@ -203,17 +211,20 @@ lq_status lq_sim_run_host(lq_sim* sim, const int8_t* host_fields, const int32_t*
                           int32_t measure, int8_t* host_fields_out, int32_t* host_occ_out, double* host_records);
 /* Wait for the stream; LQ_ENUMERIC if any chain flagged a numerical error. */
 lq_status lq_sim_sync(lq_sim* sim);
-/* log|W| and sign of chain c recomputed from freshly built QR chains (this
- * also resets the tracked weight). */
+/* log|W| and sign of chain c, W = prod_sigma det(P^T B(beta,0) P) of Eq. 1,
+ * recomputed from freshly built QR chains (this also resets the tracked
+ * weight). */
 lq_status lq_sim_log_weight(lq_sim* sim, int32_t chain, double* log_abs, int32_t* sign);
 /* log|W| and sign tracked through the accepted ratios since the last build. */
 lq_status lq_sim_tracked_weight(lq_sim* sim, int32_t chain, double* log_abs, int32_t* sign);
-/* Test hook: ratio W(s with s[slice][site] flipped) / W(s), through the
- * stabilized Green's function at that slice on freshly built chains. */
+/* Test hook: ratio W(s with s[slice][site] flipped) / W(s) (SM Sec. VI),
+ * through the stabilized Green's function at that slice on freshly built
+ * chains. */
 lq_status lq_sim_field_ratio(lq_sim* sim, int32_t chain, int32_t slice, int32_t site, double* r);
-/* Test hook: ratio of removing column k of spin `spin` and adding site j
- * (not occupied), by the Givens / Gram-Schmidt QR update; parts (nullable,
- * 6 doubles) = log|r|, sign, log|r_remove|, sign, log|r_add|, sign. */
+/* Test hook: the Fock-state ratio of Eq. 2 for removing column k of spin
+ * `spin` and adding site j (not occupied), by the Givens (Eq. S10) and
+ * Gram-Schmidt (Eq. S7) QR update; parts (nullable, 6 doubles) = log|r|,
+ * sign, log|r_remove|, sign, log|r_add|, sign. */
 lq_status lq_sim_swap_ratio(lq_sim* sim, int32_t chain, int32_t spin, int32_t k, int32_t j, double* r,
                             double* parts);
 /* Per-sweep records of chain c: *n_records rows of LQ_NOBS doubles into
