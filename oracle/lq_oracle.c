@@ -42,9 +42,20 @@
  *     the down pass;
  *   - swap proposal: column k uniform among occupied columns, target uniform
  *     among empty sites; accept iff u < |r| (ties reject); the added particle
- *     is appended as the last column;
+ *     is appended as the last column.  Alternative (swap_mode 1): target
+ *     uniform among the empty nearest neighbours E(i) of the removed site i,
+ *     accepted with the Metropolis-Hastings factor |E(i)| / |E'(j)|;
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter = (chain, sweep, tag<<24 | slice-or-attempt, site-or-sub).
+ *
+ * Pins (tests/test_oracle_pins.py): Philox known answers, closed-form
+ * spectra and the exact flat band, B_K against a matrix exponential,
+ * log-weights against dense determinants and 60-digit arithmetic, field and
+ * swap ratios against brute-force determinant ratios, QR-chain invariants,
+ * tracked against fresh weights after sweeps, measurements against dense Wick
+ * estimators, exhaustive enumeration against the Trotterized ED, and Monte
+ * Carlo against that ED (both swap proposals).  Parity unpinned: the average
+ * sign at the benchmark sizes, where no exact value exists beyond ED sizes.
  */
 #include <math.h>
 #include <stdint.h>
