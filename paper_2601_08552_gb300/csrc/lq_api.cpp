@@ -259,6 +259,11 @@ struct lq_sim {
   int* d_order = nullptr;        // chains by decreasing cost
   int* d_single = nullptr;       // scratch list of one chain
   int* d_queue = nullptr;
+  // with chains in both plan classes, the large class runs on a second stream
+  // (its own chain queue) concurrently with the small one, joined by events
+  int* d_queue2 = nullptr;
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int* d_all = nullptr;          // 0..n-1
   int M = 1, Nmax = 1, buf_bytes = 0, grid = 1;
   // sweeps run one launch per plan class: chains with at most LQ_NS_SMALL
@@ -405,7 +410,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   for (int c = 0; c < n_chains; ++c) { off[c] = tot; tot += chain_bytes(c); }
   const size_t desc_off = tot;
   tot += al256(sizeof(LqChainDev) * n_chains) + 3 * al256(sizeof(int) * (n_chains + 1)) +
-         al256(sizeof(int) * (n_chains + 1 + 1024));
+         al256(sizeof(int) * (n_chains + 1 + 1024)) + al256(sizeof(int) * (1 + 1024));
   const size_t ws_off = tot;
   tot += al256(S->ws_bytes);
   S->arena_bytes = tot;
@@ -421,6 +426,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   S->d_single = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
   S->d_all = (int*)(S->arena + o2); o2 += al256(sizeof(int) * (n_chains + 1));
   S->d_queue = (int*)(S->arena + o2);  // [0]: chain queue, [1..1024]: per-SM CTA counters
+  S->d_queue2 = (int*)(S->arena + o2 + al256(sizeof(int) * (n_chains + 1 + 1024)));
   S->ws = S->ws_bytes ? S->arena + ws_off : nullptr;
   // descriptors + host-side constant data (lattice tables, P = first sites)
   S->h.resize(n_chains);
@@ -568,6 +574,12 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
       pc.grid = std::min(pc.n, sms * per_sm);
     }
   }
+  if (S->cls[0].n && S->cls[1].n) {
+    cudaError_t es = cudaStreamCreateWithFlags(&S->st2, cudaStreamNonBlocking);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming);
+    if (es != cudaSuccess) { lq_sim_destroy(S); return cuda_fail(es, "second stream"); }
+  }
   e = cudaMemcpy(S->d_chains, S->h.data(), sizeof(LqChainDev) * n_chains, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(S->d_order, ord.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(S->d_all, all.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice);
@@ -671,11 +683,28 @@ extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) 
   if (n_sweeps == 0) return LQ_OK;
   S->mirror_fresh = false;
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-    const lq_sim::PlanClass& pc = S->cls[k];
-    if (pc.n)
-      e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + pc.off, pc.n, S->d_queue, n_sweeps, measure, pc.M,
-                           pc.Nmax, pc.buf, pc.grid, S->st, S->ws, S->ws_bytes);
+  const lq_sim::PlanClass& small = S->cls[0];
+  const lq_sim::PlanClass& large = S->cls[1];
+  if (small.n && large.n && S->st2) {
+    // the large class first, on the second stream, so that its long chains
+    // start at once; the small class fills the other SMs meanwhile
+    e = cudaEventRecord(S->ev_fork, S->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st2, S->ev_fork, 0);
+    if (e == cudaSuccess)
+      e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + large.off, large.n, S->d_queue2, n_sweeps, measure,
+                           large.M, large.Nmax, large.buf, large.grid, S->st2, S->ws, S->ws_bytes);
+    if (e == cudaSuccess)
+      e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + small.off, small.n, S->d_queue, n_sweeps, measure,
+                           small.M, small.Nmax, small.buf, small.grid, S->st, nullptr, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(S->ev_join, S->st2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st, S->ev_join, 0);
+  } else {
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      const lq_sim::PlanClass& pc = S->cls[k];
+      if (pc.n)
+        e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + pc.off, pc.n, S->d_queue, n_sweeps, measure, pc.M,
+                             pc.Nmax, pc.buf, pc.grid, S->st, S->ws, S->ws_bytes);
+    }
   }
   if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   return LQ_OK;
@@ -996,6 +1025,12 @@ extern "C" lq_status lq_sim_device_bytes(const lq_sim* S, size_t* bytes) {
 
 extern "C" lq_status lq_sim_destroy(lq_sim* S) {
   if (!S) return LQ_OK;
+  if (S->st2) {
+    cudaStreamSynchronize(S->st2);
+    cudaStreamDestroy(S->st2);
+  }
+  if (S->ev_fork) cudaEventDestroy(S->ev_fork);
+  if (S->ev_join) cudaEventDestroy(S->ev_join);
   if (S->arena) {
     cudaStreamSynchronize(S->st);
     if (S->has_alloc) S->alloc.free(S->alloc.ctx, S->arena, S->arena_bytes, S->st);
