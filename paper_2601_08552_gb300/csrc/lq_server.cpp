@@ -89,6 +89,9 @@ struct lq_server {
   int* d_order = nullptr;
   int* d_caps = nullptr;
   int* d_queue = nullptr;
+  int* d_queue2 = nullptr;                // chain queue of the large-plan launch
+  cudaStream_t st2 = nullptr;             // its stream, forked from and joined to st
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   char* d_ws = nullptr;  // workspace of big plans for the gathered launches (grown on demand)
   size_t ws_cap = 0;
   int dev_sms = 1;
@@ -300,28 +303,44 @@ static void tick(lq_server* S) {
   cudaEventCreate(&e1);
   cudaEventRecord(e0, S->st);
   cudaError_t e = cudaSuccess;
-  for (int cls = 0, q0 = 0; cls < 2 && e == cudaSuccess; ++cls) {
-    int q1 = q0;
-    int M = 1, Nmax = 1, buf = 0;
-    long long budget_ns = std::max(1LL, (long long)(target_ms * 1e6));  // 0 would mean no budget in the kernel
-    while (q1 < n && (int)big[order[q1]] == cls) {
-      const lq_sim_launch_info inf = lq_internal_sim_info(S->active[order[q1]].sim);
-      M = std::max(M, inf.M);
-      Nmax = std::max(Nmax, inf.Nmax);
-      buf = std::max(buf, inf.buf_bytes);
-      budget_ns = std::max(budget_ns, (long long)est[order[q1]]);
-      ++q1;
+  // the classes' ranges in the order array and their plans
+  int qa[3] = {0, 0, n}, Mc[2] = {1, 1}, Nc[2] = {1, 1}, bc[2] = {0, 0}, gc[2] = {0, 0};
+  long long budget[2];
+  while (qa[1] < n && !big[order[qa[1]]]) ++qa[1];
+  for (int cls = 0; cls < 2; ++cls) {
+    budget[cls] = std::max(1LL, (long long)(target_ms * 1e6));  // 0 would mean no budget in the kernel
+    for (int q = qa[cls]; q < qa[cls + 1]; ++q) {
+      const lq_sim_launch_info inf = lq_internal_sim_info(S->active[order[q]].sim);
+      Mc[cls] = std::max(Mc[cls], inf.M);
+      Nc[cls] = std::max(Nc[cls], inf.Nmax);
+      bc[cls] = std::max(bc[cls], inf.buf_bytes);
+      budget[cls] = std::max(budget[cls], (long long)est[order[q]]);
     }
-    if (q1 > q0) {
-      const size_t smem = lq::smem_bytes(M, Nmax, buf);
-      const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, M, smem));
-      const int grid = std::min(q1 - q0, S->dev_sms * per_sm);
-      e = ensure_ws(S, (size_t)grid * lq::workspace_bytes(M, Nmax, buf));
-      if (e == cudaSuccess)
-        e = lq::launch_sweep(S->prec, S->d_slots, S->d_order + q0, q1 - q0, S->d_queue, 1, 1, M, Nmax, buf, grid, S->st,
-                             S->d_ws, S->ws_cap, S->d_caps + q0, budget_ns);
+    if (qa[cls + 1] > qa[cls]) {
+      const size_t smem = lq::smem_bytes(Mc[cls], Nc[cls], bc[cls]);
+      const int per_sm = std::max(1, lq::max_active_sweep_ctas(S->prec, Mc[cls], smem));
+      gc[cls] = std::min(qa[cls + 1] - qa[cls], S->dev_sms * per_sm);
     }
-    q0 = q1;
+  }
+  if (gc[1]) e = ensure_ws(S, (size_t)gc[1] * lq::workspace_bytes(Mc[1], Nc[1], bc[1]));
+  // with both classes, the large one runs on the second stream (its own chain
+  // queue) concurrently with the small one, joined by events
+  const bool both = gc[0] && gc[1];
+  if (e == cudaSuccess && both) {
+    e = cudaEventRecord(S->ev_fork, S->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st2, S->ev_fork, 0);
+  }
+  for (int cls = 1; cls >= 0 && e == cudaSuccess; --cls) {
+    if (!gc[cls]) continue;
+    const int q0 = qa[cls], nq = qa[cls + 1] - qa[cls];
+    cudaStream_t st = (both && cls == 1) ? S->st2 : S->st;
+    int* queue = (both && cls == 1) ? S->d_queue2 : S->d_queue;
+    e = lq::launch_sweep(S->prec, S->d_slots, S->d_order + q0, nq, queue, 1, 1, Mc[cls], Nc[cls], bc[cls], gc[cls], st,
+                         cls ? S->d_ws : nullptr, cls ? S->ws_cap : 0, S->d_caps + q0, budget[cls]);
+  }
+  if (e == cudaSuccess && both) {
+    e = cudaEventRecord(S->ev_join, S->st2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st, S->ev_join, 0);
   }
   cudaEventRecord(e1, S->st);
   cudaMemcpyAsync(desc.data(), S->d_slots, sizeof(LqChainDev) * n, cudaMemcpyDeviceToHost, S->st);
@@ -410,6 +429,10 @@ extern "C" lq_status lq_server_create(int32_t device, size_t hbm_budget, int32_t
   if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_order, sizeof(int) * max_active);
   if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_caps, sizeof(int) * max_active);
   if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_queue, sizeof(int) * (1 + 1024));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_queue2, sizeof(int) * (1 + 1024));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->dev_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) {
     cudaMemPoolProps props;
@@ -539,6 +562,13 @@ extern "C" lq_status lq_server_destroy(lq_server* S) {
   cudaFree(S->d_order);
   cudaFree(S->d_caps);
   cudaFree(S->d_queue);
+  cudaFree(S->d_queue2);
+  if (S->st2) {
+    cudaStreamSynchronize(S->st2);
+    cudaStreamDestroy(S->st2);
+  }
+  if (S->ev_fork) cudaEventDestroy(S->ev_fork);
+  if (S->ev_join) cudaEventDestroy(S->ev_join);
   if (S->pool) cudaMemPoolDestroy(S->pool);
   if (S->st) cudaStreamDestroy(S->st);
   delete S;
