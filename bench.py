@@ -217,6 +217,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def measured_hbm_gbs():
+    """The pod's measured copy bandwidth (MEASURED_PEAKS.json beside this
+    file), else the earlier GB300 measurement of 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 def profiled_traffic(kind):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source."""
@@ -467,6 +477,11 @@ def main():
                     kernel="lq::sweep_kernel<double, false>", flops_per_launch=flops,
                     peak_source="GB300 dense FP64: 0.5 FMA/cycle/sub-partition x 4 x 152 SMs x 2.07 GHz x 2 = 1.26 TFLOP/s "
                                 "(nominal 1.25); an FMA loop sustains 1.19")
+    if roofline["traffic"]:
+        # the same kernel against DRAM: profiled bytes per launch over the launch time
+        hbm_peak, hbm_src = measured_hbm_gbs()
+        hbm_ach = roofline["traffic"] / (kern_ms * 1e-3) / 1e9
+        roofline["hbm"] = dict(achieved=hbm_ach, peak=hbm_peak, unit="GB/s", frac=hbm_ach / hbm_peak, source=hbm_src)
 
     # end to end through the C ABI on pinned host buffers
     n_occ = spec["n_up"] + spec["n_dn"]
