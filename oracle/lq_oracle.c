@@ -45,8 +45,15 @@
  *     is appended as the last column.  Alternative (swap_mode 1): target
  *     uniform among the empty nearest neighbours E(i) of the removed site i,
  *     accepted with the Metropolis-Hastings factor |E(i)| / |E'(j)|;
+ *   - optional second swap phase (left_swaps): after the down pass, N_up then
+ *     N_dn attempts at tau = 0 that walk the left chain from tau = beta down
+ *     to 0.  det[P^T B(beta,0) P] = det[P^T B(beta,0)^T P], and the left chain
+ *     is the right chain of B(beta,0)^T = B_1^T ... B_n^T, so the removal and
+ *     addition steps above apply unchanged with B_i -> B_{n-i+1}^T;
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
- *     counter = (chain, sweep, tag<<24 | slice-or-attempt, site-or-sub).
+ *     counter = (chain, sweep, tag<<24 | slice-or-attempt, site-or-sub);
+ *     tags 1/2 up/down field passes, 3 swaps at tau = beta, 4/5 the initial
+ *     fields and Fock states, 6 swaps at tau = 0.
  *
  * Pins (tests/test_oracle_pins.py): Philox known answers, closed-form
  * spectra and the exact flat band, B_K against a matrix exponential,
@@ -54,7 +61,8 @@
  * swap ratios against brute-force determinant ratios, QR-chain invariants,
  * tracked against fresh weights after sweeps, measurements against dense Wick
  * estimators, exhaustive enumeration against the Trotterized ED, and Monte
- * Carlo against that ED (both swap proposals).  Parity unpinned: the average
+ * Carlo against that ED (both swap proposals, with and without the swaps at
+ * tau = 0).  Parity unpinned: the average
  * sign at the benchmark sizes, where no exact value exists beyond ED sizes.
  */
 #include <math.h>
@@ -132,6 +140,7 @@ typedef struct {
    * deliberately wrong sampler for the tests) */
   int swap_mode;
   int *nb_off, *nb_site;
+  int left_swaps;           /* 1: a second swap phase at tau = 0 after the down pass */
 } orc_sim;
 
 static double* dalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
@@ -901,7 +910,7 @@ typedef struct {
   double logabs; int sign;   /* the swap ratio r = r_rem * r_add */
   double log_rem; int sign_rem;
   double log_add; int sign_add;
-  double *Q, *V;             /* trial right chain, blocks 1..n (index 0 unused) */
+  double *Q, *V;             /* trial chain, in the walked chain's storage order */
   double* Tnew;              /* (P''^T Q''_n)^{-1} */
   int* occ_new;
   int valid;
@@ -909,7 +918,24 @@ typedef struct {
 
 /* Removal of column k followed by addition of site j for spin sigma, on the
  * current right chain and T0 = (P^T Q^R_n)^{-1}.  Nothing is committed. */
-static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T0, swap_trial* tr) {
+/* A swap walks one chain from its P end to the far end.  side 0: the right
+ * chain, blocks i = 1..n at Q^R_i, V^R_i, propagator B_i.  side 1: the left
+ * chain read from tau = beta down to 0, which is the right chain of the
+ * transposed propagator B(beta,0)^T = B_1^T ... B_n^T (the weight
+ * det[P^T B(beta,0) P] equals det[P^T B(beta,0)^T P]): its block i is
+ * Q^L_{n-i}, V^L_{n-i}, with propagator B_{n-i+1}^T. */
+static int chain_ix(const orc_sim* S, int side, int i) { return side ? S->n - i : i; }
+
+static void chain_prop(const orc_sim* S, int side, int sigma, int i, double* x) {
+  if (!side) {
+    for (int l = S->bnd[i - 1]; l < S->bnd[i]; ++l) { apply_D(S, x, 1, l, sigma); apply_BK(S, x, 1); }
+  } else {
+    int jl = S->n - i + 1;
+    for (int l = S->bnd[jl] - 1; l >= S->bnd[jl - 1]; --l) { apply_BKT(S, x, 1); apply_D(S, x, 1, l, sigma); }
+  }
+}
+
+static void swap_core(const orc_sim* S, int side, int sigma, int k, int j, const double* T0, swap_trial* tr) {
   int N = S->N, m = S->ns[sigma], n = S->n;
   size_t pn = panel(S, sigma), qn = sq(S, sigma);
   tr->Q = dalloc((n + 1) * pn);
@@ -917,8 +943,8 @@ static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T
   tr->Tnew = dalloc(qn);
   tr->occ_new = (int*)calloc(m, sizeof(int));
   tr->valid = 1;
-  memcpy(tr->Q, S->QR[sigma], sizeof(double) * (n + 1) * pn);
-  memcpy(tr->V, S->VR[sigma], sizeof(double) * (n + 1) * qn);
+  memcpy(tr->Q, side ? S->QL[sigma] : S->QR[sigma], sizeof(double) * (n + 1) * pn);
+  memcpy(tr->V, side ? S->VL[sigma] : S->VR[sigma], sizeof(double) * (n + 1) * qn);
   /* column order after the permutation U: k moves to the last position */
   int* ord = (int*)calloc(m, sizeof(int));
   for (int a = 0, t = 0; a < m; ++a) if (a != k) ord[t++] = a;
@@ -929,7 +955,7 @@ static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T
   double log_rN = 0.0; int sign_rN = 1;
   double* A = dalloc(qn);
   for (int i = 1; i <= n; ++i) {
-    double* Vi = tr->V + i * qn;
+    double* Vi = tr->V + chain_ix(S, side, i) * qn;
     if (i == 1) {
       for (int a = 0; a < m; ++a) for (int b = 0; b < m; ++b) A[a * m + b] = Vi[a * m + ord[b]];
     } else {
@@ -958,7 +984,7 @@ static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T
       A[(q + 1) * m + q] = 0.0;
     }
     memcpy(Vi, A, sizeof(double) * qn);
-    double* Qi = tr->Q + i * pn;                /* Q_i' = Q_i G_i^T */
+    double* Qi = tr->Q + chain_ix(S, side, i) * pn;  /* Q_i' = Q_i G_i^T */
     for (int row = 0; row < N; ++row)
       for (int t = 0; t < nrot; ++t) {
         int q = k + t; double c = rc[t], s = rs[t];
@@ -1001,8 +1027,8 @@ static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T
   double log_rho = 0.0;
   for (int i = 1; i <= n && tr->valid; ++i) {
     memcpy(w, q, sizeof(double) * N);
-    for (int l = S->bnd[i - 1]; l < S->bnd[i]; ++l) { apply_D(S, w, 1, l, sigma); apply_BK(S, w, 1); }
-    double* Qi = tr->Q + i * pn;
+    chain_prop(S, side, sigma, i, w);
+    double* Qi = tr->Q + chain_ix(S, side, i) * pn;
     for (int a = 0; a < mr; ++a) { double acc = 0.0; for (int r = 0; r < N; ++r) acc += Qi[(size_t)r * m + a] * w[r]; v[a] = acc; }
     for (int r = 0; r < N; ++r) { double acc = 0.0; for (int a = 0; a < mr; ++a) acc += Qi[(size_t)r * m + a] * v[a]; w[r] -= acc; }
     for (int a = 0; a < mr; ++a) { double acc = 0.0; for (int r = 0; r < N; ++r) acc += Qi[(size_t)r * m + a] * w[r]; v2[a] = acc; }
@@ -1014,7 +1040,7 @@ static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T
     if (rho == 0.0) { tr->valid = 0; break; }
     for (int r = 0; r < N; ++r) q[r] = w[r] / rho;
     for (int r = 0; r < N; ++r) Qi[(size_t)r * m + (m - 1)] = q[r];
-    double* Vi = tr->V + i * qn;
+    double* Vi = tr->V + chain_ix(S, side, i) * qn;
     for (int a = 0; a < mr; ++a) { Vi[a * m + (m - 1)] = v[a]; Vi[(m - 1) * m + a] = 0.0; }
     Vi[(m - 1) * m + (m - 1)] = rho;
     log_rho += log(rho);
@@ -1022,7 +1048,7 @@ static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T
   double s_add = 0.0;
   double* av = dalloc(m); double* bv = dalloc(m);
   if (tr->valid) {
-    const double* Qn = tr->Q + n * pn;
+    const double* Qn = tr->Q + chain_ix(S, side, n) * pn;
     for (int a = 0; a < mr; ++a) {
       double acc = 0.0;
       for (int b = 0; b < mr; ++b) acc += Tp[a * mr + b] * q[occr[b]];
@@ -1050,8 +1076,9 @@ static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T
     tr->Tnew[(m - 1) * m + (m - 1)] = 1.0 / s_add;
     for (int a = 0; a < mr; ++a) tr->occ_new[a] = occr[a];
     tr->occ_new[m - 1] = j;
-    memset(tr->Q, 0, sizeof(double) * pn);
-    for (int a = 0; a < m; ++a) tr->Q[(size_t)tr->occ_new[a] * m + a] = 1.0;
+    double* P = tr->Q + chain_ix(S, side, 0) * pn;
+    memset(P, 0, sizeof(double) * pn);
+    for (int a = 0; a < m; ++a) P[(size_t)tr->occ_new[a] * m + a] = 1.0;
   }
   free(ord); free(rc); free(rs); free(A); free(Mi); free(Tp); free(occr);
   free(q); free(w); free(v); free(v2); free(av); free(bv);
@@ -1059,12 +1086,12 @@ static void swap_core(const orc_sim* S, int sigma, int k, int j, const double* T
 
 static void free_trial(swap_trial* tr) { free(tr->Q); free(tr->V); free(tr->Tnew); free(tr->occ_new); }
 
-/* T0 = (P^T Q^R_n)^{-1} */
-static void pq_inverse(const orc_sim* S, int sigma, double* T0) {
+/* T0 = (P^T Q^R_n)^{-1} (side 0) or (P^T Q^L_0)^{-1} (side 1) */
+static void pq_inverse(const orc_sim* S, int side, int sigma, double* T0) {
   int m = S->ns[sigma];
   size_t pn = panel(S, sigma);
   double* W = dalloc(sq(S, sigma));
-  const double* Qn = S->QR[sigma] + S->n * pn;
+  const double* Qn = side ? S->QL[sigma] : (S->QR[sigma] + S->n * pn);
   for (int a = 0; a < m; ++a)
     for (int b = 0; b < m; ++b) W[a * m + b] = Qn[(size_t)S->occ[sigma][a] * m + b];
   double la; int sg;
@@ -1082,15 +1109,19 @@ static int jth_empty(const orc_sim* S, int sigma, int jidx) {
   return site;
 }
 
-static void swap_phase(orc_sim* S) {
+/* N_up then N_dn swap attempts on one chain: side 0 at tau = beta on the
+ * right chain after the up pass, side 1 at tau = 0 on the left chain after the
+ * down pass (random-number tag 3 and 6). */
+static void swap_phase(orc_sim* S, int side) {
+  const uint32_t tag = side ? 6u : 3u;
   for (int sg = 0; sg < 2; ++sg) {
     int m = S->ns[sg];
     if (m == 0 || m == S->N) continue;
     size_t pn = panel(S, sg), qn = sq(S, sg);
     double* T0 = dalloc(qn);
-    pq_inverse(S, sg, T0);
+    pq_inverse(S, side, sg, T0);
     for (int att = 0; att < m; ++att) {
-      uint32_t ctr[4] = {S->chain, S->sweep, (3u << 24) | ((uint32_t)sg << 16) | (uint32_t)att, 0u}, w[4], w2[4];
+      uint32_t ctr[4] = {S->chain, S->sweep, (tag << 24) | ((uint32_t)sg << 16) | (uint32_t)att, 0u}, w[4], w2[4];
       orc_philox(ctr, S->key, w);
       ctr[3] = 1u;
       orc_philox(ctr, S->key, w2);
@@ -1128,14 +1159,14 @@ static void swap_phase(orc_sim* S) {
         log_hastings = (S->swap_mode == 2) ? 0.0 : log((double)ne) - log((double)ne2);
       }
       swap_trial tr;
-      swap_core(S, sg, k, j, T0, &tr);
+      swap_core(S, side, sg, k, j, T0, &tr);
       S->cnt[2]++;
       const double lacc = tr.logabs + log_hastings;
       int accept = tr.valid && (lacc >= 0.0 || u < exp(lacc));
       if (accept) {
         S->cnt[3]++;
-        memcpy(S->QR[sg], tr.Q, sizeof(double) * (S->n + 1) * pn);
-        memcpy(S->VR[sg] + qn, tr.V + qn, sizeof(double) * S->n * qn);
+        memcpy(side ? S->QL[sg] : S->QR[sg], tr.Q, sizeof(double) * (S->n + 1) * pn);
+        memcpy(side ? S->VL[sg] : S->VR[sg], tr.V, sizeof(double) * (S->n + 1) * qn);
         memcpy(T0, tr.Tnew, sizeof(double) * qn);
         memcpy(S->occ[sg], tr.occ_new, sizeof(int) * m);
         S->logw += tr.logabs;
@@ -1144,6 +1175,8 @@ static void swap_phase(orc_sim* S) {
       free_trial(&tr);
     }
     free(T0);
+    /* the next up pass starts the right chain from Q^R_0 = P */
+    if (side) fill_P(S, sg, S->QR[sg]);
   }
 }
 
@@ -1154,8 +1187,9 @@ static void swap_phase(orc_sim* S) {
 void orc_sweep(orc_sim* S, int nsweeps, int measure) {
   for (int t = 0; t < nsweeps; ++t) {
     up_pass(S);
-    swap_phase(S);
+    swap_phase(S, 0);
     down_pass(S, measure);
+    if (S->left_swaps) swap_phase(S, 1);
     S->sweep++;
   }
 }
@@ -1185,19 +1219,24 @@ double orc_field_ratio(orc_sim* S, int l, int i) {
   return r;
 }
 
-/* Ratio of the swap (remove column k, add site j) for one spin; the removal
- * and addition factors are returned separately. */
-double orc_swap_ratio(orc_sim* S, int sigma, int k, int j, double* out /* log|r|, sign, log|r_rem|, sign_rem, log|r_add|, sign_add */) {
+/* Ratio of the swap (remove column k, add site j) for one spin on freshly
+ * built chains, walked along the right (side 0) or left (side 1) chain; the
+ * removal and addition factors are returned separately. */
+double orc_swap_ratio_side(orc_sim* S, int side, int sigma, int k, int j, double* out /* log|r|, sign, log|r_rem|, sign_rem, log|r_add|, sign_add */) {
   orc_build_chains(S);
   double* T0 = dalloc(sq(S, sigma));
-  pq_inverse(S, sigma, T0);
+  pq_inverse(S, side, sigma, T0);
   swap_trial tr;
-  swap_core(S, sigma, k, j, T0, &tr);
+  swap_core(S, side, sigma, k, j, T0, &tr);
   out[0] = tr.logabs; out[1] = tr.sign; out[2] = tr.log_rem; out[3] = tr.sign_rem;
   out[4] = tr.log_add; out[5] = tr.sign_add;
   double r = tr.sign * exp(tr.logabs);
   free_trial(&tr); free(T0);
   return r;
+}
+
+double orc_swap_ratio(orc_sim* S, int sigma, int k, int j, double* out) {
+  return orc_swap_ratio_side(S, 0, sigma, k, j, out);
 }
 
 /* Measurement on freshly built chains at block boundary jb (0..n). */
@@ -1250,3 +1289,4 @@ void orc_get_families(const orc_sim* S, int* fam) { memcpy(fam, S->fam_of, sizeo
 
 void orc_set_sweep(orc_sim* S, uint32_t sweep) { S->sweep = sweep; }
 void orc_set_swap_mode(orc_sim* S, int mode) { S->swap_mode = mode; }
+void orc_set_left_swaps(orc_sim* S, int on) { S->left_swaps = on ? 1 : 0; }

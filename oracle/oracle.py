@@ -60,6 +60,8 @@ def _load():
     lib.orc_field_ratio.restype = C.c_double
     lib.orc_swap_ratio.argtypes = [P, C.c_int, C.c_int, C.c_int, dp]
     lib.orc_swap_ratio.restype = C.c_double
+    lib.orc_swap_ratio_side.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, dp]
+    lib.orc_swap_ratio_side.restype = C.c_double
     lib.orc_measure_at.argtypes = [P, C.c_int, dp, dp, dp]
     lib.orc_num_records.argtypes = [P]
     lib.orc_num_records.restype = C.c_int
@@ -73,6 +75,7 @@ def _load():
     lib.orc_info.argtypes = [P, ip, dp]
     lib.orc_get_families.argtypes = [P, ip]
     lib.orc_set_swap_mode.argtypes = [P, C.c_int]
+    lib.orc_set_left_swaps.argtypes = [P, C.c_int]
     lib.orc_set_sweep.argtypes = [P, C.c_uint32]
     _lib = lib
     return lib
@@ -95,7 +98,7 @@ class OracleSim:
     """One chain of the oracle.  ``lat`` is a dict from ``oracle.lattices``."""
 
     def __init__(self, lat, U, beta, dtau, n_up, n_dn, n_stab, seed=0, chain=0,
-                 max_records=100000, want_corr=False, init="seed", swap_mode=0):
+                 max_records=100000, want_corr=False, init="seed", swap_mode=0, left_swaps=False):
         lib = _load()
         self.lib = lib
         self.lat = lat
@@ -118,6 +121,7 @@ class OracleSim:
         self.lam = float(dbl[0])
         self.ns = (self.n_up, self.n_dn)
         lib.orc_set_swap_mode(self.h, int(swap_mode))  # 0 uniform target, 1 empty nearest neighbour
+        lib.orc_set_left_swaps(self.h, int(bool(left_swaps)))  # second swap phase at tau = 0
         if init == "seed":
             lib.orc_init_from_seed(self.h)
         else:
@@ -175,9 +179,12 @@ class OracleSim:
     def field_ratio(self, l, i):
         return self.lib.orc_field_ratio(self.h, int(l), int(i))
 
-    def swap_ratio(self, spin, k, j):
+    def swap_ratio(self, spin, k, j, side="right"):
+        """Swap ratio on freshly built chains, walked along the right chain
+        (tau = beta end) or the left chain (tau = 0 end)."""
         out = np.zeros(6)
-        r = self.lib.orc_swap_ratio(self.h, int(spin), int(k), int(j), _ptr(out, C.c_double))
+        r = self.lib.orc_swap_ratio_side(self.h, 0 if side == "right" else 1, int(spin), int(k), int(j),
+                                         _ptr(out, C.c_double))
         return r, out
 
     def measure_at(self, jb, corr=False):

@@ -141,11 +141,14 @@ def test_swap_ratio_matches_brute_force(case):
             j = int(empty[rng.integers(len(empty))])
             new = cur[:k] + cur[k + 1:] + [j]
             ref = np.linalg.det(B[np.ix_(new, new)]) / np.linalg.det(A)
-            r, parts = o.swap_ratio(spin, k, j)
-            assert abs(r - ref) < 1e-10 * max(1.0, abs(ref))
-            # removal factor = [(P^T B P)^{-1}]_kk (cofactor identity)
-            rem = parts[3] * np.exp(parts[2])
-            assert abs(rem - np.linalg.inv(A)[k, k]) < 1e-10 * max(1.0, abs(rem))
+            # the same ratio walked along the right chain (tau = beta) and along
+            # the left chain (tau = 0, the transposed propagator)
+            for side in ("right", "left"):
+                r, parts = o.swap_ratio(spin, k, j, side=side)
+                assert abs(r - ref) < 1e-10 * max(1.0, abs(ref)), side
+                # removal factor = [(P^T B P)^{-1}]_kk (cofactor identity)
+                rem = parts[3] * np.exp(parts[2])
+                assert abs(rem - np.linalg.inv(A)[k, k]) < 1e-10 * max(1.0, abs(rem)), side
 
 
 def test_chain_invariants():
@@ -199,6 +202,27 @@ def test_tracked_weight_equals_fresh_after_sweeps(case):
     assert st_[2] == 4 * sum(m for m in (nu, nd) if 0 < m < o.N)
 
 
+@pytest.mark.parametrize("case", range(len(SWEEP_CASES)))
+def test_tracked_weight_equals_fresh_with_left_swaps(case):
+    """A second swap phase at tau = 0 on the left chain after the down pass:
+    the tracked weight still equals the dense determinant, both chains agree,
+    and each sweep makes twice the swap attempts."""
+    lat, U, beta, dtau, nu, nd, tw = SWEEP_CASES[case]
+    o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=41 + case, left_swaps=True)
+    o.sweep(4)
+    lt, st = o.tracked()
+    s = o.get_fields()
+    up, dn = o.get_fock()
+    ref = exact.log_weight(lat, U, dtau, s, up, dn)
+    assert st == ref[1]
+    assert abs(lt - ref[0]) < 1e-9 * max(1.0, abs(ref[0]))
+    # the left chain the left swaps edited in place, against the dense weight
+    lw, sg = o.log_weight("left")
+    assert sg == ref[1] and abs(lw - ref[0]) < 1e-9 * max(1.0, abs(ref[0]))
+    st_ = o.stats()
+    assert st_[2] == 8 * sum(m for m in (nu, nd) if 0 < m < o.N)
+
+
 def test_measure_matches_dense_wick():
     lat, U, beta, dtau = lattices.chain(6), 4.0, 1.0, 0.1
     o = OracleSim(lat, U, beta, dtau, 2, 1, 3, seed=3)
@@ -240,22 +264,25 @@ def test_ed_canonical_free_trace():
     assert abs(ed.Z - Z) < 1e-10 * abs(Z)
 
 
-def _mc_records(lat, U, beta, dtau, nu, nd, tw, nsweep, seed, chains=1, swap_mode=0):
+def _mc_records(lat, U, beta, dtau, nu, nd, tw, nsweep, seed, chains=1, swap_mode=0, left_swaps=False):
     recs = []
     for c in range(chains):
-        o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=seed, chain=c, max_records=nsweep, swap_mode=swap_mode)
+        o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=seed, chain=c, max_records=nsweep, swap_mode=swap_mode,
+                      left_swaps=left_swaps)
         o.sweep(nsweep // 10, measure=False)
         o.sweep(nsweep)
         recs.append(o.records())
     return np.concatenate(recs)
 
 
-def _mc_vs_ed(lat, U, beta, dtau, nu, nd, tw, nsweep, names, seed, nsig=5.0, chains=1, swap_mode=0):
+def _mc_vs_ed(lat, U, beta, dtau, nu, nd, tw, nsweep, names, seed, nsig=5.0, chains=1, swap_mode=0,
+              left_swaps=False):
     L = int(round(beta / dtau))
     ed = exact.TrotterED(lat, U, dtau, L, nu, nd).observables()
     recs = []
     for c in range(chains):
-        o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=seed, chain=c, max_records=nsweep, swap_mode=swap_mode)
+        o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=seed, chain=c, max_records=nsweep, swap_mode=swap_mode,
+                      left_swaps=left_swaps)
         o.sweep(nsweep // 10, measure=False)
         o.sweep(nsweep)
         recs.append(o.records())
@@ -296,6 +323,22 @@ def test_mc_matches_trotter_ed_nearest_neighbour_swaps_free():
 def test_mc_matches_trotter_ed_nearest_neighbour_swaps_repulsive():
     _mc_vs_ed(lattices.chain(6, 1.0, False), 4.0, 1.0, 0.1, 2, 1, 5, 20000, ["docc", "ekin", "szz_00", "s_par"],
               seed=1, swap_mode=1)
+
+
+# Left-chain swaps at tau = 0 (a second set of attempts per sweep): the chain
+# samples the same weight, so the same exact values hold.
+def test_mc_matches_trotter_ed_left_swaps_free():
+    _mc_vs_ed(lattices.chain(7), 0.0, 2.0, 0.1, 2, 2, 5, 20000, ["ekin", "szz_00", "s_par"], seed=3, left_swaps=True)
+
+
+def test_mc_matches_trotter_ed_left_swaps_repulsive():
+    _mc_vs_ed(lattices.chain(6), 4.0, 1.0, 0.1, 2, 1, 5, 20000, ["docc", "ekin", "szz_00", "szz_01", "s_par"], seed=1,
+              left_swaps=True)
+
+
+def test_mc_matches_trotter_ed_left_swaps_nearest_neighbour():
+    _mc_vs_ed(lattices.chain(6, 1.0, False), 4.0, 1.0, 0.1, 2, 1, 5, 20000, ["docc", "ekin", "szz_00", "s_par"],
+              seed=1, swap_mode=1, left_swaps=True)
 
 
 def test_missing_hastings_factor_is_detected():
