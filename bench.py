@@ -562,6 +562,21 @@ def main():
                          precision="FP64")
         nsim.close()
 
+    # a second swap phase per sweep at tau = 0 on the left chain (FP64): twice
+    # the Fock-swap attempts, at the cost of one more swap phase
+    left = None
+    if args.workload == WORKLOAD:
+        spl = dict(spec, left_swaps=1)
+        lsim, lper, ltotal, _, lstat, lphases = run(0, spl)
+        left = dict(value=world * upd_per_step * args.steps / (ltotal * 1e-3), unit=UNIT,
+                    swap_accept=float(lstat[3] / max(lstat[2], 1)),
+                    swap_attempts_vs_one_phase=float(lstat[2]) / max(float(dstat[2]), 1.0),
+                    rate_vs_one_phase=(world * upd_per_step * args.steps / (ltotal * 1e-3)) / value,
+                    field_accept=float(lstat[1] / max(lstat[0], 1)), phase_cycle_share=lphases,
+                    swaps="N_up + N_dn attempts after the up pass (tau = beta, right chain) and again after the "
+                          "down pass (tau = 0, left chain)", precision="FP64")
+        lsim.close()
+
     serving = None
     if not args.no_serving and world == 1 and args.workload == WORKLOAD:
         serving = serving_leg(lq, inputs, 1, window_s=args.serving_window)
@@ -581,7 +596,8 @@ def main():
                     field_accept=float(dstat[1] / max(dstat[0], 1)),
                     swap_accept=float(dstat[3] / max(dstat[2], 1)), phase_cycle_share=phases,
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
-                    reduced_precision=mixed, attractive=attractive, neighbour_swaps=neighbour, uneven_flatband=uneven,
+                    reduced_precision=mixed, attractive=attractive, neighbour_swaps=neighbour, left_swaps=left,
+                    uneven_flatband=uneven,
                     serving=serving)
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -131,6 +131,11 @@ typedef struct {
   int32_t precision; /* LQ_FP64, LQ_MIXED or LQ_MIXED_DW */
   uint64_t seed;   /* Philox4x32-10 key */
   int32_t swap_mode; /* Fock-swap target: LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR (0 = uniform) */
+  int32_t left_swaps; /* 0: Fock swaps at tau = beta only, after the up pass (default).  1: also a
+                       * second set of N_up + N_dn attempts at tau = 0 after the down pass, walking
+                       * the left chain (the right chain of the transposed propagator
+                       * B(beta,0)^T, whose weight det[P^T B^T P] is the same).  Other values:
+                       * LQ_EINVAL. */
 } lq_params;
 
 /* Fock-swap proposals.  A swap removes the particle of a uniformly drawn

@@ -349,6 +349,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     if (p.n_stab < 1) return fail(LQ_EINVAL, "n_stab must be >= 1");
     if (p.swap_mode != LQ_SWAP_UNIFORM && p.swap_mode != LQ_SWAP_NEIGHBOUR)
       return fail(LQ_EINVAL, "swap_mode must be LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR");
+    if (p.left_swaps != 0 && p.left_swaps != 1) return fail(LQ_EINVAL, "left_swaps must be 0 or 1");
     if (p.n_up < 0 || p.n_dn < 0 || p.n_up > Lt->N || p.n_dn > Lt->N)
       return fail(LQ_EINVAL, "particle numbers must be in [0, N]");
     if (p.n_up > LQ_MAX_PARTICLES || p.n_dn > LQ_MAX_PARTICLES)
@@ -506,6 +507,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     D.charge = p.U < 0;
     D.prec = prec;
     D.swap_mode = p.swap_mode;
+    D.left_swaps = p.left_swaps;
     D.lambda = std::acosh(std::exp(p.dtau * std::fabs(p.U) / 2.0));
     D.dfac_p = std::exp(D.lambda); D.dfac_m = std::exp(-D.lambda);
     D.delta_p = std::expm1(-2.0 * D.lambda); D.delta_m = std::expm1(2.0 * D.lambda);

@@ -62,6 +62,7 @@ struct LqChainDev {
   float dw_delta_p[2], dw_delta_m[2], dw_cfac_p[2], dw_cfac_m[2];  // double-word forms (LQ_MIXED_DW)
   uint32_t key0, key1, chain_id, sweep;
   int swap_mode;            // LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR
+  int left_swaps;           // 1: a second swap phase at tau = 0 on the left chain after the down pass
   // configuration
   int8_t* s;                // L x N fields, row = slice
   int* occ[2];              // ordered occupied sites (columns of P)

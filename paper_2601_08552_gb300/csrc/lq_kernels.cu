@@ -1544,14 +1544,29 @@ template <class R, bool BIG> __device__ void down_pass(LqChainDev& C, int do_mea
 
 // ---------------------------------------------------------------------------
 // Particle-hole swap for spin sg: remove column k (Givens, Eqs. S9-S12), add
-// site j (Gram-Schmidt twice, Eqs. S1-S8).  T0 = (P^T Q^R_n)^{-1} lives in
+// site j (Gram-Schmidt twice, Eqs. S1-S8).  T0 = (P^T Q_end)^{-1} lives in
 // sm.T[sg].  commit: 1 Metropolis with uniform u, 0 only report (hook).
+//
+// left = 0 walks the right chain at tau = beta: block i = Q^R_i, V^R_i of the
+// current buffer, propagator B_i; the trial goes to the other buffer, which
+// becomes current on acceptance.  left = 1 walks the left chain at tau = 0,
+// read from beta down to 0: it is the right chain of B(beta,0)^T, block i =
+// Q^L_{n-i}, V^L_{n-i}, propagator B_{n-i+1}^T.  Its trial goes, in the left
+// chain's own indexing, to the spare right-chain buffer (the right chain is
+// not needed between the down pass and the next up pass, which rebuilds it
+// from P), and acceptance exchanges the two buffers' pointers.
 // ---------------------------------------------------------------------------
 template <class R>
 __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int commit, Smem& sm,
-                             double log_hastings = 0.0) {
+                             double log_hastings = 0.0, int left = 0) {
   const int N = C.N, m = C.ns[sg], n = C.n, MP = sm.MP, M = sm.M;
   const int cb = C.cur[sg], tb = cb ^ 1;
+  // storage index of walked block i, and the source / trial chains
+  auto six = [&](int i) { return left ? n - i : i; };
+  const R* qsrc = left ? (const R*)C.QL[sg] : (const R*)C.QR[sg][cb];
+  const double* vsrc = left ? C.VL[sg] : C.VR[sg][cb];
+  R* qtrial = (R*)C.QR[sg][tb];
+  double* vtrial = C.VR[sg][tb];
   const size_t pn = (size_t)N * m;
   const int nrot = m - 1 - k, mr = m - 1;
   const int warp = TID >> 5, lane = TID & 31;
@@ -1574,7 +1589,7 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     double logrN = 0.0;
     int sgnrN = 1;
     for (int i = 1; i <= n; ++i) {
-      const double* Vi = vr_mat(C, sg, cb, i);
+      const double* Vi = vsrc + (size_t)six(i) * m * m;
       for (int cc = lane; cc < m; cc += 32) {
         const int src_col = (cc < k) ? cc : (cc < m - 1 ? cc + 1 : k);
         for (int r = 0; r < m; ++r) Am[r * MP + cc] = Vi[r * m + (i == 1 ? src_col : cc)];
@@ -1614,7 +1629,7 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
         }
         __syncwarp();
       }
-      double* Vt = vr_mat(C, sg, tb, i);
+      double* Vt = vtrial + (size_t)six(i) * m * m;
       for (int cc = lane; cc < m; cc += 32)
         for (int r = 0; r < m; ++r) Vt[r * m + cc] = Am[r * MP + cc];
       const double dN = Am[(m - 1) * MP + (m - 1)];
@@ -1653,12 +1668,10 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
   __syncthreads();
   // Q_i' = Q_i G_i^T for all blocks, streamed row by row
   {
-    const R* src0 = (const R*)C.QR[sg][cb];
-    R* dst0 = (R*)C.QR[sg][tb];
     for (size_t idx = TID; idx < (size_t)n * N; idx += LQ_THREADS) {
       const int i = 1 + (int)(idx / N), row = (int)(idx % N);
-      const R* src = src0 + (size_t)i * pn + (size_t)row * m;
-      R* dst = dst0 + (size_t)i * pn + (size_t)row * m;
+      const R* src = qsrc + (size_t)six(i) * pn + (size_t)row * m;
+      R* dst = qtrial + (size_t)six(i) * pn + (size_t)row * m;
       for (int a = 0; a < k; ++a) dst[a] = src[a];
       double x = (double)src[k];
       const double* rr = rot + (size_t)(i - 1) * LQ_NS_MAX * 2;
@@ -1685,10 +1698,17 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
   double logrho = 0.0;
   int valid = sm.ip[9];
   for (int i = 1; i <= n && valid; ++i) {
-    const int lo = bnd(C, i - 1), hi = bnd(C, i);
-    prop<double, double>(C, sg, w, q, 1, 1, lo, 1, -1, sm);
-    for (int l = lo + 1; l < hi; ++l) prop<double, double>(C, sg, w, w, 1, 1, l, 1, -1, sm);
-    R* Qi = qr_panel<R>(C, sg, tb, i);
+    if (!left) {
+      const int lo = bnd(C, i - 1), hi = bnd(C, i);
+      prop<double, double>(C, sg, w, q, 1, 1, lo, 1, -1, sm);
+      for (int l = lo + 1; l < hi; ++l) prop<double, double>(C, sg, w, w, 1, 1, l, 1, -1, sm);
+    } else {
+      // B_{jl}^T with jl = n - i + 1: B_K^T then D_l, l from the block's top down
+      const int lo = bnd(C, n - i), hi = bnd(C, n - i + 1);
+      prop<double, double>(C, sg, w, q, 1, 1, -1, 2, hi - 1, sm);
+      for (int l = hi - 2; l >= lo; --l) prop<double, double>(C, sg, w, w, 1, 1, -1, 2, l, sm);
+    }
+    R* Qi = qtrial + (size_t)six(i) * pn;
     for (int pass = 0; pass < 2; ++pass) {
       double* vv = pass ? v2 : v1;
       gram<double>(Qi, m, mr, w, 1, 1, N, vv, 1);
@@ -1708,7 +1728,7 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
       q[r] = qq;
       Qi[(size_t)r * m + (m - 1)] = (R)qq;
     }
-    double* Vt = vr_mat(C, sg, tb, i);
+    double* Vt = vtrial + (size_t)six(i) * m * m;
     for (int a = TID; a < mr; a += LQ_THREADS) {
       Vt[a * m + (m - 1)] = v1[a] + v2[a];
       Vt[(m - 1) * m + a] = 0.0;
@@ -1720,7 +1740,7 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
   if (TID == 0) C.prof[7] += clock64() - tsub;
   // --- Schur complement s (Eq. S7), ratio, Metropolis, commit ---------------
   if (warp == 0) {
-    const R* Qn = qr_panel<R>(C, sg, tb, n);
+    const R* Qn = qtrial + (size_t)six(n) * pn;
     double s_add = 0.0;
     if (valid) {
       for (int rr = lane; rr < mr; rr += 32) {
@@ -1772,27 +1792,37 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
   if (sm.ip[10]) {
     const int removed = sm.ip[11];
     for (int a = TID; a < m; a += LQ_THREADS) C.occ[sg][a] = occr[a];
-    R* P = qr_panel<R>(C, sg, tb, 0);
+    R* P = qtrial + (size_t)six(0) * pn;
     for (size_t idx = TID; idx < pn; idx += LQ_THREADS) P[idx] = (R)0;
     __syncthreads();
     for (int a = TID; a < m; a += LQ_THREADS) P[(size_t)occr[a] * m + a] = (R)1;
     if (TID == 0) {
       sm.bits[removed >> 5] &= ~(1u << (removed & 31));
       sm.bits[j >> 5] |= 1u << (j & 31);
-      C.cur[sg] = tb;
+      if (!left) {
+        C.cur[sg] = tb;
+      } else {
+        void* qt = C.QL[sg];
+        C.QL[sg] = C.QR[sg][tb];
+        C.QR[sg][tb] = qt;
+        double* vt = C.VL[sg];
+        C.VL[sg] = C.VR[sg][tb];
+        C.VR[sg][tb] = vt;
+      }
     }
   }
   __syncthreads();
 }
 
-// Occupancy bitmap of spin sg, and T0 = (P^T Q^R_n)^{-1} into sm.T[sg].
-template <class R> __device__ void swap_setup(LqChainDev& C, int sg, Smem& sm) {
+// Occupancy bitmap of spin sg, and T0 = (P^T Q^R_n)^{-1} (left = 0) or
+// (P^T Q^L_0)^{-1} (left = 1) into sm.T[sg].
+template <class R> __device__ void swap_setup(LqChainDev& C, int sg, Smem& sm, int left = 0) {
   const int N = C.N, m = C.ns[sg], MP = sm.MP;
   for (int w = TID; w < N / 32 + 1; w += LQ_THREADS) sm.bits[w] = 0u;
   __syncthreads();
   if (TID == 0)
     for (int a = 0; a < m; ++a) sm.bits[C.occ[sg][a] >> 5] |= 1u << (C.occ[sg][a] & 31);
-  const R* Qn = qr_panel<R>(C, sg, C.cur[sg], C.n);
+  const R* Qn = left ? ql_panel<R>(C, sg, 0) : qr_panel<R>(C, sg, C.cur[sg], C.n);
   for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
     int a = idx / m, b = idx - a * m;
     sm.W[a * MP + b] = (double)Qn[(size_t)C.occ[sg][a] * m + b];
@@ -1825,16 +1855,20 @@ __device__ int jth_empty(const Smem& sm, int N, int jidx) {
   return -1;
 }
 
-template <class R> __device__ void swap_phase(LqChainDev& C, Smem& sm) {
+// N_up then N_dn swap attempts: left = 0 at tau = beta on the right chain
+// after the up pass (random-number tag 3), left = 1 at tau = 0 on the left
+// chain after the down pass (tag 6).
+template <class R> __device__ void swap_phase(LqChainDev& C, Smem& sm, int left = 0) {
   PhaseTimer pt_(4);
+  const uint32_t tag = left ? 6u : 3u;
   for (int sg = 0; sg < 2; ++sg) {
     const int m = C.ns[sg];
     if (m == 0 || m == C.N) continue;
-    swap_setup<R>(C, sg, sm);
+    swap_setup<R>(C, sg, sm, left);
     for (int att = 0; att < m; ++att) {
       if (TID == 0) {
         uint32_t w[4], w2[4];
-        const uint32_t c2 = (3u << 24) | ((uint32_t)sg << 16) | (uint32_t)att;
+        const uint32_t c2 = (tag << 24) | ((uint32_t)sg << 16) | (uint32_t)att;
         philox(C.chain_id, C.sweep, c2, 0u, C.key0, C.key1, w);
         philox(C.chain_id, C.sweep, c2, 1u, C.key0, C.key1, w2);
         const int k = (int)(u53(w[0], w[1]) * (double)m);
@@ -1884,8 +1918,10 @@ template <class R> __device__ void swap_phase(LqChainDev& C, Smem& sm) {
         __syncthreads();
         continue;
       }
-      swap_attempt<R>(C, sg, sm.ip[4], sm.ip[5], sm.red[50], 1, sm, sm.red[51]);
+      swap_attempt<R>(C, sg, sm.ip[4], sm.ip[5], sm.red[50], 1, sm, sm.red[51], left);
     }
+    // the next up pass starts the right chain from Q^R_0 = P
+    if (left) fill_P<R>(C, sg, qr_panel<R>(C, sg, C.cur[sg], 0));
   }
 }
 
@@ -1965,6 +2001,7 @@ __global__ void __launch_bounds__(LQ_THREADS, BIG ? 1 : 2)
       up_pass<R, BIG>(C, sm);
       swap_phase<R>(C, sm);
       down_pass<R, BIG>(C, do_measure, sm);
+      if (C.left_swaps) swap_phase<R>(C, sm, 1);
       if (TID == 0) {
         const long long t_now = global_ns();
         C.sweep++;

@@ -64,6 +64,7 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
     return lq_internal_fail(LQ_EINVAL, "n_stab must be >= 1 and particle numbers in [0, N]");
   if (p->swap_mode != LQ_SWAP_UNIFORM && p->swap_mode != LQ_SWAP_NEIGHBOUR)
     return lq_internal_fail(LQ_EINVAL, "swap_mode must be LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR");
+  if (p->left_swaps != 0 && p->left_swaps != 1) return lq_internal_fail(LQ_EINVAL, "left_swaps must be 0 or 1");
   if (p->n_up > LQ_MAX_PARTICLES || p->n_dn > LQ_MAX_PARTICLES)
     return lq_internal_fail(LQ_EUNSUPPORTED, "at most LQ_MAX_PARTICLES particles per spin");
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -150,6 +151,7 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   D.charge = p->U < 0;
   D.prec = p->precision;
   D.swap_mode = p->swap_mode;
+  D.left_swaps = p->left_swaps;
   D.lambda = std::acosh(std::exp(p->dtau * std::fabs(p->U) / 2.0));
   D.dfac_p = std::exp(D.lambda); D.dfac_m = std::exp(-D.lambda);
   D.delta_p = std::expm1(-2.0 * D.lambda); D.delta_m = std::expm1(2.0 * D.lambda);

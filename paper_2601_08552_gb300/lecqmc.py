@@ -48,7 +48,7 @@ class LqError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("U", C.c_double), ("beta", C.c_double), ("dtau", C.c_double), ("n_up", C.c_int32),
                 ("n_dn", C.c_int32), ("n_stab", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64),
-                ("swap_mode", C.c_int32)]
+                ("swap_mode", C.c_int32), ("left_swaps", C.c_int32)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -444,7 +444,7 @@ class Sim:
 def _params_struct(p):
     return Params(float(p["U"]), float(p["beta"]), float(p["dtau"]), int(p["n_up"]), int(p["n_dn"]),
                   int(p["n_stab"]), int(p.get("precision", LQ_FP64)), int(p.get("seed", 0)) & (2**64 - 1),
-                  int(p.get("swap_mode", LQ_SWAP_UNIFORM)))
+                  int(p.get("swap_mode", LQ_SWAP_UNIFORM)), int(p.get("left_swaps", 0)))
 
 
 class Server:
