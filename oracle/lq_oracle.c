@@ -50,10 +50,19 @@
  *     to 0.  det[P^T B(beta,0) P] = det[P^T B(beta,0)^T P], and the left chain
  *     is the right chain of B(beta,0)^T = B_1^T ... B_n^T, so the removal and
  *     addition steps above apply unchanged with B_i -> B_{n-i+1}^T;
+ *   - constrained-path inner loop (SM Sec. VI; orc_cp_walk, not on the CUDA
+ *     path): for a fixed Fock state, independent walkers sample each site's
+ *     field with probability proportional to (1/2) max(0, r(s)), r the
+ *     overlap ratio with the trial P^T e^{-(beta - tau_l) H_0}, carry the
+ *     weight (1/2) sum_s max(0, r(s)) and are dropped at 0.  The paper fixes
+ *     neither the field-sampling law nor population control; this heat-bath
+ *     choice without branching is the plainest one whose mean weight is the
+ *     unconstrained R(eta) whenever nothing is truncated;
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter = (chain, sweep, tag<<24 | slice-or-attempt, site-or-sub);
  *     tags 1/2 up/down field passes, 3 swaps at tau = beta, 4/5 the initial
- *     fields and Fock states, 6 swaps at tau = 0.
+ *     fields and Fock states, 6 swaps at tau = 0, 7 constrained-path fields
+ *     (counter word 0 = walker).
  *
  * Pins (tests/test_oracle_pins.py): Philox known answers, closed-form
  * spectra and the exact flat band, B_K against a matrix exponential,
@@ -62,8 +71,11 @@
  * tracked against fresh weights after sweeps, measurements against dense Wick
  * estimators, exhaustive enumeration against the Trotterized ED, and Monte
  * Carlo against that ED (both swap proposals, with and without the swaps at
- * tau = 0).  Parity unpinned: the average
- * sign at the benchmark sizes, where no exact value exists beyond ED sizes.
+ * tau = 0); the constrained-path walk against the exact R(eta) of the
+ * Trotterized ED where no walker can be truncated (tests/test_oracle_cp.py).
+ * Parity unpinned: the average sign at the benchmark sizes, where no exact
+ * value exists beyond ED sizes, and the constrained-path estimate where the
+ * constraint acts (an approximation with no exact value).
  */
 #include <math.h>
 #include <stdint.h>
@@ -1290,3 +1302,100 @@ void orc_get_families(const orc_sim* S, int* fam) { memcpy(fam, S->fam_of, sizeo
 void orc_set_sweep(orc_sim* S, uint32_t sweep) { S->sweep = sweep; }
 void orc_set_swap_mode(orc_sim* S, int mode) { S->swap_mode = mode; }
 void orc_set_left_swaps(orc_sim* S, int on) { S->left_swaps = on ? 1 : 0; }
+
+/* ------------------------------------------------------------------------ */
+/* Constrained-path inner loop for one Fock state (SM Sec. VI)               */
+/* ------------------------------------------------------------------------ */
+
+/* log|det| and sign of the overlap Psi^T Phi of two N x m panels (m = 0: 1). */
+static void overlap_det(const double* Psi, const double* Phi, int N, int m, double* la, int* sg) {
+  *la = 0.0; *sg = 1;
+  if (m == 0) return;
+  double* W = dalloc((size_t)m * m); double* Wi = dalloc((size_t)m * m);
+  gram(Psi, Phi, N, m, m, W);
+  inv_lu(W, m, Wi, la, sg);
+  free(W); free(Wi);
+}
+
+/* n_walkers independent walkers of the inner loop for the current Fock state
+ * eta (the columns of P), with the fields sampled afresh.  The trial state
+ * at slice l is Psi_l^T = P^T e^{-(beta - tau_l) H_0} = P^T B_K^{L-l}, i.e.
+ * Psi_l = (B_K^T)^{L-l} P: everything that still acts on the walker after
+ * the fields of slice l, with the fields off.  A walker starts at Phi = P
+ * with weight 1.  At each site i of slice l it draws s = +-1 with
+ * probability proportional to (1/2) max(0, r(s)), where
+ * r(s) = prod_sigma det(Psi_l^T D_i(s) Phi) / det(Psi_l^T Phi) (times the
+ * charge-channel scalar e^{-lambda s} for U < 0) is the overlap ratio of the
+ * site's interaction factor, multiplies its weight by
+ * (1/2) [max(0, r(+1)) + max(0, r(-1))] and applies D_i(s) to row i.  After
+ * the slice's fields Phi <- B_K Phi; with the trial advanced one slice that
+ * step leaves the overlap unchanged (ratio 1).  A walker whose factor is 0
+ * has crossed the node of the trial and is dropped (weight 0).  Without such
+ * truncation the mean weight is R(eta) = sum_s 2^{-LN} <eta|U(s)|eta> /
+ * <eta|e^{-beta H_0}|eta>.  Panels are re-orthonormalized (QR, R dropped)
+ * after every slice: every ratio is a ratio of two determinants with the
+ * same panels, so a right factor cancels.  Random numbers: Philox counter
+ * (walker, sweep, 7<<24 | slice, site).  Returns the number of dropped
+ * walkers; weights go to w_out[n_walkers]. */
+int orc_cp_walk(orc_sim* S, int n_walkers, double* w_out) {
+  int N = S->N, L = S->L, dropped = 0;
+  double* Psi[2]; double* Phi[2]; double* Tr[2];
+  double* R = dalloc((size_t)N * N);
+  for (int sg = 0; sg < 2; ++sg) {
+    int m = S->ns[sg];
+    size_t pn = panel(S, sg);
+    Psi[sg] = dalloc((size_t)L * pn);
+    Phi[sg] = dalloc(pn);
+    Tr[sg] = dalloc(pn);
+    double* X = dalloc(pn);
+    fill_P(S, sg, X);
+    for (int l = L - 1; l >= 0; --l) {
+      apply_BKT(S, X, m);
+      qr_pos(X, N, m, R);
+      memcpy(Psi[sg] + (size_t)l * pn, X, sizeof(double) * pn);
+    }
+    free(X);
+  }
+  for (int wk = 0; wk < n_walkers; ++wk) {
+    double weight = 1.0;
+    for (int sg = 0; sg < 2; ++sg) fill_P(S, sg, Phi[sg]);
+    for (int l = 0; l < L && weight > 0.0; ++l) {
+      for (int i = 0; i < N && weight > 0.0; ++i) {
+        double a[2];
+        for (int t = 0; t < 2; ++t) {
+          int8_t s = t ? -1 : 1;
+          double r = S->charge ? exp(-S->lambda * s) : 1.0;
+          for (int sg = 0; sg < 2; ++sg) {
+            int m = S->ns[sg];
+            if (m == 0) continue;
+            const double* Ps = Psi[sg] + (size_t)l * panel(S, sg);
+            double la0, la1; int s0, s1;
+            overlap_det(Ps, Phi[sg], N, m, &la0, &s0);
+            memcpy(Tr[sg], Phi[sg], sizeof(double) * panel(S, sg));
+            for (int c = 0; c < m; ++c) Tr[sg][(size_t)i * m + c] *= dfac(S, sg, s);
+            overlap_det(Ps, Tr[sg], N, m, &la1, &s1);
+            r *= (double)(s0 * s1) * exp(la1 - la0);
+          }
+          a[t] = 0.5 * (r > 0.0 ? r : 0.0);
+        }
+        double tot = a[0] + a[1];
+        if (!(tot > 0.0)) { weight = 0.0; break; }
+        weight *= tot;
+        uint32_t ctr[4] = {(uint32_t)wk, S->sweep, (7u << 24) | (uint32_t)l, (uint32_t)i}, w[4];
+        orc_philox(ctr, S->key, w);
+        int8_t s = (u53(w[0], w[1]) * tot < a[0]) ? 1 : -1;
+        for (int sg = 0; sg < 2; ++sg)
+          for (int c = 0; c < S->ns[sg]; ++c) Phi[sg][(size_t)i * S->ns[sg] + c] *= dfac(S, sg, s);
+      }
+      for (int sg = 0; sg < 2; ++sg) {
+        apply_BK(S, Phi[sg], S->ns[sg]);
+        qr_pos(Phi[sg], N, S->ns[sg], R);
+      }
+    }
+    if (!(weight > 0.0)) { weight = 0.0; dropped++; }
+    w_out[wk] = weight;
+  }
+  for (int sg = 0; sg < 2; ++sg) { free(Psi[sg]); free(Phi[sg]); free(Tr[sg]); }
+  free(R);
+  return dropped;
+}

@@ -76,6 +76,8 @@ def _load():
     lib.orc_get_families.argtypes = [P, ip]
     lib.orc_set_swap_mode.argtypes = [P, C.c_int]
     lib.orc_set_left_swaps.argtypes = [P, C.c_int]
+    lib.orc_cp_walk.argtypes = [P, C.c_int, dp]
+    lib.orc_cp_walk.restype = C.c_int
     lib.orc_set_sweep.argtypes = [P, C.c_uint32]
     _lib = lib
     return lib
@@ -186,6 +188,13 @@ class OracleSim:
         r = self.lib.orc_swap_ratio_side(self.h, 0 if side == "right" else 1, int(spin), int(k), int(j),
                                          _ptr(out, C.c_double))
         return r, out
+
+    def cp_walk(self, n_walkers):
+        """Constrained-path inner loop for the current Fock state: the final
+        weights of n_walkers independent walkers and how many were dropped."""
+        w = np.zeros(max(int(n_walkers), 1))
+        dropped = self.lib.orc_cp_walk(self.h, int(n_walkers), _ptr(w, C.c_double))
+        return w[: int(n_walkers)].copy(), int(dropped)
 
     def measure_at(self, jb, corr=False):
         obs = np.zeros(NOBS)
