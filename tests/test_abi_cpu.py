@@ -1,5 +1,6 @@
 """CPU-only checks of the C ABI: the library builds and loads, exports every
-symbol that include/lecqmc.h declares, and its host-side lattice builders give
+symbol that include/lecqmc.h declares, the binding's ctypes structs have the
+header's fields, sizes and offsets, and its host-side lattice builders give
 the same bond lists and checkerboard families as the oracle's builders."""
 import os
 import re
@@ -65,3 +66,59 @@ def test_lattice_argument_errors(lq):
         lq.Lattice.from_bonds(4, [0], [0], [-1.0])
     with pytest.raises(lq.LqError):
         lq.Lattice.chain(0)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes mirrors of the header's structs have the C sizes
+    and field offsets (a small C program compiled against include/lecqmc.h
+    prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2601_08552_gb300 import lecqmc as b
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    mirrors = {"lq_params": b.Params, "lq_request": b.Request, "lq_result": b.Result,
+               "lq_server_info": b.ServerStats, "lq_allocator": b.Allocator}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lecqmc.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+        # and every field the header declares, in order (padding can hide a missing last field)
+        assert header_fields(cname) == [f for f, _ in py._fields_], cname
+
+
+def header_fields(cname):
+    """Field names of `typedef struct { ... } cname;` in include/lecqmc.h, in order."""
+    txt = open(os.path.join(ROOT, "include", "lecqmc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + r"\s*;", txt)
+    assert m, cname
+    names = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        fp = re.search(r"\(\s*\*\s*(\w+)\s*\)", decl)   # function pointer: ret (*name)(args)
+        if fp:
+            names.append(fp.group(1))
+            continue
+        first, *rest = decl.split(",")
+        names.append(re.search(r"(\w+)\s*(\[[^\]]*\])?\s*$", first).group(1))
+        names += [re.search(r"(\w+)\s*(\[[^\]]*\])?\s*$", r).group(1) for r in rest]
+    return names
