@@ -54,15 +54,18 @@
  *     path): for a fixed Fock state, independent walkers sample each site's
  *     field with probability proportional to (1/2) max(0, r(s)), r the
  *     overlap ratio with the trial P^T e^{-(beta - tau_l) H_0}, carry the
- *     weight (1/2) sum_s max(0, r(s)) and are dropped at 0.  The paper fixes
- *     neither the field-sampling law nor population control; this heat-bath
- *     choice without branching is the plainest one whose mean weight is the
- *     unconstrained R(eta) whenever nothing is truncated;
+ *     weight (1/2) sum_s max(0, r(s)) and are dropped at 0; orc_cp_population
+ *     adds branching by systematic (comb) resampling every few slices, the
+ *     estimate being the product of the population's mean weights.  The paper
+ *     fixes neither the field-sampling law nor population control; these are
+ *     the plainest choices whose estimate has the unconstrained R(eta) as its
+ *     mean whenever nothing is truncated;
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter = (chain, sweep, tag<<24 | slice-or-attempt, site-or-sub);
  *     tags 1/2 up/down field passes, 3 swaps at tau = beta, 4/5 the initial
  *     fields and Fock states, 6 swaps at tau = 0, 7 constrained-path fields
- *     (counter word 0 = walker).
+ *     (counter word 0 = walker), 8 and 9 the fields and the comb of a
+ *     branching population.
  *
  * Pins (tests/test_oracle_pins.py): Philox known answers, closed-form
  * spectra and the exact flat band, B_K against a matrix exponential,
@@ -1317,85 +1320,165 @@ static void overlap_det(const double* Psi, const double* Phi, int N, int m, doub
   free(W); free(Wi);
 }
 
-/* n_walkers independent walkers of the inner loop for the current Fock state
- * eta (the columns of P), with the fields sampled afresh.  The trial state
- * at slice l is Psi_l^T = P^T e^{-(beta - tau_l) H_0} = P^T B_K^{L-l}, i.e.
- * Psi_l = (B_K^T)^{L-l} P: everything that still acts on the walker after
- * the fields of slice l, with the fields off.  A walker starts at Phi = P
- * with weight 1.  At each site i of slice l it draws s = +-1 with
- * probability proportional to (1/2) max(0, r(s)), where
- * r(s) = prod_sigma det(Psi_l^T D_i(s) Phi) / det(Psi_l^T Phi) (times the
- * charge-channel scalar e^{-lambda s} for U < 0) is the overlap ratio of the
- * site's interaction factor, multiplies its weight by
- * (1/2) [max(0, r(+1)) + max(0, r(-1))] and applies D_i(s) to row i.  After
- * the slice's fields Phi <- B_K Phi; with the trial advanced one slice that
- * step leaves the overlap unchanged (ratio 1).  A walker whose factor is 0
- * has crossed the node of the trial and is dropped (weight 0).  Without such
- * truncation the mean weight is R(eta) = sum_s 2^{-LN} <eta|U(s)|eta> /
- * <eta|e^{-beta H_0}|eta>.  Panels are re-orthonormalized (QR, R dropped)
- * after every slice: every ratio is a ratio of two determinants with the
- * same panels, so a right factor cancels.  Random numbers: Philox counter
- * (walker, sweep, 7<<24 | slice, site).  Returns the number of dropped
- * walkers; weights go to w_out[n_walkers]. */
-int orc_cp_walk(orc_sim* S, int n_walkers, double* w_out) {
-  int N = S->N, L = S->L, dropped = 0;
-  double* Psi[2]; double* Phi[2]; double* Tr[2];
-  double* R = dalloc((size_t)N * N);
+/* Trial panels Psi_l = (B_K^T)^{L-l} P, l = 0..L-1, per spin (N x m each,
+ * columns orthonormalized: a right factor cancels in every ratio). */
+static void cp_trials(const orc_sim* S, double* Psi[2]) {
+  double* R = dalloc((size_t)S->N * S->N);
   for (int sg = 0; sg < 2; ++sg) {
     int m = S->ns[sg];
     size_t pn = panel(S, sg);
-    Psi[sg] = dalloc((size_t)L * pn);
-    Phi[sg] = dalloc(pn);
-    Tr[sg] = dalloc(pn);
+    Psi[sg] = dalloc((size_t)S->L * pn);
     double* X = dalloc(pn);
     fill_P(S, sg, X);
-    for (int l = L - 1; l >= 0; --l) {
+    for (int l = S->L - 1; l >= 0; --l) {
       apply_BKT(S, X, m);
-      qr_pos(X, N, m, R);
+      qr_pos(X, S->N, m, R);
       memcpy(Psi[sg] + (size_t)l * pn, X, sizeof(double) * pn);
     }
     free(X);
   }
+  free(R);
+}
+
+/* One walker through slice l: at each site i draw s = +-1 with probability
+ * proportional to (1/2) max(0, r(s)), r(s) = prod_sigma
+ * det(Psi_l^T D_i(s) Phi) / det(Psi_l^T Phi) (times the charge-channel scalar
+ * e^{-lambda s} for U < 0), multiply the weight by
+ * (1/2) [max(0, r(+1)) + max(0, r(-1))] and apply D_i(s) to row i; then
+ * Phi <- B_K Phi and re-orthonormalize (with the trial advanced one slice the
+ * kinetic step leaves the overlap unchanged, and a right factor of Phi
+ * cancels in every ratio).  Philox counter (c0, c1, tag<<24 | l, i).
+ * Returns the slice's weight factor; 0 drops the walker (Phi then unused). */
+static double cp_slice(const orc_sim* S, double* const Psi[2], double* Phi[2], double* Tr[2], int l, uint32_t c0,
+                       uint32_t c1, uint32_t tag) {
+  int N = S->N;
+  double factor = 1.0;
+  for (int i = 0; i < N; ++i) {
+    double a[2];
+    for (int t = 0; t < 2; ++t) {
+      int8_t s = t ? -1 : 1;
+      double r = S->charge ? exp(-S->lambda * s) : 1.0;
+      for (int sg = 0; sg < 2; ++sg) {
+        int m = S->ns[sg];
+        if (m == 0) continue;
+        const double* Ps = Psi[sg] + (size_t)l * panel(S, sg);
+        double la0, la1; int s0, s1;
+        overlap_det(Ps, Phi[sg], N, m, &la0, &s0);
+        memcpy(Tr[sg], Phi[sg], sizeof(double) * panel(S, sg));
+        for (int c = 0; c < m; ++c) Tr[sg][(size_t)i * m + c] *= dfac(S, sg, s);
+        overlap_det(Ps, Tr[sg], N, m, &la1, &s1);
+        r *= (double)(s0 * s1) * exp(la1 - la0);
+      }
+      a[t] = 0.5 * (r > 0.0 ? r : 0.0);
+    }
+    double tot = a[0] + a[1];
+    if (!(tot > 0.0)) return 0.0;
+    factor *= tot;
+    uint32_t ctr[4] = {c0, c1, (tag << 24) | (uint32_t)l, (uint32_t)i}, w[4];
+    orc_philox(ctr, S->key, w);
+    int8_t s = (u53(w[0], w[1]) * tot < a[0]) ? 1 : -1;
+    for (int sg = 0; sg < 2; ++sg)
+      for (int c = 0; c < S->ns[sg]; ++c) Phi[sg][(size_t)i * S->ns[sg] + c] *= dfac(S, sg, s);
+  }
+  double* R = dalloc((size_t)N * N);
+  for (int sg = 0; sg < 2; ++sg) {
+    apply_BK(S, Phi[sg], S->ns[sg]);
+    qr_pos(Phi[sg], N, S->ns[sg], R);
+  }
+  free(R);
+  return factor;
+}
+
+/* n_walkers independent walkers of the inner loop for the current Fock state
+ * eta (the columns of P), with the fields sampled afresh.  The trial state
+ * at slice l is Psi_l^T = P^T e^{-(beta - tau_l) H_0} = P^T B_K^{L-l}: all
+ * that still acts on the walker after the fields of slice l, with the fields
+ * off.  A walker starts at Phi = P with weight 1 and goes through the slices
+ * (cp_slice); a walker whose factor is 0 has crossed the node of the trial
+ * and is dropped (weight 0).  Without such truncation the mean weight is
+ * R(eta) = sum_s 2^{-LN} <eta|U(s)|eta> / <eta|e^{-beta H_0}|eta>.  Random
+ * numbers: Philox counter (walker, sweep, 7<<24 | slice, site).  Returns the
+ * number of dropped walkers; weights go to w_out[n_walkers]. */
+int orc_cp_walk(orc_sim* S, int n_walkers, double* w_out) {
+  int dropped = 0;
+  double* Psi[2]; double* Phi[2]; double* Tr[2];
+  cp_trials(S, Psi);
+  for (int sg = 0; sg < 2; ++sg) { Phi[sg] = dalloc(panel(S, sg)); Tr[sg] = dalloc(panel(S, sg)); }
   for (int wk = 0; wk < n_walkers; ++wk) {
     double weight = 1.0;
     for (int sg = 0; sg < 2; ++sg) fill_P(S, sg, Phi[sg]);
-    for (int l = 0; l < L && weight > 0.0; ++l) {
-      for (int i = 0; i < N && weight > 0.0; ++i) {
-        double a[2];
-        for (int t = 0; t < 2; ++t) {
-          int8_t s = t ? -1 : 1;
-          double r = S->charge ? exp(-S->lambda * s) : 1.0;
-          for (int sg = 0; sg < 2; ++sg) {
-            int m = S->ns[sg];
-            if (m == 0) continue;
-            const double* Ps = Psi[sg] + (size_t)l * panel(S, sg);
-            double la0, la1; int s0, s1;
-            overlap_det(Ps, Phi[sg], N, m, &la0, &s0);
-            memcpy(Tr[sg], Phi[sg], sizeof(double) * panel(S, sg));
-            for (int c = 0; c < m; ++c) Tr[sg][(size_t)i * m + c] *= dfac(S, sg, s);
-            overlap_det(Ps, Tr[sg], N, m, &la1, &s1);
-            r *= (double)(s0 * s1) * exp(la1 - la0);
-          }
-          a[t] = 0.5 * (r > 0.0 ? r : 0.0);
-        }
-        double tot = a[0] + a[1];
-        if (!(tot > 0.0)) { weight = 0.0; break; }
-        weight *= tot;
-        uint32_t ctr[4] = {(uint32_t)wk, S->sweep, (7u << 24) | (uint32_t)l, (uint32_t)i}, w[4];
-        orc_philox(ctr, S->key, w);
-        int8_t s = (u53(w[0], w[1]) * tot < a[0]) ? 1 : -1;
-        for (int sg = 0; sg < 2; ++sg)
-          for (int c = 0; c < S->ns[sg]; ++c) Phi[sg][(size_t)i * S->ns[sg] + c] *= dfac(S, sg, s);
-      }
-      for (int sg = 0; sg < 2; ++sg) {
-        apply_BK(S, Phi[sg], S->ns[sg]);
-        qr_pos(Phi[sg], N, S->ns[sg], R);
-      }
-    }
+    for (int l = 0; l < S->L && weight > 0.0; ++l) weight *= cp_slice(S, Psi, Phi, Tr, l, (uint32_t)wk, S->sweep, 7u);
     if (!(weight > 0.0)) { weight = 0.0; dropped++; }
     w_out[wk] = weight;
   }
   for (int sg = 0; sg < 2; ++sg) { free(Psi[sg]); free(Phi[sg]); free(Tr[sg]); }
-  free(R);
   return dropped;
+}
+
+/* Systematic ("comb") resampling (Kitagawa 1996): n new walkers from n old
+ * ones with weights w (total > 0), one uniform u in [0, 1): new walker k
+ * copies the first old walker whose cumulative weight exceeds (k + u)/n of
+ * the total.  Old walker j is copied floor or ceil of n w_j / sum(w) times,
+ * and n w_j / sum(w) times on average over u; weight-0 walkers never. */
+void orc_comb(const double* w, int n, double u, int* src_out) {
+  double tot = 0.0;
+  for (int j = 0; j < n; ++j) tot += w[j];
+  double cum = w[0];
+  for (int k = 0, src = 0; k < n; ++k) {
+    double pos = (k + u) / n * tot;
+    while (src < n - 1 && cum <= pos) cum += w[++src];
+    src_out[k] = src;
+  }
+}
+
+/* A branching population of n_walkers for the current Fock state: the
+ * walkers go through the slices as in orc_cp_walk; after every comb_every
+ * slices (and after the last) the population's mean weight joins the
+ * estimate, and n_walkers new walkers are drawn from the old ones with
+ * probabilities proportional to their weights (orc_comb).  New walkers carry weight 1; dropped walkers (weight 0) are never drawn.
+ * The estimate of R(eta) is the product of the mean weights, an unbiased
+ * estimator of the unconstrained R(eta) when nothing is truncated (the
+ * normalizing-constant property of sequential Monte Carlo).  run selects
+ * the random numbers: Philox counters (slot, run, 8<<24 | slice, site) for
+ * the fields and (run, 0xFFFFFFFD, 9<<24 | slice, 0) for the comb.  Returns
+ * log of the estimate (-inf when every walker was dropped). */
+double orc_cp_population(orc_sim* S, int n_walkers, int comb_every, uint32_t run) {
+  double* Psi[2]; double* Phi[2]; double* Nw[2]; double* Tr[2];
+  cp_trials(S, Psi);
+  for (int sg = 0; sg < 2; ++sg) {
+    Phi[sg] = dalloc((size_t)n_walkers * panel(S, sg));
+    Nw[sg] = dalloc((size_t)n_walkers * panel(S, sg));
+    Tr[sg] = dalloc(panel(S, sg));
+    for (int k = 0; k < n_walkers; ++k) fill_P(S, sg, Phi[sg] + (size_t)k * panel(S, sg));
+  }
+  double* w = dalloc(n_walkers);
+  int* src = (int*)calloc(n_walkers, sizeof(int));
+  for (int k = 0; k < n_walkers; ++k) w[k] = 1.0;
+  double log_est = 0.0;
+  for (int l = 0; l < S->L; ++l) {
+    for (int k = 0; k < n_walkers; ++k) {
+      if (!(w[k] > 0.0)) continue;
+      double* Pk[2] = {Phi[0] + (size_t)k * panel(S, 0), Phi[1] + (size_t)k * panel(S, 1)};
+      w[k] *= cp_slice(S, Psi, Pk, Tr, l, (uint32_t)k, run, 8u);
+    }
+    if ((comb_every > 0 && (l + 1) % comb_every == 0) || l == S->L - 1) {
+      double tot = 0.0;
+      for (int k = 0; k < n_walkers; ++k) tot += w[k];
+      if (!(tot > 0.0)) { log_est = -INFINITY; break; }
+      log_est += log(tot / n_walkers);
+      if (l == S->L - 1) break;
+      uint32_t ctr[4] = {run, 0xFFFFFFFDu, (9u << 24) | (uint32_t)l, 0u}, rw[4];
+      orc_philox(ctr, S->key, rw);
+      orc_comb(w, n_walkers, u53(rw[0], rw[1]), src);
+      for (int k = 0; k < n_walkers; ++k)
+        for (int sg = 0; sg < 2; ++sg)
+          memcpy(Nw[sg] + (size_t)k * panel(S, sg), Phi[sg] + (size_t)src[k] * panel(S, sg),
+                 sizeof(double) * panel(S, sg));
+      for (int sg = 0; sg < 2; ++sg) { double* t = Phi[sg]; Phi[sg] = Nw[sg]; Nw[sg] = t; }
+      for (int k = 0; k < n_walkers; ++k) w[k] = 1.0;
+    }
+  }
+  for (int sg = 0; sg < 2; ++sg) { free(Psi[sg]); free(Phi[sg]); free(Nw[sg]); free(Tr[sg]); }
+  free(w); free(src);
+  return log_est;
 }

@@ -78,6 +78,9 @@ def _load():
     lib.orc_set_left_swaps.argtypes = [P, C.c_int]
     lib.orc_cp_walk.argtypes = [P, C.c_int, dp]
     lib.orc_cp_walk.restype = C.c_int
+    lib.orc_cp_population.argtypes = [P, C.c_int, C.c_int, C.c_uint32]
+    lib.orc_cp_population.restype = C.c_double
+    lib.orc_comb.argtypes = [dp, C.c_int, C.c_double, ip]
     lib.orc_set_sweep.argtypes = [P, C.c_uint32]
     _lib = lib
     return lib
@@ -85,6 +88,16 @@ def _load():
 
 def _ptr(a, ct):
     return a.ctypes.data_as(C.POINTER(ct))
+
+
+def comb(w, u):
+    """Systematic resampling of the oracle: indices of the old walkers that
+    the len(w) new walkers copy, for one uniform u in [0, 1)."""
+    lib = _load()
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros(len(w), dtype=np.int32)
+    lib.orc_comb(_ptr(w, C.c_double), len(w), float(u), _ptr(out, C.c_int))
+    return out
 
 
 def philox4x32_10(ctr, key):
@@ -195,6 +208,11 @@ class OracleSim:
         w = np.zeros(max(int(n_walkers), 1))
         dropped = self.lib.orc_cp_walk(self.h, int(n_walkers), _ptr(w, C.c_double))
         return w[: int(n_walkers)].copy(), int(dropped)
+
+    def cp_population(self, n_walkers, comb_every, run=0):
+        """Branching population with comb resampling every comb_every slices:
+        log of its estimate of R(eta) (-inf if every walker was dropped)."""
+        return float(self.lib.orc_cp_population(self.h, int(n_walkers), int(comb_every), int(run)))
 
     def measure_at(self, jb, corr=False):
         obs = np.zeros(NOBS)

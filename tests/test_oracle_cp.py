@@ -102,3 +102,52 @@ def test_cp_walk_weights_nonnegative_with_constraint():
     w, dropped = _walk(lattices.chain(6), 4.0, 1.0, 0.1, (0, 1), (2, 4), 2000)
     assert np.all(np.isfinite(w)) and np.all(w >= 0.0)
     assert dropped == int(np.sum(w == 0.0))
+
+
+def _population(lat, U, beta, dtau, up, dn, n_walkers, comb_every, runs, seed=5):
+    o = OracleSim(lat, U, beta, dtau, len(up), len(dn), 4, seed=seed)
+    o.set_fock(np.array(up), np.array(dn))
+    return np.exp([o.cp_population(n_walkers, comb_every, run=r) for r in runs])
+
+
+@pytest.mark.parametrize("comb_every", [1, 3])
+def test_cp_population_with_comb_is_unbiased(comb_every):
+    """Branching populations (systematic resampling every comb_every slices):
+    the product of the population's mean weights averages to the exact R(eta)
+    where nothing is truncated."""
+    lat, U, beta, dtau = lattices.chain(6), -3.0, 0.6, 0.1
+    up = dn = (0, 3)
+    est = _population(lat, U, beta, dtau, up, dn, 8, comb_every, range(3000))
+    assert np.all(est > 0)
+    _assert_unbiased(est, exact_ratio(lat, U, dtau, 6, up, dn))
+
+
+def test_cp_population_one_particle_per_spin():
+    lat, U, beta, dtau = lattices.chain(6), 4.0, 0.8, 0.1
+    up, dn = (1,), (4,)
+    est = _population(lat, U, beta, dtau, up, dn, 8, 2, range(2000))
+    _assert_unbiased(est, exact_ratio(lat, U, dtau, 8, up, dn))
+
+
+def test_comb_resampling_law():
+    """Systematic resampling: n new walkers, old walker j copied floor or ceil
+    of n w_j / W times (never when w_j = 0), and n w_j / W times on average
+    over the uniform (checked exactly on a fine grid of u)."""
+    from oracle import comb
+
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 16):
+        w = rng.exponential(size=n)
+        if n > 2:
+            w[[1, n - 1]] = 0.0
+        expect = n * w / w.sum()
+        grid = (np.arange(4096) + 0.5) / 4096
+        mean = np.zeros(n)
+        for u in grid:
+            src = comb(w, u)
+            assert len(src) == n and np.all(np.diff(src) >= 0)
+            cnt = np.bincount(src, minlength=n)
+            assert np.all((cnt == np.floor(expect)) | (cnt == np.ceil(expect)))
+            assert np.all(cnt[w == 0] == 0)
+            mean += cnt / len(grid)
+        assert np.max(np.abs(mean - expect)) < 2.0 / 4096
