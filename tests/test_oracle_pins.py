@@ -223,9 +223,17 @@ def test_tracked_weight_equals_fresh_with_left_swaps(case):
     assert st_[2] == 8 * sum(m for m in (nu, nd) if 0 < m < o.N)
 
 
-def test_measure_matches_dense_wick():
-    lat, U, beta, dtau = lattices.chain(6), 4.0, 1.0, 0.1
-    o = OracleSim(lat, U, beta, dtau, 2, 1, 3, seed=3)
+WICK_CASES = [
+    (lattices.chain(6), 4.0, 1.0, 0.1, 2, 1, 3),
+    (lattices.square(3, 2), -4.0, 0.8, 0.1, 2, 2, 3),     # charge channel
+    (lattices.flatband(3), 2.0, 1.0, 0.1, 2, 2, 4),       # two sublattices
+]
+
+
+@pytest.mark.parametrize("case", range(len(WICK_CASES)))
+def test_measure_matches_dense_wick(case):
+    lat, U, beta, dtau, nu, nd, tw = WICK_CASES[case]
+    o = OracleSim(lat, U, beta, dtau, nu, nd, tw, seed=3 + case)
     s = o.get_fields()
     up, dn = o.get_fock()
     for jb in range(o.n + 1):
