@@ -208,7 +208,7 @@ def kernel_source_hash():
     import re
 
     h = hashlib.sha256()
-    for f in ("lq_device.h", "lq_kernels.cu", "lq_kernels.h"):
+    for f in ("lq_device.h", "lq_sweep.cuh", "lq_kernels.cu", "lq_kernels.h"):
         with open(os.path.join(ROOT, "paper_2601_08552_gb300", "csrc", f), encoding="utf-8") as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
