@@ -32,10 +32,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "HS field updates/sec & sweeps/sec vs plain FP64 same GPU; p50/p99 sweep latency"
 UNIT = "field-updates/s"
-# GB300 dense FP64 on the CUDA cores: one FP64 warp instruction per 64 cycles per sub-partition
-# (tests/fp64_cost_probe.cu) = 0.5 FMA/cycle x 4 sub-partitions x 152 SMs x 2.07 GHz x 2 flops
-# = 1.26 TFLOP/s, NVIDIA's nominal 1.25; an FMA loop sustains 1.19
-FP64_PEAK_TFLOPS = 1.25
+# The FP64 roof is measured in the run (lq_device_fp64_rate: independent FMA chains on every SM, CUDA
+# events).  Only if that probe fails does the line fall back to the unit-count figure: 0.5 FP64 FMA per
+# cycle per sub-partition x 4 x 152 SMs x 2.07 GHz x 2 flops = 1.26 TFLOP/s.
+FP64_FALLBACK_TFLOPS = 1.26
 WORKLOAD = "gas32x32"
 
 
@@ -95,8 +95,17 @@ class OraclePool:
             p.join(timeout=10)
 
 
+def host_cores():
+    """Cores this process may run on (nproc)."""
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+ORACLE_CAP = 16
+
+
 def oracle_cores():
-    return max(1, min(16, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()))
+    """Oracle processes: one per host core, at most ORACLE_CAP."""
+    return max(1, min(ORACLE_CAP, host_cores()))
 
 
 def run_reference(args, spec, n_chains):
@@ -121,22 +130,30 @@ def run_reference(args, spec, n_chains):
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=workload_desc(spec, n_chains), sample=sample),
                 sweeps_per_s=P * args.steps / tot,
-                cpu_baseline=dict(value=value, unit=UNIT, cores=P, kind="oracle", sample=sample),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=P, nproc=host_cores(), core_cap=ORACLE_CAP,
+                                  kind="oracle", sample=sample),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(spec, n_chains):
+def cpu_baseline(spec, n_chains, target_s=12.0):
+    """The oracle as it stands on the host cores: one single-threaded process
+    per core (P = nproc, at most ORACLE_CAP), each sweeping its own chain of
+    the workload; one untimed sweep, then as many timed sweeps as fill about
+    target_s of wall time."""
     from paper_2601_08552_gb300 import inputs
 
     P = oracle_cores()
     pool = OraclePool(spec, inputs.SEED0, P)
     upd = 2 * round(spec["beta"] / spec["dtau"]) * spec["lattice"][1] * spec["lattice"][2]
-    dt, res = pool.step(1)
+    dt1, _ = pool.step(1)
+    k = max(2, min(200, int(target_s / max(dt1, 1e-3))))
+    dt, _ = pool.step(k)
     pool.close()
-    sample = "%d chains of the %d-chain workload, 1 sweep each, one process per host core (%.1f s wall)" % (
-        P, n_chains, dt)
-    return dict(value=P * upd / dt, unit=UNIT, cores=P, kind="oracle", sample=sample)
+    sample = ("%d chains of the %d-chain workload (one process per host core), %d timed sweeps each after one "
+              "untimed, %.1f s wall" % (P, n_chains, k, dt))
+    return dict(value=P * upd * k / dt, unit=UNIT, cores=P, nproc=host_cores(), core_cap=ORACLE_CAP, kind="oracle",
+                sample=sample, sweeps_per_s=P * k / dt)
 
 
 # ---------------------------------------------------------------------------
@@ -215,6 +232,19 @@ def kernel_source_hash():
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
+
+
+def measured_fp64_peak(lq):
+    """The FP64 roof measured in this run by lq_device_fp64_rate (independent
+    FMA chains on every SM, grown to about 300 ms, CUDA events), else the
+    unit-count figure."""
+    try:
+        t, cyc = lq.device_fp64_rate(300.0)
+        return t, ("measured in this run: lq_device_fp64_rate, FP64 FMA chains on every SM, CUDA events "
+                   "(%.3f TFLOP/s)" % t), cyc
+    except Exception as e:  # the probe failed: say so and use the unit-count figure
+        return FP64_FALLBACK_TFLOPS, "fallback (probe failed: %s): 0.5 FMA/cycle/sub-partition x 4 x 152 x " \
+                                     "2.07 GHz x 2" % e, None
 
 
 def measured_hbm_gbs():
@@ -341,6 +371,71 @@ def uneven_leg(lq, inputs, torch, stream, prec=0, n_chains=608, steps=2, warmup=
                     "beta U[1, 4], dtau 0.05, U=2, half periodic")
 
 
+def gas64_leg(lq, inputs, torch, stream, fp64_peak, warmup=1, steps=2, n_chains=None):
+    """The mixed-precision configuration at full size: 64x64 periodic square
+    (N = 4096), N_up = N_dn = 16, U = +4, beta = 16 (L = 320), QR every 8
+    slices, 512 chains in one launch.  FP64, LQ_MIXED (FP32 panels, FP64
+    algebra and ratios) and LQ_MIXED_DW run from identical seeded states (same
+    seeds, so the same initial fields and Fock states); each reports its rate,
+    its ratio to FP64, the log-weight error of its freshly built chains
+    against FP64's on those states, and its chain-mean observables against
+    FP64's in standard errors."""
+    w = inputs.WORKLOADS["gas64x64"]
+    spec = {k: w[k] for k in ("lattice", "U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
+    n = n_chains or w["chains"]
+    lat = lq.Lattice.square(64, 64)
+    N, L = lat.N, round(spec["beta"] / spec["dtau"])
+    upd = n * 2 * L * N
+    out, lw0, obs = {}, {}, {}
+    for prec, key in ((0, "fp64"), (1, "mixed"), (2, "mixed_dw")):
+        sim = lq.Sim([lat] * n, [dict(spec, precision=prec, seed=inputs.SEED0)] * n, stream=stream.cuda_stream)
+        sim.init()
+        lw0[prec] = np.array([sim.log_weight(c)[0] for c in range(4)])
+        for _ in range(warmup):
+            sim.sweep(1, measure=True)
+        sim.sync()
+        st0 = sum(sim.stats(c) for c in range(n))
+        pr0 = sum(sim.profile(c) for c in range(n))
+        per = time_steps(torch, sim, steps, stream)
+        sim.sync()
+        d = sum(sim.stats(c) for c in range(n)) - st0
+        pr = sum(sim.profile(c) for c in range(n)) - pr0
+        tot = max(float(pr[:6].sum()), 1.0)
+        shares = {k: round(float(pr[i]) / tot, 4) for i, k in
+                  enumerate(["flips", "propagation", "qr", "block_inverse", "swaps", "measure"])}
+        obs[prec] = np.stack([sim.records(c).mean(axis=0) for c in range(n)])
+        ms = float(np.mean(per))
+        r = dict(value=upd / (ms * 1e-3), unit=UNIT, sweeps_per_s=n / (ms * 1e-3), ms_per_sweep=ms,
+                 field_accept=float(d[1] / max(d[0], 1)), swap_accept=float(d[3] / max(d[2], 1)),
+                 phase_cycle_share=shares)
+        if prec < 2:  # LQ_MIXED_DW runs the flip algebra in double-word FP32, not on the FP64 pipe
+            flops = algorithmic_fp64_flops(spec, n, d[1], d[0], lat.n_bonds, prec)
+            r["fp64_alu"] = dict(achieved=flops / (ms * 1e-3) / 1e12, peak=fp64_peak, unit="TFLOP/s",
+                                 frac=flops / (ms * 1e-3) / 1e12 / fp64_peak)
+        # propagation streams every N x N_sigma panel through the SM once per slice and
+        # panel (read and write): its bytes over the wall time the phase takes
+        b = 4 if prec else 8
+        prop_bytes = n * sum(4 * L * 2 * N * m * b for m in (spec["n_up"], spec["n_dn"]))
+        prop_s = ms * 1e-3 * shares["propagation"]
+        hbm_peak, _ = measured_hbm_gbs()
+        r["propagation_effective_gbs"] = dict(achieved=prop_bytes / max(prop_s, 1e-12) / 1e9, peak=hbm_peak,
+                                              frac=prop_bytes / max(prop_s, 1e-12) / 1e9 / hbm_peak,
+                                              note="panel bytes (read + write per slice) over the sweep time "
+                                                   "times the propagation share of the cycles")
+        if prec:
+            r["speedup_vs_fp64"] = r["value"] / out["fp64"]["value"]
+            r["logw_max_rel_err_vs_fp64"] = float(np.max(np.abs(lw0[prec] - lw0[0]) /
+                                                         np.maximum(1.0, np.abs(lw0[0]))))
+            r["observables_vs_fp64"] = observable_deviation(obs[prec], obs[0])
+        out[key] = r
+        sim.close()
+        del sim
+    out["workload"] = ("64x64 periodic square, t=1, U=+4, beta=16, dtau=0.05 (L=320), N_up=N_dn=16, QR every 8, "
+                       "%d chains in one launch; %d warm-up and %d timed sweeps per precision, identical seeded "
+                       "initial states" % (n, warmup, steps))
+    return out
+
+
 def observable_deviation(a, b):
     """Chain-mean observables of two runs from the same seeded states: the
     largest |difference| over the measured observables in units of the
@@ -381,6 +476,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-gas64", action="store_true", help="skip the 64x64 mixed-precision leg (512 chains)")
     ap.add_argument("--serving-window", type=float, default=10.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=["gas32x32", "gas64x64"],
                     help="gas64x64: the 64x64 mixed-precision comparison (512 chains, ~10 s per sweep)")
@@ -472,11 +568,11 @@ def main():
     flops = algorithmic_fp64_flops(spec, n_chains, dstat[1], dstat[0], lat.n_bonds, 0)
     kern_ms = total_ms / args.steps
     achieved = flops / (kern_ms * 1e-3) / 1e12
-    roofline = dict(bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                    frac=achieved / FP64_PEAK_TFLOPS, traffic=profiled_traffic("fp64_bytes_per_launch"),
-                    kernel="lq::sweep_kernel<double, false>", flops_per_launch=flops,
-                    peak_source="GB300 dense FP64: 0.5 FMA/cycle/sub-partition x 4 x 152 SMs x 2.07 GHz x 2 = 1.26 TFLOP/s "
-                                "(nominal 1.25); an FMA loop sustains 1.19")
+    fp64_peak, peak_src, issue = measured_fp64_peak(lq)
+    roofline = dict(bound="alu", achieved=achieved, peak=fp64_peak, unit="TFLOP/s",
+                    frac=achieved / fp64_peak, traffic=profiled_traffic("fp64_bytes_per_launch"),
+                    kernel="lq::sweep_kernel<double, false>", flops_per_launch=flops, peak_source=peak_src,
+                    fp64_issue_cycles=issue)
     if roofline["traffic"]:
         # the same kernel against DRAM: profiled bytes per launch over the launch time
         hbm_peak, hbm_src = measured_hbm_gbs()
@@ -577,9 +673,19 @@ def main():
                           "down pass (tau = 0, left chain)", precision="FP64")
         lsim.close()
 
+    gas64 = None
+    if not args.no_gas64 and args.workload == WORKLOAD:
+        gas64 = gas64_leg(lq, inputs, torch, stream, roofline["peak"])
+
     serving = None
     if not args.no_serving and world == 1 and args.workload == WORKLOAD:
+        # the same request stream served in LQ_MIXED and in plain FP64
         serving = serving_leg(lq, inputs, 1, window_s=args.serving_window)
+        serving_fp64 = serving_leg(lq, inputs, 0, window_s=args.serving_window)
+        serving["fp64"] = {k: serving_fp64[k] for k in ("updates_per_s", "p50_sweep_ms", "p99_sweep_ms",
+                                                        "request_p50_ms", "request_p99_ms", "completed", "wall_s",
+                                                        "device_busy_s")}
+        serving["mixed_vs_fp64_updates"] = serving["updates_per_s"] / max(serving_fp64["updates_per_s"], 1e-9)
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -597,7 +703,7 @@ def main():
                     swap_accept=float(dstat[3] / max(dstat[2], 1)), phase_cycle_share=phases,
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
                     reduced_precision=mixed, attractive=attractive, neighbour_swaps=neighbour, left_swaps=left,
-                    uneven_flatband=uneven,
+                    uneven_flatband=uneven, gas64x64=gas64,
                     serving=serving)
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -78,7 +78,7 @@ typedef enum {
 #define LQ_OBS_SPAR 8  /* S^par(q=0) = (1/(N/2)) sum_ij <S^x_i S^x_j + S^y_i S^y_j> */
 
 /* largest particle number per spin the library supports */
-#define LQ_MAX_PARTICLES 256
+#define LQ_MAX_PARTICLES 512
 
 typedef struct lq_lattice lq_lattice;
 typedef struct lq_sim lq_sim;
@@ -353,15 +353,31 @@ lq_status lq_server_destroy(lq_server* srv);
  * All calls on a device share the scratch, which keeps the last call's
  * contents (every call rebuilds what it reads), so calls whose work overlaps
  * on the GPU race; serialize them on one stream.
- * Errors: LQ_EINVAL (bad arguments; bad fields or sites, reported when a
- * host output is requested), LQ_EUNSUPPORTED (the chain needs more scratch
- * than LQ_NOALLOC_SCRATCH_BYTES, or more than LQ_MAX_PARTICLES per spin),
- * LQ_ECUDA, LQ_ENUMERIC. */
+ * Errors: LQ_EINVAL (bad arguments), LQ_EUNSUPPORTED (the chain needs more
+ * scratch than LQ_NOALLOC_SCRATCH_BYTES, more than LQ_MAX_PARTICLES per spin,
+ * or a shared-memory plan that does not fit one CTA per SM), LQ_ECUDA.  The
+ * errors the kernels detect (LQ_EINVAL for fields other than +-1 or repeated
+ * or out-of-range sites, LQ_ENUMERIC for a singular overlap, a CholeskyQR
+ * breakdown or a non-finite ratio) can only be read back after the stream
+ * has run, so they are reported only when a host output is requested; a call
+ * with all three host outputs null returns LQ_OK for launched work. */
 #define LQ_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 lq_status lq_sweep_noalloc(const lq_lattice* lattice, const lq_params* params, uint32_t chain_id,
                            uint32_t sweep_index, int8_t* dev_fields, int32_t* dev_occ, int32_t n_sweeps,
                            double* dev_records, void* cuda_stream, double* host_log_weight, int32_t* host_sign,
                            int64_t* host_counts4);
+
+/* ---- device FP64 throughput (build-side, no counterpart in the paper) -----
+ * The sweep's field-flip algebra is FP64 on the CUDA cores, so the roof it is
+ * reported against is the device's FP64 FMA rate.  This measures it on the
+ * current device: a kernel of independent FMA chains on every SM, grown until
+ * one launch takes about `ms` milliseconds and timed with CUDA events, gives
+ * *host_tflops (2 flops per FMA).  host_cycles3 (nullable, 3 doubles) receives
+ * the sub-partition cycles of one FP64 FMA warp instruction with 1 and with 32
+ * active lanes and of one FP32 FMA warp instruction (one warp, clock64).
+ * Allocates and frees a small device buffer; synchronous.
+ * Errors: LQ_EINVAL (ms outside (0, 60000] or a null output), LQ_ECUDA. */
+lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles3);
 
 const char* lq_last_error(void);
 const char* lq_version(void);

@@ -453,11 +453,10 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     for (int t = 0; t < ci.nb; ++t) {
       const int b = order[t];
       vi[t] = Lt->bi[b]; vj[t] = Lt->bj[b]; vk[t] = Lt->kb[b];
-      vc[t] = std::cosh(p.dtau * Lt->kb[b]);
-      vs[t] = -std::sinh(p.dtau * Lt->kb[b]);
+      lq_bond_factors(p.dtau, Lt->kb[b], &vc[t], &vs[t]);
       vcf[t] = (float)vc[t]; vsf[t] = (float)vs[t];
     }
-    for (int i = 0; i < ci.N; ++i) { ep[i] = Lt->eps[i]; ce[i] = std::exp(-p.dtau * Lt->eps[i]); cef[i] = (float)ce[i]; }
+    for (int i = 0; i < ci.N; ++i) { ep[i] = Lt->eps[i]; ce[i] = lq_onsite_factor(p.dtau, Lt->eps[i]); cef[i] = (float)ce[i]; }
     auto up = [&](void* dst, const void* src, size_t bytes) {
       return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S->st);
     };
@@ -692,14 +691,21 @@ extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) 
     // start at once; the small class fills the other SMs meanwhile
     e = cudaEventRecord(S->ev_fork, S->st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st2, S->ev_fork, 0);
+    const bool forked = e == cudaSuccess;
     if (e == cudaSuccess)
       e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + large.off, large.n, S->d_queue2, n_sweeps, measure,
                            large.M, large.Nmax, large.buf, large.grid, S->st2, S->ws, S->ws_bytes);
     if (e == cudaSuccess)
       e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + small.off, small.n, S->d_queue, n_sweeps, measure,
                            small.M, small.Nmax, small.buf, small.grid, S->st, nullptr, 0);
-    if (e == cudaSuccess) e = cudaEventRecord(S->ev_join, S->st2);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st, S->ev_join, 0);
+    if (forked) {
+      // join even after a failed launch, so that nothing later on the
+      // caller's stream overtakes the second stream's work
+      cudaError_t ej = cudaEventRecord(S->ev_join, S->st2);
+      if (ej == cudaSuccess) ej = cudaStreamWaitEvent(S->st, S->ev_join, 0);
+      if (ej != cudaSuccess) cudaStreamSynchronize(S->st2);
+      if (e == cudaSuccess) e = ej;
+    }
   } else {
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       const lq_sim::PlanClass& pc = S->cls[k];

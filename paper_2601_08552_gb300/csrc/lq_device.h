@@ -12,7 +12,7 @@ static inline void lq_dw_split(double x, float out[2]) {
 }
 
 #define LQ_NOBS 9          // sign, n_up, n_dn, docc, ekin, szz_00, szz_11, szz_01, s_par
-#define LQ_NS_MAX 256      // particles per spin (the C ABI's LQ_MAX_PARTICLES)
+#define LQ_NS_MAX 512      // particles per spin (the C ABI's LQ_MAX_PARTICLES)
 #define LQ_NS_SMALL 32     // up to this many per spin, one warp per spin flips with one lane per column and
                            // the m x m matrices live in shared memory; above it, a four-warp group per spin
                            // flips and those matrices live in a global workspace per CTA

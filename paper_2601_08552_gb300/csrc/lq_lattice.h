@@ -1,6 +1,7 @@
 // Internal view of a host lattice object (family-sorted bond tables built
 // when the lattice is created) and the shared error setter.
 #pragma once
+#include <cmath>
 #include <string>
 
 #include "../../include/lecqmc.h"
@@ -20,3 +21,14 @@ struct lq_lattice_view {
 
 lq_lattice_view lq_lattice_get_view(const lq_lattice* L);
 lq_status lq_internal_fail(lq_status s, const std::string& msg);
+
+// Factors of the checkerboard propagator for a Trotter step dtau: the exact
+// 2x2 bond exponential e^{-dtau k (|i><j| + |j><i|)} has cosh(dtau k) on the
+// diagonal and -sinh(dtau k) off it, and the onsite factor is e^{-dtau eps}.
+// Every table is built on the host with these same expressions, so two
+// entry points given the same lattice and dtau hold bit-identical tables.
+static inline void lq_bond_factors(double dtau, double k, double* c, double* s) {
+  *c = std::cosh(dtau * k);
+  *s = -std::sinh(dtau * k);
+}
+static inline double lq_onsite_factor(double dtau, double eps) { return std::exp(-dtau * eps); }

@@ -32,17 +32,39 @@ unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Lattice factors for a given dtau, computed on the device into the scratch.
-__global__ void noalloc_tables_kernel(int nb, int N, double dtau, const double* kb, const double* eps, double* bc,
-                                      double* bs, float* bcf, float* bsf, double* ceps, float* cepsf) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-    const double c = cosh(dtau * kb[b]), s = -sinh(dtau * kb[b]);
-    bc[b] = c; bs[b] = s; bcf[b] = (float)c; bsf[b] = (float)s;
+// Upload the dtau-dependent lattice factors.  They are computed on the host
+// with the same expressions as the regular entry point's tables
+// (lq_bond_factors, lq_onsite_factor), a chunk at a time through a small
+// stack buffer: a copy from pageable host memory has taken its source by the
+// time cudaMemcpyAsync returns, so the buffer can be refilled at once.
+cudaError_t upload_factors(const lq_lattice_view& v, double dtau, unsigned char* base, size_t o_bc, size_t o_bs,
+                           size_t o_bcf, size_t o_bsf, size_t o_ce, size_t o_cef, cudaStream_t st) {
+  constexpr int CH = 256;
+  double c[CH], s[CH];
+  float cf[CH], sf[CH];
+  cudaError_t e = cudaSuccess;
+  for (int b0 = 0; b0 < v.nb && e == cudaSuccess; b0 += CH) {
+    const int n = std::min(CH, v.nb - b0);
+    for (int t = 0; t < n; ++t) {
+      lq_bond_factors(dtau, v.sorted_k[b0 + t], &c[t], &s[t]);
+      cf[t] = (float)c[t];
+      sf[t] = (float)s[t];
+    }
+    e = cudaMemcpyAsync(base + o_bc + (size_t)b0 * 8, c, (size_t)n * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_bs + (size_t)b0 * 8, s, (size_t)n * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_bcf + (size_t)b0 * 4, cf, (size_t)n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_bsf + (size_t)b0 * 4, sf, (size_t)n * 4, cudaMemcpyHostToDevice, st);
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const double c = exp(-dtau * eps[i]);
-    ceps[i] = c; cepsf[i] = (float)c;
+  for (int i0 = 0; i0 < v.N && e == cudaSuccess; i0 += CH) {
+    const int n = std::min(CH, v.N - i0);
+    for (int t = 0; t < n; ++t) {
+      c[t] = lq_onsite_factor(dtau, v.eps[i0 + t]);
+      cf[t] = (float)c[t];
+    }
+    e = cudaMemcpyAsync(base + o_ce + (size_t)i0 * 8, c, (size_t)n * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_cef + (size_t)i0 * 4, cf, (size_t)n * 4, cudaMemcpyHostToDevice, st);
   }
+  return e;
 }
 
 }  // namespace
@@ -110,6 +132,9 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
     return lq_internal_fail(LQ_EUNSUPPORTED, "lq_sweep_noalloc: this chain needs " + std::to_string(o) +
                                                  " scratch bytes, more than LQ_NOALLOC_SCRATCH_BYTES (" +
                                                  std::to_string((size_t)LQ_NOALLOC_SCRATCH_BYTES) + ")");
+  // the shared-memory plan must fit one CTA per SM, as lq_sim_create requires
+  if (lq::max_active_sweep_ctas(p->precision, M, lq::smem_bytes(M, N, buf_bytes)) < 1)
+    return lq_internal_fail(LQ_EUNSUPPORTED, "shared-memory plan does not fit one CTA per SM");
   // lattice tables (host vectors owned by the lattice) and zeroed counters
   auto up = [&](size_t at, const void* src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(base + at, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
@@ -124,11 +149,8 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   if (e == cudaSuccess) e = up(o_nbs, v.nb_site, (size_t)v.nb_off[N] * 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_order, 0, sizeof(int), st);
   if (e != cudaSuccess) return lq_internal_fail(LQ_ECUDA, std::string("lq_sweep_noalloc upload: ") + cudaGetErrorString(e));
-  noalloc_tables_kernel<<<(std::max(nb, N) + 255) / 256, 256, 0, st>>>(
-      nb, N, p->dtau, (const double*)(base + o_bk), (const double*)(base + o_eps), (double*)(base + o_bc),
-      (double*)(base + o_bs), (float*)(base + o_bcf), (float*)(base + o_bsf), (double*)(base + o_ce),
-      (float*)(base + o_cef));
-  if ((e = cudaGetLastError()) != cudaSuccess) return lq_internal_fail(LQ_ECUDA, cudaGetErrorString(e));
+  if (e == cudaSuccess) e = upload_factors(v, p->dtau, base, o_bc, o_bs, o_bcf, o_bsf, o_ce, o_cef, st);
+  if (e != cudaSuccess) return lq_internal_fail(LQ_ECUDA, std::string("lq_sweep_noalloc upload: ") + cudaGetErrorString(e));
   // descriptor
   LqChainDev D;
   std::memset(&D, 0, sizeof(D));

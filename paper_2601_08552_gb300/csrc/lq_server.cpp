@@ -326,9 +326,11 @@ static void tick(lq_server* S) {
   // with both classes, the large one runs on the second stream (its own chain
   // queue) concurrently with the small one, joined by events
   const bool both = gc[0] && gc[1];
+  bool forked = false;
   if (e == cudaSuccess && both) {
     e = cudaEventRecord(S->ev_fork, S->st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st2, S->ev_fork, 0);
+    forked = e == cudaSuccess;
   }
   for (int cls = 1; cls >= 0 && e == cudaSuccess; --cls) {
     if (!gc[cls]) continue;
@@ -338,9 +340,13 @@ static void tick(lq_server* S) {
     e = lq::launch_sweep(S->prec, S->d_slots, S->d_order + q0, nq, queue, 1, 1, Mc[cls], Nc[cls], bc[cls], gc[cls], st,
                          cls ? S->d_ws : nullptr, cls ? S->ws_cap : 0, S->d_caps + q0, budget[cls]);
   }
-  if (e == cudaSuccess && both) {
-    e = cudaEventRecord(S->ev_join, S->st2);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->st, S->ev_join, 0);
+  if (forked) {
+    // join even if a launch failed: later work on st (a workspace release
+    // among it) must not overtake what st2 still runs
+    cudaError_t ej = cudaEventRecord(S->ev_join, S->st2);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(S->st, S->ev_join, 0);
+    if (ej != cudaSuccess) cudaStreamSynchronize(S->st2);
+    if (e == cudaSuccess) e = ej;
   }
   cudaEventRecord(e1, S->st);
   cudaMemcpyAsync(desc.data(), S->d_slots, sizeof(LqChainDev) * n, cudaMemcpyDeviceToHost, S->st);

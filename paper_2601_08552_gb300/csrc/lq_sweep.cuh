@@ -47,10 +47,11 @@ namespace lq {
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct SmemPlan {
-  int M, MP, Nmax, buf_bytes, big, s_global;
+  int M, MP, Nmax, buf_bytes, big, s_global, win_global, vec_global;
   // offsets of T0, T1 and W are in shared memory for small plans and in the
   // CTA's slab of the global workspace for big ones (M > LQ_NS_SMALL); the
-  // four scratch matrices S stay in shared memory while they fit there
+  // four scratch matrices S, the field-flip window and the scratch vectors
+  // stay in shared memory while they fit there, in that order of priority
   size_t off_T0, off_T1, off_W, off_S, off_vec, off_red, off_obs, off_gx, off_ip, off_occ, off_bits, off_chain, off_win,
       off_buf, total;
   size_t ws_cta;  // global workspace bytes per CTA (0 for small plans)
@@ -69,12 +70,9 @@ __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
   p.big = p.M > LQ_NS_SMALL;
   p.ws = nullptr;
   const size_t mat = (size_t)p.M * p.MP * 8;
+  const size_t vec_b = al16((size_t)10 * p.M * 8), win_b = al16((size_t)2 * LQ_WIN_ELEMS(p.MP) * 8);
+  const size_t s_b = al16(4 * mat);
   size_t o = 0, g = 0;
-  size_t& om = p.big ? g : o;  // where T and the Gauss-Jordan workspace go
-  p.off_T0 = om; om = al16(om + mat);
-  p.off_T1 = om; om = al16(om + mat);
-  p.off_W = om; om = al16(om + (size_t)p.M * 2 * p.MP * 8);  // Gauss-Jordan / Gram workspace
-  p.off_vec = o; o = al16(o + (size_t)10 * p.M * 8);
   p.off_red = o; o = al16(o + 64 * 8);
   p.off_obs = o; o = al16(o + 16 * 8);
   p.off_gx = o; o = al16(o + 8 * 8);
@@ -82,18 +80,26 @@ __host__ __device__ inline SmemPlan plan_smem(int M, int Nmax, int buf_bytes) {
   p.off_occ = o; o = al16(o + (size_t)2 * p.M * 4);
   p.off_bits = o; o = al16(o + (size_t)(Nmax / 32 + 2) * 4);
   p.off_chain = o; o = al16(o + sizeof(LqChainDev));
-  p.off_win = o; o = al16(o + (size_t)2 * LQ_WIN_ELEMS(p.MP) * 8);
   p.off_buf = o; o = al16(o + (size_t)buf_bytes);
-  // four scratch matrices (swap, QR and measurement work): shared memory
-  // unless a big plan runs out of it
-  p.s_global = p.big && o + 4 * mat > LQ_SMEM_CAP;
+  // big plans move the scratch matrices, then the window, then the vectors
+  // to the global workspace until the rest fits
+  p.s_global = p.big && o + vec_b + win_b + s_b > LQ_SMEM_CAP;
+  p.win_global = p.big && o + vec_b + win_b + (p.s_global ? 0 : s_b) > LQ_SMEM_CAP;
+  p.vec_global = p.big && o + vec_b + (p.win_global ? 0 : win_b) + (p.s_global ? 0 : s_b) > LQ_SMEM_CAP;
+  size_t& om = p.big ? g : o;  // where T and the Gauss-Jordan workspace go
+  p.off_T0 = om; om = al16(om + mat);
+  p.off_T1 = om; om = al16(om + mat);
+  p.off_W = om; om = al16(om + (size_t)p.M * 2 * p.MP * 8);  // Gauss-Jordan / Gram workspace
   size_t& os = p.s_global ? g : o;
-  p.off_S = os; os = al16(os + 4 * mat);
+  p.off_S = os; os = al16(os + s_b);
+  size_t& ow = p.win_global ? g : o;
+  p.off_win = ow; ow = al16(ow + win_b);
+  size_t& ov = p.vec_global ? g : o;
+  p.off_vec = ov; ov = al16(ov + vec_b);
   p.ws_cta = p.big ? ((g + 255) & ~(size_t)255) : 0;
   p.total = o;
   return p;
 }
-
 
 struct Smem {
   double* T[2];
@@ -119,7 +125,7 @@ __device__ inline Smem carve(const SmemPlan& p, char* base) {
   s.T[1] = (double*)(mb + p.off_T1);
   s.W = (double*)(mb + p.off_W);
   s.S = (double*)((p.s_global ? mb : base) + p.off_S);
-  s.vec = (double*)(base + p.off_vec);
+  s.vec = (double*)((p.vec_global ? mb : base) + p.off_vec);
   s.red = (double*)(base + p.off_red);
   s.obs = (double*)(base + p.off_obs);
   s.gx = (double*)(base + p.off_gx);
@@ -127,7 +133,7 @@ __device__ inline Smem carve(const SmemPlan& p, char* base) {
   s.occ2 = (int*)(base + p.off_occ);
   s.bits = (unsigned*)(base + p.off_bits);
   s.C = (LqChainDev*)(base + p.off_chain);
-  s.win = (void*)(base + p.off_win);
+  s.win = (void*)((p.win_global ? mb : base) + p.off_win);
   s.buf = (void*)(base + p.off_buf);
   s.buf_bytes = p.buf_bytes;
   s.M = p.M;

@@ -35,14 +35,16 @@ WORKLOADS = {
 
 def flatband_batch(rng, n_chains, periodic_frac=0.5, cells=(64, 512), beta_range=(4.0, 40.0)):
     """Uneven flat-band chains: cells uniform in `cells` (U[64, 512] in the
-    paper-shaped workload), filling U[1/4, 3/4] of the flat band split evenly
-    by spin, beta uniform in beta_range (U[4, 40]), dtau 0.05, U = 2; half of
-    the chains periodic."""
+    paper-shaped workload), filling f uniform in [1/4, 3/4] of the flat band
+    split evenly by spin, beta uniform in beta_range (U[4, 40]), dtau 0.05,
+    U = 2; half of the chains periodic.  The flat band has one state per cell
+    and spin, and half filling is N_e = N_up + N_dn = N_cells (the paper's
+    half-filling condition), so N_up = N_dn = f * N_cells."""
     out = []
     for _ in range(n_chains):
         nc = int(rng.integers(cells[0], cells[1] + 1))
         f = rng.uniform(0.25, 0.75)
-        ns = max(1, int(round(f * nc / 2)))
+        ns = max(1, int(round(f * nc)))
         beta = float(np.round(rng.uniform(*beta_range) / 0.05) * 0.05)
         out.append(dict(lattice=("flatband", nc, 1.0, 1.0, 1.0, 1.0, bool(rng.random() < periodic_frac)), U=2.0,
                         beta=beta, dtau=0.05, n_up=ns, n_dn=ns, n_stab=8))

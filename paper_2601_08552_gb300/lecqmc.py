@@ -19,7 +19,7 @@ LQ_SWAP_UNIFORM = 0
 LQ_SWAP_NEIGHBOUR = 1
 LQ_NOBS = 9
 OBS_NAMES = ["sign", "n_up", "n_dn", "docc", "ekin", "szz_00", "szz_11", "szz_01", "s_par"]
-LQ_MAX_PARTICLES = 256
+LQ_MAX_PARTICLES = 512
 
 _STATUS = {0: "LQ_OK", 1: "LQ_EINVAL", 2: "LQ_ENOMEM", 3: "LQ_ECUDA", 4: "LQ_ENUMERIC", 5: "LQ_ETIMEOUT",
            6: "LQ_EBUSY", 7: "LQ_ENOTFOUND", 8: "LQ_EUNSUPPORTED"}
@@ -35,6 +35,7 @@ EXPORTS = [
     "lq_sim_device_bytes", "lq_sim_destroy", "lq_sim_measure", "lq_sim_check_drift", "lq_server_create",
     "lq_server_submit",
     "lq_server_poll", "lq_server_stats", "lq_server_set_tick_target", "lq_server_destroy", "lq_sweep_noalloc",
+    "lq_device_fp64_rate",
     "lq_last_error", "lq_version",
 ]
 
@@ -139,6 +140,7 @@ def load(build_if_missing=True):
         "lq_server_stats": [P, C.POINTER(ServerStats)],
         "lq_server_set_tick_target": [P, dbl],
         "lq_server_destroy": [P],
+        "lq_device_fp64_rate": [dbl, pdbl, pdbl],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +235,7 @@ def sweep_noalloc(lattice, params, chain_id, sweep_index, dev_fields, dev_occ, n
     import torch
 
     p = _params_struct(params)
+    _check_noalloc_buffers(torch, lattice, params, dev_fields, dev_occ, n_sweeps, dev_records)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     lw, sg = C.c_double(), C.c_int32()
@@ -244,6 +247,44 @@ def sweep_noalloc(lattice, params, chain_id, sweep_index, dev_fields, dev_occ, n
                                  C.byref(lw) if want_state else None, C.byref(sg) if want_state else None,
                                  cnt.ctypes.data_as(C.POINTER(C.c_int64)) if want_state else None))
     return (lw.value, sg.value, cnt) if want_state else None
+
+
+def _check_noalloc_buffers(torch, lattice, params, dev_fields, dev_occ, n_sweeps, dev_records):
+    """The C entry point receives raw device pointers and cannot check them:
+    every buffer must be a contiguous CUDA tensor of the right dtype and
+    element count on the current device, or the kernels would write out of
+    bounds.  Raises ValueError on any mismatch."""
+    L = int(round(float(params["beta"]) / float(params["dtau"])))
+    want = [("dev_fields", dev_fields, torch.int8, L * lattice.N),
+            ("dev_occ", dev_occ, torch.int32, int(params["n_up"]) + int(params["n_dn"]))]
+    if dev_records is not None:
+        want.append(("dev_records", dev_records, torch.float64, int(n_sweeps) * LQ_NOBS))
+    for name, t, dtype, numel in want:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.dtype != dtype:
+            raise ValueError("%s must have dtype %s, not %s" % (name, dtype, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.numel() != numel:
+            raise ValueError("%s must hold %d elements, not %d" % (name, numel, t.numel()))
+    for name, t, _, _ in want:
+        if not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        dev = torch.cuda.current_device()
+        if t.device.index != dev:
+            raise ValueError("%s must be on the current device (cuda:%d), not %s" % (name, dev, t.device))
+
+
+def device_fp64_rate(ms=200.0):
+    """Measured FP64 FMA throughput of the current device (lq_device_fp64_rate):
+    (TFLOP/s, {cycles of one FP64 FMA warp instruction with 1 and 32 active
+    lanes, of one FP32 FMA warp instruction})."""
+    load()
+    t = C.c_double()
+    cyc = np.zeros(3)
+    _check(_lib.lq_device_fp64_rate(float(ms), C.byref(t), _p(cyc, C.c_double)))
+    return t.value, dict(dfma_1lane=float(cyc[0]), dfma_32lanes=float(cyc[1]), ffma_32lanes=float(cyc[2]))
 
 
 def _torch_allocator():

@@ -122,3 +122,31 @@ def header_fields(cname):
         names.append(re.search(r"(\w+)\s*(\[[^\]]*\])?\s*$", first).group(1))
         names += [re.search(r"(\w+)\s*(\[[^\]]*\])?\s*$", r).group(1) for r in rest]
     return names
+
+
+def test_noalloc_binding_rejects_bad_buffers_before_the_call(lq):
+    """lq_sweep_noalloc receives raw device pointers: the binding checks each
+    buffer's dtype, contiguity, element count and device first and raises
+    ValueError, so a wrong buffer never reaches the kernels."""
+    torch = pytest.importorskip("torch")
+    from paper_2601_08552_gb300.lecqmc import sweep_noalloc
+
+    lat = lq.Lattice.chain(8)
+    params = dict(U=4.0, beta=1.0, dtau=0.1, n_up=2, n_dn=3, n_stab=4, precision=0, seed=1)
+    L = 10
+    good_f = torch.ones(L * 8, dtype=torch.int8)
+    good_o = torch.arange(5, dtype=torch.int32)
+    cases = [
+        (torch.ones(L * 8, dtype=torch.int32), good_o, None, "dtype"),
+        (torch.ones(L * 8 - 1, dtype=torch.int8), good_o, None, "elements"),
+        (torch.ones((8, L), dtype=torch.int8).t(), good_o, None, "contiguous"),
+        (good_f, torch.arange(4, dtype=torch.int32), None, "elements"),
+        (good_f, torch.arange(5, dtype=torch.int64), None, "dtype"),
+        (good_f, good_o, torch.zeros(3 * 9, dtype=torch.float32), "dtype"),
+        (good_f, good_o, torch.zeros(2 * 9, dtype=torch.float64), "elements"),
+        (good_f, good_o, None, "CUDA"),
+        (good_f.numpy(), good_o, None, "torch tensor"),
+    ]
+    for f, o, r, what in cases:
+        with pytest.raises(ValueError, match=what):
+            sweep_noalloc(lat, params, 0, 0, f, o, 3, r)

@@ -8,8 +8,11 @@ import numpy as np
 import pytest
 
 from oracle import OracleSim, lattices
+from parity import elem_rel
 
 pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
 
 SPECS = [
     dict(lattice=("square", 4, 4), U=4.0, beta=0.8, dtau=0.1, n_up=3, n_dn=2, n_stab=4),
@@ -62,10 +65,10 @@ def test_autotune_keeps_the_trajectory(lq):
         assert np.array_equal(sim.stats(c), o.stats())
         lt, st = sim.tracked_weight(c)
         lo, so = o.tracked()
-        assert st == so and abs(lt - lo) < 1e-9 * max(1.0, abs(lo))
+        assert st == so and abs(lt - lo) < TOL * max(1.0, abs(lo))
         rg = sim.records(c)
         ro = o.records()[-2:]
-        assert np.max(np.abs(rg - ro)) < 1e-10 * max(1.0, float(np.max(np.abs(ro))))
+        assert elem_rel(rg, ro) < TOL
 
 
 def test_autotune_cache(lq):

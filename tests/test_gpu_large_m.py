@@ -11,6 +11,7 @@ import pytest
 
 from oracle import OracleSim, lattices
 from paper_2601_08552_gb300 import inputs
+from parity import elem_rel, norm_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +28,19 @@ CASES = {
     "square12x12_m100": dict(lattice=("square", 12, 12), U=4.0, beta=0.2, dtau=0.1, n_up=100, n_dn=70, n_stab=2),
 }
 
+# the largest particle numbers, on short imaginary time (the oracle's cost
+# grows as L N m^2): the flat-band chain's 3/4 filling at 256 cells (m = 192),
+# at 512 cells (m = 384, the largest of the uneven flat-band workload), and the
+# library's limit LQ_MAX_PARTICLES = 512.  The scratch matrices, the flip
+# window and the vectors of these plans live in the global workspace.
+LARGEST = {
+    "flat256_m192": dict(lattice=("flatband", 256, 1.0, 1.0, 1.0, 1.0, True), U=2.0, beta=0.2, dtau=0.05,
+                         n_up=192, n_dn=192, n_stab=2),
+    "flat512_m384": dict(lattice=("flatband", 512, 1.0, 1.0, 1.0, 1.0, False), U=2.0, beta=0.1, dtau=0.05,
+                         n_up=384, n_dn=383, n_stab=2),
+    "chain1024_m512": dict(lattice=("chain", 1024), U=-2.0, beta=0.1, dtau=0.05, n_up=512, n_dn=500, n_stab=1),
+}
+
 
 @pytest.fixture(scope="module")
 def lq():
@@ -39,11 +53,6 @@ def lq():
     return p
 
 
-def rel(a, b):
-    a, b = np.asarray(a, float), np.asarray(b, float)
-    if a.size == 0 and b.size == 0:
-        return 0.0
-    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
 
 
 def make(lq, spec, prec=0, seed=7, chain=0):
@@ -76,7 +85,7 @@ def test_log_weight_and_chains_large_m(lq, name):
                     continue
                 Qg, Vg = sim.chain_panel(0, side, spin, j)
                 Qo, Vo = o.chain_panel(side, spin, j)
-                assert rel(Qg, Qo) < 1e-9 and rel(Vg, Vo) < 1e-9, (side, spin, j)
+                assert norm_rel(Qg, Qo) < TOL and norm_rel(Vg, Vo) < TOL, (side, spin, j)
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -118,8 +127,8 @@ def test_sweep_trajectory_large_m(lq, name):
     assert np.array_equal(sim.stats(0), o.stats())
     lt, st = sim.tracked_weight(0)
     lo, so = o.tracked()
-    assert st == so and abs(lt - lo) < 1e-9 * max(1.0, abs(lo))
-    assert rel(sim.records(0), o.records()) < TOL
+    assert st == so and abs(lt - lo) < TOL * max(1.0, abs(lo))
+    assert elem_rel(sim.records(0), o.records()) < TOL
 
 
 def test_mixed_sizes_in_one_launch(lq):
@@ -144,7 +153,7 @@ def test_mixed_sizes_in_one_launch(lq):
     for c, o in enumerate(oracles):
         assert np.array_equal(sim.get_fields(c), o.get_fields())
         assert np.array_equal(sim.stats(c), o.stats())
-        assert rel(sim.records(c), o.records()) < TOL
+        assert elem_rel(sim.records(c), o.records()) < TOL
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -166,4 +175,47 @@ def test_reduced_precision_large_m(lq, name, prec):
     sim.sync()
     assert np.array_equal(sim.get_fields(0), o.get_fields())
     assert np.array_equal(sim.stats(0), o.stats())
-    assert rel(sim.records(0), o.records()) < 1e-5
+    assert elem_rel(sim.records(0), o.records()) < 1e-5
+
+
+@pytest.mark.parametrize("name", sorted(LARGEST))
+def test_largest_particle_numbers(lq, name):
+    """Up to LQ_MAX_PARTICLES per spin: log-weight of freshly built chains,
+    a field ratio and a swap ratio through the hooks, then one sweep with its
+    trajectory (integer state bit-exact, records and tracked weight within
+    1e-10)."""
+    spec = LARGEST[name]
+    o, sim = make(lq, spec, seed=17, chain=1)
+    sim.init()
+    lw, sg = sim.log_weight(0)
+    lo, so = o.log_weight()
+    assert sg == so and abs(lw - lo) < TOL * max(1.0, abs(lo))
+    rng = np.random.default_rng(9)
+    l, i = int(rng.integers(o.L)), int(rng.integers(o.N))
+    rg, ro = sim.field_ratio(0, l, i), o.field_ratio(l, i)
+    assert abs(rg - ro) < TOL * max(1.0, abs(ro))
+    occ = o.get_fock()
+    empty = [x for x in range(o.N) if x not in set(occ[0].tolist())]
+    k, j = int(rng.integers(o.ns[0])), int(empty[rng.integers(len(empty))])
+    rg, pg = sim.swap_ratio(0, 0, k, j)
+    ro, po = o.swap_ratio(0, k, j)
+    assert abs(rg - ro) < TOL * max(1.0, abs(ro)) and pg[1] == po[1]
+    o.sweep(1)
+    sim.sweep(1)
+    sim.sync()
+    assert np.array_equal(sim.get_fields(0), o.get_fields())
+    gu, gd = sim.get_fock(0)
+    ou, od = o.get_fock()
+    assert np.array_equal(gu, ou) and np.array_equal(gd, od)
+    assert np.array_equal(sim.stats(0), o.stats())
+    lt, st = sim.tracked_weight(0)
+    lo, so = o.tracked()
+    assert st == so and abs(lt - lo) < TOL * max(1.0, abs(lo))
+    assert elem_rel(sim.records(0), o.records()) < TOL
+
+
+def test_beyond_the_particle_limit_is_rejected(lq):
+    L = lq.Lattice.chain(1100)
+    with pytest.raises(lq.LqError) as e:
+        lq.Sim([L], [dict(U=2.0, beta=0.1, dtau=0.05, n_up=lq.LQ_MAX_PARTICLES + 1, n_dn=1, n_stab=1)])
+    assert e.value.status == 8

@@ -13,6 +13,7 @@ import pytest
 import exact
 from oracle import OBS_NAMES, OracleSim, lattices
 from stats import jackknife_ratio
+from parity import elem_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -69,10 +70,10 @@ def test_left_swap_trajectory(lq, name, prec):
     assert st[2] == 3 * 2 * sum(m for m in (spec["n_up"], spec["n_dn"]) if 0 < m < o.N)
     tol = 1e-10 if prec == 0 else 1e-5
     rg, ro = sim.records(0), o.records()
-    assert np.max(np.abs(rg - ro)) < tol * max(1.0, float(np.max(np.abs(ro))))
+    assert elem_rel(rg, ro) < tol
     lt, sg = sim.tracked_weight(0)
     lo, so = o.tracked()
-    assert sg == so and abs(lt - lo) < (1e-9 if prec == 0 else 1e-5) * max(1.0, abs(lo))
+    assert sg == so and abs(lt - lo) < (1e-10 if prec == 0 else 1e-5) * max(1.0, abs(lo))
 
 
 def test_left_swaps_accept_and_tracked_weight_is_fresh(lq):
@@ -85,8 +86,8 @@ def test_left_swaps_accept_and_tracked_weight_is_fresh(lq):
     sim.sync()
     st = sim.stats(0)
     assert st[3] > 0  # some swaps were accepted
-    worst, bad = sim.check_drift(1e-9)
-    assert bad == 0 and worst < 1e-9
+    worst, bad = sim.check_drift(1e-10)
+    assert bad == 0 and worst < 1e-10
     o.sweep(2)
     sim.sweep(2)
     sim.sync()

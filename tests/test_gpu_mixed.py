@@ -12,6 +12,7 @@ import pytest
 import exact
 from oracle import OBS_NAMES, OracleSim, lattices
 from stats import jackknife_ratio
+from parity import elem_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -85,7 +86,7 @@ def test_reduced_precision_short_trajectory(lq, name, prec):
     lo, so = o.tracked()
     assert st == so and abs(lt - lo) < RTOL * max(1.0, abs(lo))
     rg, ro = sim.records(0), o.records()
-    assert np.max(np.abs(rg - ro)) < RTOL * max(1.0, np.max(np.abs(ro)))
+    assert elem_rel(rg, ro) < RTOL
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])

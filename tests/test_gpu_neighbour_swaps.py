@@ -13,6 +13,7 @@ import pytest
 import exact
 from oracle import OBS_NAMES, OracleSim, lattices
 from stats import jackknife_ratio
+from parity import elem_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +57,7 @@ def test_neighbour_swap_trajectory(lq, name, prec):
     assert np.array_equal(sim.stats(0), o.stats())
     tol = 1e-10 if prec == 0 else 1e-5
     rg, ro = sim.records(0), o.records()
-    assert np.max(np.abs(rg - ro)) < tol * max(1.0, float(np.max(np.abs(ro))))
+    assert elem_rel(rg, ro) < tol
 
 
 def test_neighbour_swaps_match_trotter_ed(lq):
