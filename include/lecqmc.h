@@ -136,7 +136,23 @@ typedef struct {
                        * the left chain (the right chain of the transposed propagator
                        * B(beta,0)^T, whose weight det[P^T B^T P] is the same).  Other values:
                        * LQ_EINVAL. */
+  int32_t kinetic;    /* how e^{-dtau K} of B_l = e^{-dtau K} e^{-dtau V(s_l)} (Eq. 1) is applied:
+                       * LQ_CHECKERBOARD (0, default) or LQ_EXACT (1); other values LQ_EINVAL */
 } lq_params;
+
+/* Kinetic propagator.  The paper's linear scaling needs e^{-dtau K} applied in
+ * O(N) per panel column; it does not say how.
+ * LQ_CHECKERBOARD: B_K = E_{G-1} ... E_0 C_eps, each E_g the exact product of
+ *   the 2x2 bond exponentials of checkerboard family g, C_eps = diag(e^{-dtau
+ *   K_ii}).  Exact for its own Trotter splitting; G passes over the bonds.
+ * LQ_EXACT: B_K = e^{-dtau K} itself (no splitting error), applied as the
+ *   Taylor polynomial of degree q in the sparse -dtau K, q the smallest degree
+ *   whose remainder is below 1e-17 relative (about 10-20 for dtau = 0.05):
+ *   q sparse products per slice, still O(N N_sigma) per slice.  Needs
+ *   theta = dtau max_i sum_j |K_ij| <= 2 (LQ_EUNSUPPORTED otherwise) and a
+ *   shared-memory staging buffer of two panel columns. */
+#define LQ_CHECKERBOARD 0
+#define LQ_EXACT 1
 
 /* Fock-swap proposals.  A swap removes the particle of a uniformly drawn
  * occupied column k and adds one at a target site j.  UNIFORM draws j
@@ -297,17 +313,29 @@ typedef struct {
   int64_t counts[4];         /* field attempts, accepts, swap attempts, accepts */
   double queue_ms;           /* submit -> admission */
   double total_ms;           /* submit -> retirement */
-  double sweep_ms_mean;      /* mean per-sweep latency this request saw */
+  double sweep_ms_mean;      /* mean device time of one of its sweeps */
+  double wall_ms_per_sweep;  /* total_ms / sweeps: wall latency per sweep, queueing and batching included */
+  int32_t active_at_admit;   /* requests already on the device when it was admitted */
+  int32_t waited_for_memory; /* 1 if it reached the head of the queue and waited for memory to be freed */
 } lq_result;
 typedef struct {
-  double p50_sweep_ms, p99_sweep_ms; /* per-sweep latency: one sample per sweep run, the chain's own sweep time */
+  double p50_sweep_ms, p99_sweep_ms; /* per-sweep latency: one sample per sweep run, that sweep's own device time */
   double p50_tick_ms, p99_tick_ms;   /* duration of the batched launches */
   double updates_per_s;              /* field-update attempts per second of device busy time */
   double busy_s, wall_s;             /* device time of the batched launches; wall time since creation */
   double admit_s, retire_s;          /* host time spent admitting and retiring requests */
   int64_t submitted, admitted, completed, rejected, active, queued, ticks;
   size_t hbm_in_use;
+  double p50_wall_sweep_ms, p99_wall_sweep_ms; /* over retired requests: (retirement - submission) / sweeps */
+  int64_t sweeps;                              /* sweeps run */
 } lq_server_info;
+/* Percentiles come from fixed histograms (200 logarithmic bins per decade
+ * from 1 us to 10^4 s, 1.2 % wide), so the statistics use constant memory. */
+/* Device bytes a request of this lattice and these parameters holds while
+ * it is admitted (fields, both QR chains, the stored block, scratch and
+ * records): the amount the server charges against its budget.  Errors:
+ * LQ_EINVAL for a null argument or parameters out of range. */
+lq_status lq_request_footprint(const lq_lattice* lattice, const lq_params* params, size_t* bytes);
 /* Errors: LQ_EINVAL for a bad budget, slot count, queue capacity or precision. */
 lq_status lq_server_create(int32_t device, size_t hbm_budget, int32_t precision, int32_t max_active,
                            int32_t queue_capacity, lq_server** out);
@@ -378,6 +406,14 @@ lq_status lq_sweep_noalloc(const lq_lattice* lattice, const lq_params* params, u
  * Allocates and frees a small device buffer; synchronous.
  * Errors: LQ_EINVAL (ms outside (0, 60000] or a null output), LQ_ECUDA. */
 lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles3);
+/* Test hook (no counterpart in the paper): the field-flip loop divides by
+ * 1 + Delta G_tt with a hardware reciprocal seed and one third-order
+ * Newton-Raphson step instead of the IEEE division sequence.  This evaluates
+ * that quotient and the IEEE quotient d[k] / r[k] on the device for n host
+ * operand pairs (host arrays of n; outputs host arrays of n).  Allocates
+ * device memory; synchronous.  Errors: LQ_EINVAL, LQ_ECUDA. */
+lq_status lq_test_quotient(int32_t n, const double* host_d, const double* host_r, double* host_q,
+                           double* host_q_ieee);
 
 const char* lq_last_error(void);
 const char* lq_version(void);

@@ -156,6 +156,7 @@ typedef struct {
   int swap_mode;
   int *nb_off, *nb_site;
   int left_swaps;           /* 1: a second swap phase at tau = 0 after the down pass */
+  double* BKd;              /* exact kinetic mode: the dense N x N e^{-dtau K}, else NULL */
 } orc_sim;
 
 static double* dalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
@@ -273,8 +274,25 @@ static void gram(const double* A, const double* B, int N, int p, int q, double* 
 /* Propagators                                                               */
 /* ------------------------------------------------------------------------ */
 
-/* X (N x m) <- B_K X with B_K = E_{G-1} ... E_0 C_eps. */
+/* Exact kinetic mode: X (N x m) <- B X or B^T X for the dense B = e^{-dtau K}
+ * given by the caller (a plain matrix product through a copy of X). */
+static void apply_dense(const orc_sim* S, double* X, int m, int transpose) {
+  const int N = S->N;
+  double* Y = dalloc((size_t)N * m);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      const double b = transpose ? S->BKd[(size_t)j * N + i] : S->BKd[(size_t)i * N + j];
+      if (b == 0.0) continue;
+      for (int a = 0; a < m; ++a) Y[(size_t)i * m + a] += b * X[(size_t)j * m + a];
+    }
+  memcpy(X, Y, sizeof(double) * (size_t)N * m);
+  free(Y);
+}
+
+/* X (N x m) <- B_K X with B_K = E_{G-1} ... E_0 C_eps (checkerboard), or with
+ * the dense e^{-dtau K} in the exact kinetic mode. */
 static void apply_BK(const orc_sim* S, double* X, int m) {
+  if (S->BKd) { apply_dense(S, X, m, 0); return; }
   for (int i = 0; i < S->N; ++i)
     for (int a = 0; a < m; ++a) X[i * m + a] *= S->ceps[i];
   for (int g = 0; g < S->G; ++g)
@@ -290,8 +308,9 @@ static void apply_BK(const orc_sim* S, double* X, int m) {
     }
 }
 
-/* X <- B_K^T X = C_eps E_0 ... E_{G-1} X. */
+/* X <- B_K^T X = C_eps E_0 ... E_{G-1} X (or the dense transpose). */
 static void apply_BKT(const orc_sim* S, double* X, int m) {
+  if (S->BKd) { apply_dense(S, X, m, 1); return; }
   for (int g = S->G - 1; g >= 0; --g)
     for (int b = 0; b < S->nb; ++b) {
       if (S->fam_of[b] != g) continue;
@@ -424,8 +443,21 @@ orc_sim* orc_create(int N, int nb, const int* bi, const int* bj, const double* k
   return S;
 }
 
+/* Exact kinetic mode (Eq. 1 with B_l = e^{-dtau K} e^{-dtau V(s_l)} and no
+ * checkerboard splitting): B is the dense N x N matrix e^{-dtau K}, row-major,
+ * computed by the caller; NULL returns to the checkerboard.  The caller
+ * rebuilds the chains afterwards. */
+void orc_set_dense_BK(orc_sim* S, const double* B) {
+  free(S->BKd);
+  S->BKd = NULL;
+  if (!B) return;
+  S->BKd = dalloc((size_t)S->N * S->N);
+  memcpy(S->BKd, B, sizeof(double) * (size_t)S->N * S->N);
+}
+
 void orc_destroy(orc_sim* S) {
   if (!S) return;
+  free(S->BKd);
   free(S->bi); free(S->bj); free(S->kb); free(S->eps); free(S->sub); free(S->fam_of);
   free(S->nb_off); free(S->nb_site);
   free(S->bc); free(S->bs); free(S->ceps); free(S->bnd); free(S->s);

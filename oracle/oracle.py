@@ -71,6 +71,7 @@ def _load():
     lib.orc_get_corr.restype = C.c_longlong
     lib.orc_get_chain.argtypes = [P, C.c_int, C.c_int, C.c_int, dp, dp]
     lib.orc_get_BK.argtypes = [P, dp]
+    lib.orc_set_dense_BK.argtypes = [P, dp]
     lib.orc_stats.argtypes = [P, C.POINTER(C.c_longlong)]
     lib.orc_info.argtypes = [P, ip, dp]
     lib.orc_get_families.argtypes = [P, ip]
@@ -113,7 +114,8 @@ class OracleSim:
     """One chain of the oracle.  ``lat`` is a dict from ``oracle.lattices``."""
 
     def __init__(self, lat, U, beta, dtau, n_up, n_dn, n_stab, seed=0, chain=0,
-                 max_records=100000, want_corr=False, init="seed", swap_mode=0, left_swaps=False):
+                 max_records=100000, want_corr=False, init="seed", swap_mode=0, left_swaps=False,
+                 kinetic="checkerboard"):
         lib = _load()
         self.lib = lib
         self.lat = lat
@@ -135,6 +137,16 @@ class OracleSim:
         self.N, self.L, self.tw, self.n, self.G, self.n_up, self.n_dn, self.charge = [int(x) for x in ints[:8]]
         self.lam = float(dbl[0])
         self.ns = (self.n_up, self.n_dn)
+        if kinetic == "exact":
+            # Eq. 1 with e^{-dtau K} itself: the dense matrix exponential of the hopping matrix
+            from scipy.linalg import expm
+
+            from .lattices import dense_K
+
+            self._BK = np.ascontiguousarray(expm(-float(dtau) * dense_K(lat)))
+            lib.orc_set_dense_BK(self.h, _ptr(self._BK, C.c_double))
+        elif kinetic != "checkerboard":
+            raise ValueError("kinetic must be 'checkerboard' or 'exact'")
         lib.orc_set_swap_mode(self.h, int(swap_mode))  # 0 uniform target, 1 empty nearest neighbour
         lib.orc_set_left_swaps(self.h, int(bool(left_swaps)))  # second swap phase at tau = 0
         if init == "seed":

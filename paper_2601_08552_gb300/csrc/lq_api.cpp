@@ -49,6 +49,11 @@ struct lq_lattice {
   std::vector<double> sorted_k;
   // each site's distinct bond partners, ascending (nearest-neighbour swaps)
   std::vector<int> nb_off, nb_site;
+  // K in compressed rows, bonds summed and the onsite term on the diagonal
+  // (the exact kinetic propagator), and max_i sum_j |K_ij|
+  std::vector<int> k_off, k_col;
+  std::vector<double> k_val;
+  double k_rownorm = 0.0;
 };
 
 // each bond, in order, goes to the lowest family where neither site is used
@@ -112,6 +117,26 @@ static lq_status make_lattice(int N, const std::vector<int>& bi, const std::vect
     L->nb_off[i + 1] = L->nb_off[i] + (int)adj[i].size();
     L->nb_site.insert(L->nb_site.end(), adj[i].begin(), adj[i].end());
   }
+  {
+    std::vector<std::map<int, double>> rows(N);
+    for (int i = 0; i < N; ++i)
+      if (L->eps[i] != 0.0) rows[i][i] += L->eps[i];
+    for (int b = 0; b < nb; ++b) {
+      rows[L->bi[b]][L->bj[b]] += L->kb[b];
+      rows[L->bj[b]][L->bi[b]] += L->kb[b];
+    }
+    L->k_off.assign(N + 1, 0);
+    for (int i = 0; i < N; ++i) {
+      double rs = 0.0;
+      for (const auto& e : rows[i]) {
+        L->k_col.push_back(e.first);
+        L->k_val.push_back(e.second);
+        rs += std::fabs(e.second);
+      }
+      L->k_off[i + 1] = (int)L->k_col.size();
+      L->k_rownorm = std::max(L->k_rownorm, rs);
+    }
+  }
   *out = L;
   return LQ_OK;
 }
@@ -122,6 +147,8 @@ lq_lattice_view lq_lattice_get_view(const lq_lattice* L) {
   v.fam_off = L->fam_off.data(); v.sorted_i = L->sorted_i.data(); v.sorted_j = L->sorted_j.data();
   v.sorted_k = L->sorted_k.data(); v.eps = L->eps.data(); v.sub = L->sub.data();
   v.nb_off = L->nb_off.data(); v.nb_site = L->nb_site.data();
+  v.nnz = (int)L->k_col.size(); v.k_off = L->k_off.data(); v.k_col = L->k_col.data(); v.k_val = L->k_val.data();
+  v.k_rownorm = L->k_rownorm;
   return v;
 }
 
@@ -242,7 +269,8 @@ extern "C" lq_status lq_lattice_destroy(lq_lattice* L) {
 // ---------------------------------------------------------------------------
 struct ChainHost {
   int N, L, tw, n, ns[2];
-  int G, nb;
+  int G, nb, nnz;
+  int exact, taylor_q;  // exact kinetic propagator and its Taylor degree
   double cost;
 };
 
@@ -270,7 +298,7 @@ struct lq_sim {
   // particles per spin (shared-memory plan), then the larger ones (global
   // workspace); d_order holds the small class first, each by decreasing cost
   struct PlanClass {
-    int n = 0, off = 0, M = 1, Nmax = 1, buf = 0, grid = 1;
+    int n = 0, off = 0, M = 1, Nmax = 1, buf = 0, grid = 1, pcols = 1;
   } cls[2];
   char* ws = nullptr;            // global workspace of big plans (grid x per-CTA slab)
   size_t ws_bytes = 0;
@@ -294,12 +322,18 @@ static lq_status check_chain(const lq_sim* S, int c) {
   return LQ_OK;
 }
 
-static size_t footprint_one(int N, int nb, int G, int L, int tw, const int ns[2], int prec, int max_records) {
+static size_t csr_bytes(int N, int nnz) {
+  return al256((size_t)(N + 1) * 4) + al256((size_t)std::max(nnz, 1) * 4) + al256((size_t)std::max(nnz, 1) * 8) +
+         al256((size_t)std::max(nnz, 1) * 4);
+}
+
+static size_t footprint_one(int N, int nb, int G, int L, int tw, const int ns[2], int prec, int max_records,
+                            int exact) {
   const size_t PS = prec == LQ_FP64 ? sizeof(double) : sizeof(float);
   const int n = (L + tw - 1) / tw;
   size_t b = al256((G + 1) * 4) + 3 * al256(nb * 4) + 3 * al256(nb * 8) + 2 * al256(nb * 4) + 3 * al256(N * 8) +
              al256(N * 4) + al256(N * 4) + al256((size_t)(N + 1) * 4) + al256((size_t)std::max(2 * nb, 1) * 4) +
-             al256((size_t)L * N);
+             al256((size_t)L * N) + csr_bytes(N, N + 2 * nb);
   for (int sg = 0; sg < 2; ++sg) {
     const size_t pn = (size_t)N * ns[sg], qn = (size_t)ns[sg] * ns[sg];
     b += al256(std::max(ns[sg], 1) * 4);
@@ -309,7 +343,7 @@ static size_t footprint_one(int N, int nb, int G, int L, int tw, const int ns[2]
   }
   b += al256((size_t)2 * N * 8) + al256((size_t)n * LQ_NS_MAX * 2 * 8) + al256((size_t)max_records * LQ_NOBS * 8);
   const int M = std::max(std::max(ns[0], ns[1]), 1);
-  b += al256(lq::workspace_bytes(M, N, lq::staging_bytes(M, N)));  // one CTA's workspace (big plans)
+  b += al256(lq::workspace_bytes(M, N, lq::staging_bytes(M, N, exact ? 2 : 1)));  // one CTA's workspace (big plans)
   return b + al256(sizeof(LqChainDev)) + 4 * al256(sizeof(int) * 1026);
 }
 
@@ -335,7 +369,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   if (prec != LQ_FP64 && prec != LQ_MIXED && prec != LQ_MIXED_DW)
     return fail(LQ_EINVAL, "precision must be LQ_FP64, LQ_MIXED or LQ_MIXED_DW");
   std::vector<ChainHost> info(n_chains);
-  int M = 1, Nmax = 1;
+  int M = 1, Nmax = 1, any_exact = 0;
   for (int c = 0; c < n_chains; ++c) {
     const lq_lattice* Lt = lats[c];
     const lq_params& p = params[c];
@@ -350,16 +384,23 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     if (p.swap_mode != LQ_SWAP_UNIFORM && p.swap_mode != LQ_SWAP_NEIGHBOUR)
       return fail(LQ_EINVAL, "swap_mode must be LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR");
     if (p.left_swaps != 0 && p.left_swaps != 1) return fail(LQ_EINVAL, "left_swaps must be 0 or 1");
+    if (p.kinetic != LQ_CHECKERBOARD && p.kinetic != LQ_EXACT)
+      return fail(LQ_EINVAL, "kinetic must be LQ_CHECKERBOARD or LQ_EXACT");
+    if (p.kinetic == LQ_EXACT && p.dtau * Lt->k_rownorm > LQ_EXACT_THETA_MAX)
+      return fail(LQ_EUNSUPPORTED, "LQ_EXACT needs dtau * max_i sum_j |K_ij| <= 2");
     if (p.n_up < 0 || p.n_dn < 0 || p.n_up > Lt->N || p.n_dn > Lt->N)
       return fail(LQ_EINVAL, "particle numbers must be in [0, N]");
     if (p.n_up > LQ_MAX_PARTICLES || p.n_dn > LQ_MAX_PARTICLES)
       return fail(LQ_EUNSUPPORTED, "at most LQ_MAX_PARTICLES particles per spin");
     ChainHost& ci = info[c];
     ci.N = Lt->N; ci.L = (int)Ll; ci.tw = p.n_stab; ci.n = (ci.L + ci.tw - 1) / ci.tw;
-    ci.ns[0] = p.n_up; ci.ns[1] = p.n_dn; ci.G = Lt->G; ci.nb = (int)Lt->bi.size();
+    ci.ns[0] = p.n_up; ci.ns[1] = p.n_dn; ci.G = Lt->G; ci.nb = (int)Lt->bi.size(); ci.nnz = (int)Lt->k_col.size();
+    ci.exact = p.kinetic == LQ_EXACT;
+    ci.taylor_q = ci.exact ? lq_taylor_degree(p.dtau * Lt->k_rownorm) : 0;
     ci.cost = (double)ci.L * ci.N * (ci.ns[0] * ci.ns[0] + ci.ns[1] * ci.ns[1] + (3.0 * ci.G + 1) * (ci.ns[0] + ci.ns[1]) + 1);
     M = std::max(M, std::max(ci.ns[0], ci.ns[1]));
     Nmax = std::max(Nmax, ci.N);
+    any_exact |= ci.exact;
   }
   lq_sim* S = new (std::nothrow) lq_sim();
   if (!S) return fail(LQ_ENOMEM, "host allocation");
@@ -373,7 +414,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
   const size_t PS = prec == LQ_FP64 ? sizeof(double) : sizeof(float);
   // shared-memory staging buffer: at least one full column of the largest
   // panel, and room for a chunk of rows in the flip loop
-  S->buf_bytes = lq::staging_bytes(M, Nmax);
+  S->buf_bytes = lq::staging_bytes(M, Nmax, any_exact ? 2 : 1);
   {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
@@ -391,7 +432,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     const ChainHost& ci = info[c];
     return al256((ci.G + 1) * 4) + 3 * al256(ci.nb * 4) + 3 * al256(ci.nb * 8) + 2 * al256(ci.nb * 4) +
            3 * al256(ci.N * 8) + al256(ci.N * 4) + al256(ci.N * 4) + al256((size_t)(ci.N + 1) * 4) +
-           al256((size_t)std::max(2 * ci.nb, 1) * 4);
+           al256((size_t)std::max(2 * ci.nb, 1) * 4) + csr_bytes(ci.N, ci.nnz);
   };
   const int max_records = 1 << 16;
   auto chain_bytes = [&](int c) {
@@ -476,7 +517,18 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     int* d_sub = (int*)take(ci.N * 4);
     int* d_nbo = (int*)take((size_t)(ci.N + 1) * 4);
     int* d_nbs = (int*)take((size_t)std::max(2 * ci.nb, 1) * 4);
+    int* d_ko = (int*)take((size_t)(ci.N + 1) * 4);
+    int* d_kc = (int*)take((size_t)std::max(ci.nnz, 1) * 4);
+    double* d_kv = (double*)take((size_t)std::max(ci.nnz, 1) * 8);
+    float* d_kvf = (float*)take((size_t)std::max(ci.nnz, 1) * 4);
+    std::vector<float> kvf(Lt->k_val.begin(), Lt->k_val.end());
     std::vector<cudaError_t> es;
+    es.push_back(up(d_ko, Lt->k_off.data(), (size_t)(ci.N + 1) * 4));
+    if (ci.nnz) {
+      es.push_back(up(d_kc, Lt->k_col.data(), (size_t)ci.nnz * 4));
+      es.push_back(up(d_kv, Lt->k_val.data(), (size_t)ci.nnz * 8));
+      es.push_back(up(d_kvf, kvf.data(), (size_t)ci.nnz * 4));
+    }
     es.push_back(up(d_fo, fo.data(), fo.size() * 4));
     if (ci.nb) {
       es.push_back(up(d_bi, vi.data(), ci.nb * 4)); es.push_back(up(d_bj, vj.data(), ci.nb * 4));
@@ -502,6 +554,13 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     D.lat.sub = d_sub;
     D.lat.nb_off = d_nbo;
     D.lat.nb_site = d_nbs;
+    D.lat.exact = ci.exact;
+    D.lat.taylor_q = ci.taylor_q;
+    D.lat.mdtau = -p.dtau;
+    D.lat.k_off = d_ko;
+    D.lat.k_col = d_kc;
+    D.lat.k_val = d_kv;
+    D.lat.k_valf = d_kvf;
     D.N = ci.N; D.L = ci.L; D.tw = ci.tw; D.n = ci.n; D.ns[0] = ci.ns[0]; D.ns[1] = ci.ns[1];
     D.charge = p.U < 0;
     D.prec = prec;
@@ -567,9 +626,10 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
         pc.n++;
         pc.M = std::max(pc.M, std::max(info[c].ns[0], info[c].ns[1]));
         pc.Nmax = std::max(pc.Nmax, info[c].N);
+        if (info[c].exact) pc.pcols = 2;
       }
       if (!pc.n) continue;
-      pc.buf = lq::staging_bytes(pc.M, pc.Nmax);
+      pc.buf = lq::staging_bytes(pc.M, pc.Nmax, pc.pcols);
       const int per_sm = lq::max_active_sweep_ctas(prec, pc.M, lq::smem_bytes(pc.M, pc.Nmax, pc.buf));
       if (per_sm < 1) { lq_sim_destroy(S); return fail(LQ_EUNSUPPORTED, "shared-memory plan does not fit one CTA per SM"); }
       pc.grid = std::min(pc.n, sms * per_sm);
@@ -746,7 +806,7 @@ extern "C" lq_status lq_sim_autotune(lq_sim* S, int32_t sweeps_per_candidate, in
     if (host_buf2) host_buf2[k] = pc.n ? pc.buf : 0;
     if (!pc.n) continue;
     const auto key = std::make_tuple(S->prec, k, pc.M, pc.Nmax, chain_bucket(pc.n));
-    const int need = lq::staging_min_bytes(pc.M, pc.Nmax);
+    const int need = lq::staging_min_bytes(pc.M, pc.Nmax, pc.pcols);
     // a feasible (grid, fits) for a candidate buffer
     auto feasible = [&](int buf, int* grid) {
       if (buf < need) return false;
@@ -1069,7 +1129,17 @@ const LqChainDev* lq_internal_sim_host_desc(const lq_sim* S) { return S->h.data(
 size_t lq_internal_footprint(const lq_lattice* L, const lq_params* p) {
   const long Ll = std::lround(p->beta / p->dtau);
   const int ns[2] = {p->n_up, p->n_dn};
-  return footprint_one(L->N, (int)L->bi.size(), L->G, (int)Ll, std::max(p->n_stab, 1), ns, p->precision, 1 << 16);
+  return footprint_one(L->N, (int)L->bi.size(), L->G, (int)Ll, std::max(p->n_stab, 1), ns, p->precision, 1 << 16,
+                       p->kinetic == LQ_EXACT);
+}
+
+extern "C" lq_status lq_request_footprint(const lq_lattice* L, const lq_params* p, size_t* bytes) {
+  if (!L || !p || !bytes) return fail(LQ_EINVAL, "bad arguments to lq_request_footprint");
+  if (!(p->beta > 0) || !(p->dtau > 0) || p->n_stab < 1 || p->n_up < 0 || p->n_dn < 0 || p->n_up > L->N ||
+      p->n_dn > L->N)
+    return fail(LQ_EINVAL, "parameters out of range");
+  *bytes = lq_internal_footprint(L, p);
+  return LQ_OK;
 }
 
 void lq_internal_obs_stats(const double* rec, int n, int nbins, double* mean, double* err) {

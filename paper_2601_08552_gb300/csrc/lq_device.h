@@ -18,6 +18,7 @@ static inline void lq_dw_split(double x, float out[2]) {
                            // flips and those matrices live in a global workspace per CTA
 #define LQ_THREADS 256     // threads per CTA (one CTA per chain)
 #define LQ_WIN 8           // sites per field-flip window (submatrix update)
+#define LQ_SWEEP_RING 32   // per-sweep wall times a chain descriptor keeps
 // 8-byte elements of one spin's window: x rows, y rows (K x MP each), G (K x (K+1)), c (K),
 // c-scaled G factors of the x/y recurrences (K x K)
 #define LQ_WIN_ELEMS(MP) (2 * LQ_WIN * (MP) + LQ_WIN * (LQ_WIN + 1) + LQ_WIN + LQ_WIN * LQ_WIN)
@@ -46,6 +47,15 @@ struct LqLatticeDev {
   const int* sub;           // sublattice label 0/1
   const int* nb_off;        // N + 1 offsets into nb_site
   const int* nb_site;       // each site's distinct bond partners, ascending
+  // exact kinetic propagator e^{-dtau K} (LQ_EXACT): K in compressed rows
+  // (the onsite term on the diagonal), applied as a Taylor polynomial of
+  // degree taylor_q in -dtau K evaluated by Horner's rule
+  int exact, taylor_q;
+  double mdtau;             // -dtau
+  const int* k_off;         // N + 1 row offsets
+  const int* k_col;         // column of each entry, ascending within a row
+  const double* k_val;      // K_ij
+  const float* k_valf;      // the same in FP32 (FP32 panels)
 };
 
 struct LqChainDev {
@@ -88,4 +98,5 @@ struct LqChainDev {
                             // then two parts of the swaps: removal (with Q streaming), addition
   long long sweep_ns_last;  // wall time of the chain's most recent sweep (device global timer)
   long long sweep_ns_sum;   // summed wall time of its sweeps (the caller may reset it)
+  long long sweep_ns_ring[LQ_SWEEP_RING];  // wall time of sweep k at [k % LQ_SWEEP_RING]
 };

@@ -8,11 +8,12 @@
 namespace lq {
 size_t smem_bytes(int M, int Nmax, int buf_bytes) { return plan_smem(M, Nmax, buf_bytes).total; }
 size_t workspace_bytes(int M, int Nmax, int buf_bytes) { return plan_smem(M, Nmax, buf_bytes).ws_cta; }
-int staging_min_bytes(int M, int Nmax) {
-  // one panel column (N values) for the propagation; for big plans one window
-  // of sites for the flip staging
+int staging_min_bytes(int M, int Nmax, int prop_cols) {
+  // prop_cols panel columns (N values each: 1 for the checkerboard, 2 for the
+  // exact propagator's Horner buffers) for the propagation; for big plans one
+  // window of sites for the flip staging
   const int MP = (M < 1 ? 1 : M) | 1;
-  size_t b = (size_t)Nmax * 8;
+  size_t b = (size_t)Nmax * 8 * (prop_cols < 1 ? 1 : prop_cols);
   if (b < 16 * 1024) b = 16 * 1024;
   if (M > LQ_NS_SMALL) {
     const size_t w = (size_t)LQ_WIN * (4 * (size_t)MP * 8 + 32);
@@ -20,11 +21,12 @@ int staging_min_bytes(int M, int Nmax) {
   }
   return (int)b;
 }
-int staging_bytes(int M, int Nmax) {
-  // propagation needs one panel column (N values); the flip staging of the
-  // big path needs at least one window of sites (four rows of MP per site)
+int staging_bytes(int M, int Nmax, int prop_cols) {
+  // propagation needs prop_cols panel columns (N values each); the flip
+  // staging of the big path needs at least one window of sites (four rows of
+  // MP per site)
   const int MP = (M < 1 ? 1 : M) | 1;
-  size_t b = (size_t)Nmax * 8;
+  size_t b = (size_t)Nmax * 8 * (prop_cols < 1 ? 1 : prop_cols);
   if (b < 48 * 1024) b = 48 * 1024;
   if (M > LQ_NS_SMALL) {
     const size_t w = (size_t)LQ_WIN * (4 * (size_t)MP * 8 + 32);
@@ -229,6 +231,18 @@ cudaError_t launch_swap_ratio(int prec, LqChainDev* chains, int c, int sg, int k
 }  // namespace lq
 
 namespace lq {
+// The flip loop's FP64 quotient beside the IEEE one (test hook).
+__global__ void quotient_kernel(const double* d, const double* r, int n, double* q_ours, double* q_ieee) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    q_ours[k] = OpsF64<double>::div(d[k], r[k]);
+    q_ieee[k] = d[k] / r[k];
+  }
+}
+cudaError_t launch_quotient(const double* d, const double* r, int n, double* q_ours, double* q_ieee, cudaStream_t st) {
+  quotient_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(d, r, n, q_ours, q_ieee);
+  return cudaGetLastError();
+}
+
 int max_active_sweep_ctas(int prec, int M, size_t smem) {
   int n = 0;
   const void* fn = sweep_fn(prec, M > LQ_NS_SMALL);

@@ -12,8 +12,10 @@ namespace lq {
 // plan wants for M particles per spin and Nmax sites.
 size_t smem_bytes(int M, int Nmax, int buf_bytes);
 size_t workspace_bytes(int M, int Nmax, int buf_bytes);
-int staging_bytes(int M, int Nmax);
-int staging_min_bytes(int M, int Nmax);  // the smallest staging buffer a plan can run with
+// prop_cols: panel columns the propagation stages at once (1 for the
+// checkerboard, 2 when a chain uses the exact kinetic propagator)
+int staging_bytes(int M, int Nmax, int prop_cols = 1);
+int staging_min_bytes(int M, int Nmax, int prop_cols = 1);  // the smallest staging buffer a plan can run with
 cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
                          int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st, void* ws,
                          size_t ws_bytes, const int* caps = nullptr, long long budget_ns = 0);
@@ -26,4 +28,6 @@ cudaError_t launch_field_ratio(int prec, LqChainDev* chains, int c, int l, int i
 cudaError_t launch_swap_ratio(int prec, LqChainDev* chains, int c, int sg, int k, int j, int M, int Nmax,
                               int buf_bytes, cudaStream_t st, void* ws, size_t ws_bytes);
 int max_active_sweep_ctas(int prec, int M, size_t smem);
+// the flip loop's FP64 quotient d/r and the IEEE one, elementwise (device arrays of n)
+cudaError_t launch_quotient(const double* d, const double* r, int n, double* q_ours, double* q_ieee, cudaStream_t st);
 }  // namespace lq

@@ -17,6 +17,12 @@ struct lq_lattice_view {
   const int* sub;          // N sublattice labels
   const int* nb_off;       // N + 1 offsets into nb_site
   const int* nb_site;      // each site's distinct bond partners, ascending
+  // K in compressed rows (bonds summed, onsite term on the diagonal)
+  int nnz;
+  const int* k_off;
+  const int* k_col;
+  const double* k_val;
+  double k_rownorm;        // max_i sum_j |K_ij|
 };
 
 lq_lattice_view lq_lattice_get_view(const lq_lattice* L);
@@ -32,3 +38,20 @@ static inline void lq_bond_factors(double dtau, double k, double* c, double* s) 
   *s = -std::sinh(dtau * k);
 }
 static inline double lq_onsite_factor(double dtau, double eps) { return std::exp(-dtau * eps); }
+
+// Degree of the Taylor polynomial that stands for e^{-dtau K} in the exact
+// kinetic mode, for theta = dtau max_i sum_j |K_ij| >= ||dtau K||: the
+// smallest q whose remainder bound theta^{q+1} / (q+1)! / (1 - theta/(q+2))
+// is below 1e-17 e^{-theta}, a lower bound of the smallest singular value of
+// e^{-dtau K}, i.e. below 1e-17 relative to every column the propagator
+// produces.  Exact chains need theta <= LQ_EXACT_THETA_MAX.
+#define LQ_EXACT_THETA_MAX 2.0
+static inline int lq_taylor_degree(double theta) {
+  double term = theta;  // theta^{q+1} / (q+1)! at q = 0
+  for (int q = 1; q <= 64; ++q) {
+    term *= theta / (double)(q + 1);
+    const double tail = term / (1.0 - theta / (double)(q + 2));
+    if (tail <= 1e-17 * std::exp(-theta)) return q;
+  }
+  return 64;
+}

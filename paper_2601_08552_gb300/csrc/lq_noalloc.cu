@@ -67,6 +67,19 @@ cudaError_t upload_factors(const lq_lattice_view& v, double dtau, unsigned char*
   return e;
 }
 
+// FP32 copies of n doubles, converted through the same small stack buffer.
+cudaError_t upload_floats(const double* src, int n, unsigned char* dst, cudaStream_t st) {
+  constexpr int CH = 256;
+  float f[CH];
+  cudaError_t e = cudaSuccess;
+  for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += CH) {
+    const int k = std::min(CH, n - i0);
+    for (int t = 0; t < k; ++t) f[t] = (float)src[i0 + t];
+    e = cudaMemcpyAsync(dst + (size_t)i0 * 4, f, (size_t)k * 4, cudaMemcpyHostToDevice, st);
+  }
+  return e;
+}
+
 }  // namespace
 
 extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p, uint32_t chain_id,
@@ -87,6 +100,11 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   if (p->swap_mode != LQ_SWAP_UNIFORM && p->swap_mode != LQ_SWAP_NEIGHBOUR)
     return lq_internal_fail(LQ_EINVAL, "swap_mode must be LQ_SWAP_UNIFORM or LQ_SWAP_NEIGHBOUR");
   if (p->left_swaps != 0 && p->left_swaps != 1) return lq_internal_fail(LQ_EINVAL, "left_swaps must be 0 or 1");
+  if (p->kinetic != LQ_CHECKERBOARD && p->kinetic != LQ_EXACT)
+    return lq_internal_fail(LQ_EINVAL, "kinetic must be LQ_CHECKERBOARD or LQ_EXACT");
+  const int exact = p->kinetic == LQ_EXACT;
+  if (exact && p->dtau * v.k_rownorm > LQ_EXACT_THETA_MAX)
+    return lq_internal_fail(LQ_EUNSUPPORTED, "LQ_EXACT needs dtau * max_i sum_j |K_ij| <= 2");
   if (p->n_up > LQ_MAX_PARTICLES || p->n_dn > LQ_MAX_PARTICLES)
     return lq_internal_fail(LQ_EUNSUPPORTED, "at most LQ_MAX_PARTICLES particles per spin");
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -115,6 +133,8 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   const size_t o_bc = take(nb * 8), o_bs = take(nb * 8), o_bcf = take(nb * 4), o_bsf = take(nb * 4);
   const size_t o_eps = take(N * 8), o_ce = take(N * 8), o_cef = take(N * 4), o_sub = take(N * 4);
   const size_t o_nbo = take((size_t)(N + 1) * 4), o_nbs = take((size_t)std::max(2 * nb, 1) * 4);
+  const size_t o_ko = take((size_t)(N + 1) * 4), o_kc = take((size_t)std::max(v.nnz, 1) * 4);
+  const size_t o_kv = take((size_t)std::max(v.nnz, 1) * 8), o_kvf = take((size_t)std::max(v.nnz, 1) * 4);
   size_t o_QR[2][2], o_VR[2][2], o_QL[2], o_VL[2], o_st[2], o_live[2], o_work[2];
   for (int sg = 0; sg < 2; ++sg) {
     const size_t pn = (size_t)N * ns[sg], qn = (size_t)ns[sg] * ns[sg];
@@ -125,7 +145,7 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   }
   const size_t o_vec = take((size_t)2 * N * 8), o_rot = take((size_t)n * LQ_NS_MAX * 2 * 8);
   const int M = std::max(std::max(ns[0], ns[1]), 1);
-  const int buf_bytes = lq::staging_bytes(M, N);
+  const int buf_bytes = lq::staging_bytes(M, N, exact ? 2 : 1);
   const size_t ws_bytes = lq::workspace_bytes(M, N, buf_bytes);  // one CTA's slab (big plans only)
   const size_t o_ws = take(ws_bytes);
   if (o > (size_t)LQ_NOALLOC_SCRATCH_BYTES)
@@ -147,6 +167,10 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   if (e == cudaSuccess) e = up(o_sub, v.sub, N * 4);
   if (e == cudaSuccess) e = up(o_nbo, v.nb_off, (size_t)(N + 1) * 4);
   if (e == cudaSuccess) e = up(o_nbs, v.nb_site, (size_t)v.nb_off[N] * 4);
+  if (e == cudaSuccess) e = up(o_ko, v.k_off, (size_t)(N + 1) * 4);
+  if (e == cudaSuccess) e = up(o_kc, v.k_col, (size_t)v.nnz * 4);
+  if (e == cudaSuccess) e = up(o_kv, v.k_val, (size_t)v.nnz * 8);
+  if (e == cudaSuccess) e = upload_floats(v.k_val, v.nnz, base + o_kvf, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_order, 0, sizeof(int), st);
   if (e != cudaSuccess) return lq_internal_fail(LQ_ECUDA, std::string("lq_sweep_noalloc upload: ") + cudaGetErrorString(e));
   if (e == cudaSuccess) e = upload_factors(v, p->dtau, base, o_bc, o_bs, o_bcf, o_bsf, o_ce, o_cef, st);
@@ -169,6 +193,13 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   D.lat.sub = (const int*)(base + o_sub);
   D.lat.nb_off = (const int*)(base + o_nbo);
   D.lat.nb_site = (const int*)(base + o_nbs);
+  D.lat.exact = exact;
+  D.lat.taylor_q = exact ? lq_taylor_degree(p->dtau * v.k_rownorm) : 0;
+  D.lat.mdtau = -p->dtau;
+  D.lat.k_off = (const int*)(base + o_ko);
+  D.lat.k_col = (const int*)(base + o_kc);
+  D.lat.k_val = (const double*)(base + o_kv);
+  D.lat.k_valf = (const float*)(base + o_kvf);
   D.N = N; D.L = L; D.tw = tw; D.n = n; D.ns[0] = ns[0]; D.ns[1] = ns[1];
   D.charge = p->U < 0;
   D.prec = p->precision;

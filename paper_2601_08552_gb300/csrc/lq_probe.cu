@@ -12,6 +12,7 @@
 #include <string>
 
 #include "../../include/lecqmc.h"
+#include "lq_kernels.h"
 #include "lq_lattice.h"
 
 namespace {
@@ -109,5 +110,24 @@ extern "C" lq_status lq_device_fp64_rate(double ms, double* host_tflops, double*
   if (e1) cudaEventDestroy(e1);
   cudaFree(out);
   if (e != cudaSuccess) return probe_fail(e, "fp64 rate probe");
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_test_quotient(int32_t n, const double* host_d, const double* host_r, double* host_q,
+                                      double* host_q_ieee) {
+  if (n < 0 || (n > 0 && (!host_d || !host_r || !host_q || !host_q_ieee)))
+    return lq_internal_fail(LQ_EINVAL, "bad arguments to lq_test_quotient");
+  if (n == 0) return LQ_OK;
+  double* buf = nullptr;
+  const size_t b = sizeof(double) * (size_t)n;
+  cudaError_t e = cudaMalloc((void**)&buf, 4 * b);
+  if (e != cudaSuccess) return probe_fail(e, "quotient buffers");
+  e = cudaMemcpy(buf, host_d, b, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(buf + n, host_r, b, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = lq::launch_quotient(buf, buf + n, n, buf + 2 * (size_t)n, buf + 3 * (size_t)n, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(host_q, buf + 2 * (size_t)n, b, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(host_q_ieee, buf + 3 * (size_t)n, b, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return probe_fail(e, "quotient test");
   return LQ_OK;
 }

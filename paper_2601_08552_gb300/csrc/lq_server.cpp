@@ -46,6 +46,7 @@ struct Pending {
   uint32_t chain_id;
   size_t footprint;
   double t_submit;
+  int waited_for_memory;
 };
 
 struct Active {
@@ -60,6 +61,46 @@ struct Active {
   double cost;          // cost-model units per sweep
   long long last_ns;    // measured duration of its latest sweep (0 until one ran)
   double sweep_ms_sum;
+  int active_at_admit;  // requests already on the device when this one was admitted
+  int waited_for_memory;  // 1 if it reached the head of the queue and had to wait for memory to be freed
+};
+
+// Latency samples in a fixed histogram: 200 logarithmic bins per decade from
+// 1 microsecond to 10^4 s (a bin is 1.2 % wide), so the store does not grow
+// with the number of sweeps and a percentile costs one pass over the bins.
+struct LatencyHist {
+  static constexpr int kPerDecade = 200, kDecades = 10;
+  static constexpr double kLo = 1e-3;  // ms
+  std::vector<long long> bins = std::vector<long long>(kPerDecade * kDecades + 2, 0);
+  long long n = 0;
+  double lo = 0.0, hi = 0.0;
+  void add(double ms, long long count = 1) {
+    if (count <= 0 || !(ms >= 0.0)) return;
+    int b;
+    if (ms < kLo) b = 0;
+    else {
+      b = 1 + (int)std::floor(std::log10(ms / kLo) * kPerDecade);
+      if (b > kPerDecade * kDecades) b = kPerDecade * kDecades + 1;
+    }
+    bins[b] += count;
+    if (n == 0 || ms < lo) lo = ms;
+    if (n == 0 || ms > hi) hi = ms;
+    n += count;
+  }
+  // the q-quantile as the geometric centre of its bin (clamped to the extremes seen)
+  double quantile(double q) const {
+    if (n == 0) return 0.0;
+    const long long want = (long long)std::ceil(q * (double)n);
+    long long c = 0;
+    for (size_t b = 0; b < bins.size(); ++b) {
+      c += bins[b];
+      if (c >= std::max(want, 1LL)) {
+        double v = b == 0 ? lo : kLo * std::pow(10.0, ((double)b - 0.5) / kPerDecade);
+        return std::min(std::max(v, lo), hi);
+      }
+    }
+    return hi;
+  }
 };
 
 double now_s() {
@@ -98,8 +139,9 @@ struct lq_server {
   double tick_target_ms = 20.0;
   double ns_per_cost = 0.0;  // running estimate of sweep nanoseconds per cost unit
   // statistics
-  std::vector<double> sweep_ms;  // one sample per sweep: that chain's sweep time in its tick
-  std::vector<double> tick_ms;   // one sample per launch
+  LatencyHist sweep_ms;       // one sample per sweep: that sweep's own device time
+  LatencyHist tick_ms;        // one sample per batched launch
+  LatencyHist wall_sweep_ms;  // one sample per request: (retirement - submission) / sweeps
   long long submitted = 0, admitted = 0, completed = 0, rejected = 0;
   double updates_done = 0.0, busy_s = 0.0, t_start = 0.0, admit_s = 0.0, retire_s = 0.0;
   std::string last_err;
@@ -175,9 +217,13 @@ static void retire_impl(lq_server* S, Active& a) {
   r.queue_ms = 1e3 * (a.t_admit - a.t_submit);
   r.total_ms = 1e3 * (now_s() - a.t_submit);
   r.sweep_ms_mean = a.done ? a.sweep_ms_sum / a.done : 0.0;
+  r.wall_ms_per_sweep = a.done ? r.total_ms / a.done : 0.0;
+  r.active_at_admit = a.active_at_admit;
+  r.waited_for_memory = a.waited_for_memory;
   lq_sim_destroy(a.sim);
   lq_lattice_destroy(a.lat);
   std::lock_guard<std::mutex> g(S->mu);
+  if (a.done) S->wall_sweep_ms.add(r.wall_ms_per_sweep);
   S->in_use -= a.footprint;
   S->done[a.id] = r;
   S->state[a.id] = 2;
@@ -198,6 +244,8 @@ static void admit(lq_server* S) {
       in_use += S->queue.front().footprint;
       S->queue.pop_front();
     }
+    // the head of the queue that does not fit waits for a retirement
+    if (!S->queue.empty() && in_use + S->queue.front().footprint > S->budget) S->queue.front().waited_for_memory = 1;
     S->in_use = in_use;
   }
   if (take.empty()) return;
@@ -220,6 +268,8 @@ static void admit(lq_server* S) {
     a.updates_per_sweep = 2LL * (long long)std::lround(p.params.beta / p.params.dtau) * lq_lattice_get_view(p.lat).N;
     a.last_ns = 0;
     a.sweep_ms_sum = 0.0;
+    a.active_at_admit = (int)S->active.size();
+    a.waited_for_memory = p.waited_for_memory;
     fresh.push_back(a);
     M = std::max(M, inf.M);
     Nmax = std::max(Nmax, inf.Nmax);
@@ -356,16 +406,24 @@ static void tick(lq_server* S) {
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  std::vector<double> samples;
+  std::vector<std::pair<double, long long>> samples;  // (ms, count)
   double upd = 0.0, ratio_sum = 0.0;
   int ratio_n = 0;
   for (int k = 0; k < n; ++k) {
     Active& a = S->active[k];
     const int d = (int)(desc[k].sweep - a.desc.sweep);
     if (d > 0) {
-      const double per_ms = 1e-6 * (double)desc[k].sweep_ns_sum / d;
-      for (int t = 0; t < d; ++t) samples.push_back(per_ms);
-      a.sweep_ms_sum += per_ms * d;
+      // each sweep's own time from the descriptor's ring; a chain that ran
+      // more sweeps than the ring holds gives the rest their mean
+      const int kept = std::min(d, LQ_SWEEP_RING);
+      double kept_ns = 0.0;
+      for (int t = d - kept; t < d; ++t) {
+        const long long ns = desc[k].sweep_ns_ring[(a.desc.sweep + (uint32_t)t) % LQ_SWEEP_RING];
+        kept_ns += (double)ns;
+        samples.emplace_back(1e-6 * (double)ns, 1);
+      }
+      if (d > kept) samples.emplace_back(1e-6 * ((double)desc[k].sweep_ns_sum - kept_ns) / (d - kept), d - kept);
+      a.sweep_ms_sum += 1e-6 * (double)desc[k].sweep_ns_sum;
       a.last_ns = desc[k].sweep_ns_last;
       if (a.cost > 0) { ratio_sum += (double)desc[k].sweep_ns_last / a.cost; ++ratio_n; }
       upd += (double)d * (double)a.updates_per_sweep;
@@ -378,8 +436,8 @@ static void tick(lq_server* S) {
   {
     std::lock_guard<std::mutex> g(S->mu);
     S->busy_s += ms * 1e-3;
-    S->tick_ms.push_back(ms);
-    S->sweep_ms.insert(S->sweep_ms.end(), samples.begin(), samples.end());
+    S->tick_ms.add(ms);
+    for (const auto& sm : samples) S->sweep_ms.add(sm.first, sm.second);
     S->updates_done += upd;
     if (e != cudaSuccess) S->last_err = cudaGetErrorString(e);
   }
@@ -491,6 +549,7 @@ extern "C" lq_status lq_server_submit(lq_server* S, const lq_request* req, uint6
   p.chain_id = req->chain_id;
   p.footprint = fp;
   p.t_submit = now_s();
+  p.waited_for_memory = 0;
   S->queue.push_back(p);
   S->state[p.id] = 0;
   S->submitted++;
@@ -517,19 +576,14 @@ extern "C" lq_status lq_server_stats(lq_server* S, lq_server_info* out) {
   if (!S || !out) return srv_fail(LQ_EINVAL, "bad arguments");
   std::lock_guard<std::mutex> g(S->mu);
   std::memset(out, 0, sizeof(*out));
-  std::vector<double> t = S->sweep_ms;
-  if (!t.empty()) {
-    std::sort(t.begin(), t.end());
-    out->p50_sweep_ms = t[(size_t)(0.50 * (t.size() - 1))];
-    out->p99_sweep_ms = t[(size_t)(0.99 * (t.size() - 1))];
-  }
-  t = S->tick_ms;
-  if (!t.empty()) {
-    std::sort(t.begin(), t.end());
-    out->p50_tick_ms = t[(size_t)(0.50 * (t.size() - 1))];
-    out->p99_tick_ms = t[(size_t)(0.99 * (t.size() - 1))];
-  }
-  out->ticks = (int64_t)S->tick_ms.size();
+  out->p50_sweep_ms = S->sweep_ms.quantile(0.50);
+  out->p99_sweep_ms = S->sweep_ms.quantile(0.99);
+  out->p50_tick_ms = S->tick_ms.quantile(0.50);
+  out->p99_tick_ms = S->tick_ms.quantile(0.99);
+  out->p50_wall_sweep_ms = S->wall_sweep_ms.quantile(0.50);
+  out->p99_wall_sweep_ms = S->wall_sweep_ms.quantile(0.99);
+  out->sweeps = S->sweep_ms.n;
+  out->ticks = (int64_t)S->tick_ms.n;
   out->submitted = S->submitted;
   out->admitted = S->admitted;
   out->completed = S->completed;

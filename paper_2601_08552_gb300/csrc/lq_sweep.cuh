@@ -319,11 +319,74 @@ __device__ __forceinline__ bool dw_gt(dw a, dw b) { return a.h > b.h || (a.h == 
 // Columns are independent, so the panel goes through shared memory in column
 // chunks; each family is one parallel pass of 2x2 rotations there.
 // ---------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ const R* kval_ptr(const LqLatticeDev& L);
+template <> __device__ __forceinline__ const double* kval_ptr<double>(const LqLatticeDev& L) { return L.k_val; }
+template <> __device__ __forceinline__ const float* kval_ptr<float>(const LqLatticeDev& L) { return L.k_valf; }
+
+// Exact kinetic propagator: dst <- D_post e^{-dtau K} D_pre src.  K is
+// symmetric, so B_K and B_K^T are the same operator.  For each column chunk,
+// Horner's rule y <- x + (-dtau/k) K y, k = q .. 1, starting from y = x,
+// evaluates sum_{j <= q} (-dtau K)^j x / j! with two buffers in shared
+// memory; x = D_pre src is re-read from src at each step (src is written, in
+// place, only after the last step).
+template <class R, class S>
+__device__ void prop_exact(const LqChainDev& C, int sigma, R* dst, const S* src, int m, int ld, int preD, int postD,
+                           Smem& sm) {
+  const int N = C.N;
+  const LqLatticeDev& lat = C.lat;
+  R* buf = (R*)sm.buf;
+  int cmax = sm.buf_bytes / (int)(2 * sizeof(R) * N);
+  if (cmax > m) cmax = m;
+  if (cmax < 1) cmax = 1;  // the staging plan holds at least two columns for exact chains
+  const int8_t* spre = preD >= 0 ? C.s + (size_t)preD * N : nullptr;
+  const int8_t* spost = postD >= 0 ? C.s + (size_t)postD * N : nullptr;
+  const R* kv = kval_ptr<R>(lat);
+  const int* ko = lat.k_off;
+  const int* kc = lat.k_col;
+  for (int c0 = 0; c0 < m; c0 += cmax) {
+    const int cw = min(cmax, m - c0);
+    const int tot = N * cw;
+    R* y0 = buf;
+    R* y1 = buf + tot;
+    for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+      const int i = idx / cw, a = idx - i * cw;
+      R v = (R)src[(size_t)i * ld + c0 + a];
+      if (spre) v *= (R)dfac(C, sigma, spre[i]);
+      y0[idx] = v;
+    }
+    __syncthreads();
+    for (int k = lat.taylor_q; k >= 1; --k) {
+      const R ck = (R)(lat.mdtau / (double)k);
+      for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+        const int i = idx / cw, a = idx - i * cw;
+        R acc = (R)0;
+        for (int p = ko[i]; p < ko[i + 1]; ++p) acc += kv[p] * y0[kc[p] * cw + a];
+        R x = (R)src[(size_t)i * ld + c0 + a];
+        if (spre) x *= (R)dfac(C, sigma, spre[i]);
+        y1[idx] = x + ck * acc;
+      }
+      __syncthreads();
+      R* t = y0; y0 = y1; y1 = t;
+    }
+    for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+      const int i = idx / cw, a = idx - i * cw;
+      R v = y0[idx];
+      if (spost) v *= (R)dfac(C, sigma, spost[i]);
+      dst[(size_t)i * ld + c0 + a] = v;
+    }
+    __syncthreads();
+  }
+}
+
 template <class R, class S>
 __device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m, int ld, int preD, int op, int postD,
                      Smem& sm) {
   PhaseTimer pt_(1);
   if (m == 0) return;
+  if (op != 0 && C.lat.exact) {
+    prop_exact<R, S>(C, sigma, dst, src, m, ld, preD, postD, sm);
+    return;
+  }
   const int N = C.N;
   const LqLatticeDev& lat = C.lat;
   R* buf = (R*)sm.buf;
@@ -584,14 +647,21 @@ template <class RowT> struct OpsF64 {
   __device__ static V xor_(V a, int o) { return __shfl_xor_sync(FULL, a, o); }
   __device__ static V from_lane(V a, int src) { return __shfl_sync(FULL, a, src); }
   __device__ static V one_plus(V d, V g) { return fma(d, g, 1.0); }
+  // d / r without the IEEE division sequence: the hardware reciprocal seed
+  // x0 (rcp.approx.ftz.f64) refined by one third-order step of the
+  // Newton-Raphson family for 1/r.  With e = 1 - r x0 exact to rounding,
+  // 1/r = x0 / (1 - e) = x0 (1 + e + e^2 + ...), so d x0 (1 + e + e^2) leaves
+  // a truncation error e^3 (below 2^-60 for a seed good to 2^-20) and a few
+  // roundings: at most 4 ulp from the correctly rounded quotient for normal
+  // operands (tested against the IEEE quotient on the device).  Four FP64
+  // instructions after the seed, against six for two second-order steps.
   __device__ static V div(V d, V r) {
     double x0;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x0) : "d"(r));
-    double e = fma(-r, x0, 1.0);
-    x0 = fma(x0, e, x0);
-    e = fma(-r, x0, 1.0);
-    x0 = fma(x0, e, x0);
-    return d * x0;
+    const double e = fma(-r, x0, 1.0);
+    const double p = fma(e, e, e);
+    const double y0 = d * x0;
+    return fma(y0, p, y0);
   }
   __device__ static double pack(V v) { return v; }
   __device__ static V unpack(double v) { return v; }
@@ -940,6 +1010,255 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
   }
 }
 
+// ---------------------------------------------------------------------------
+// Field flips for m <= 16 particles per spin: the same submatrix update in
+// windows of K = 4 sites, with the work of a window spread over the CTA and
+// the serial chain of BOTH spins on one leader warp:
+//   A  (all warps)  x_t = R~_t T and y_t = T L~_t of both spins, one output
+//                   per thread;
+//   B  (leader)     the window blocks G = X L~_W of both spins, one element
+//                   per lane (lanes 0-15 spin up, 16-31 spin down);
+//   C  (leader)     per site: G[t][t], the ratio factor 1 + Delta G[t][t] of
+//                   each spin, their product by one shuffle between the half
+//                   warps, the Metropolis test, and the rank-1 update of the
+//                   rest of each block (one element per lane);
+//   D  (4 warps)    the x and y recurrences of both spins, one warp each;
+//   E  (all warps)  T -= sum_t (c_t y_t) x_t^T of both spins.
+// On GB300 an FP64 warp instruction occupies its sub-partition for tens of
+// cycles whatever the number of active lanes, so the per-site chain is the
+// count of dependent FP64 instructions on one warp: this path keeps it at the
+// ratio, the quotient, the product and one update per site for both spins at
+// once, and moves every m-length product off it.
+// ---------------------------------------------------------------------------
+template <class R, class Ops, int MT>
+__device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag,
+                                Smem& sm) {
+  PhaseTimer pt_(PH_FLIP);
+  typedef typename Ops::V V;
+  typedef typename Ops::Row Row;
+  typedef typename Ops::U U;
+  constexpr int K = 4, KP = K + 1;
+  constexpr int NXY = 2 * 2 * K * MT;  // x and y outputs of both spins
+  constexpr int NT = 2 * MT * MT;      // T elements of both spins
+  constexpr int GP = MT >= 16 ? 4 : 2; // partial sums of the m-long products
+  const int N = C.N, MP = sm.MP;
+  const int m0 = C.ns[0], m1 = C.ns[1];
+  const size_t per_site = (size_t)4 * MP * sizeof(Row) + 8 + sizeof(U) + 4 + 4;
+  int cs = (int)(sm.buf_bytes / per_site);
+  if (cs > 512) cs = 512;
+  Row* rrow = (Row*)sm.buf;
+  Row* lrow = rrow + (size_t)2 * cs * MP;
+  double* racc = (double*)(lrow + (size_t)2 * cs * MP);  // accepted ratios (packed), multiplied per chunk
+  U* uni = (U*)(racc + cs);
+  int* sf = (int*)(uni + cs);
+  int* af = sf + cs;
+  const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
+  const int warp = TID >> 5, lane = TID & 31;
+  const bool leader = warp == sm.ip[14];
+  V* const win0 = (V*)sm.win;
+  // window buffers of spin sg: X (K x MP), Y (K x MP), G (K x KP), c (K), c-scaled G factors (K x K)
+  auto Xb = [&](int sg) { return win0 + (size_t)sg * LQ_WIN_ELEMS(MP); };
+  auto Yb = [&](int sg) { return Xb(sg) + K * MP; };
+  auto Gb = [&](int sg) { return Yb(sg) + K * MP; };
+  auto cb = [&](int sg) { return Gb(sg) + K * KP; };
+  auto CGb = [&](int sg) { return cb(sg) + K; };
+  for (int i0 = 0; i0 < N; i0 += cs) {
+    const int cn = min(cs, N - i0);
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = sg ? m1 : m0;
+      const R* rp = sg ? Rp1 : Rp0;
+      const R* lp = sg ? Lp1 : Lp0;
+      Row* rr = rrow + (size_t)sg * cs * MP;
+      Row* ll = lrow + (size_t)sg * cs * MP;
+      for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
+        const int a = TID % MT;
+        if (a < m) {
+          rr[(size_t)ii * MP + a] = (Row)rp[(size_t)(i0 + ii) * m + a];
+          ll[(size_t)ii * MP + a] = (Row)lp[(size_t)(i0 + ii) * m + a];
+        }
+      }
+    }
+    for (int ii = TID; ii < cn; ii += LQ_THREADS) {
+      uint32_t w[4];
+      philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
+      uni[ii] = Ops::make_u(u53(w[0], w[1]));
+      sf[ii] = C.s[(size_t)l * N + i0 + ii];
+    }
+    __syncthreads();
+    int wsign = 1, nacc = 0, nbad = 0;  // kept by the leader's lane 0
+    for (int t0 = 0; t0 < cn; t0 += K) {
+      const int kw = min(K, cn - t0);
+      // A: x_t = R_t T (xy = 0) and y_t = T L_t (xy = 1), element (sg, xy, t, b)
+#pragma unroll
+      for (int e0 = 0; e0 < NXY; e0 += LQ_THREADS) {
+        const int e = e0 + TID;
+        const int b = e % MT, t = (e / MT) % K, xy = (e / (MT * K)) & 1, sg = e / (2 * MT * K);
+        const int m = sg ? m1 : m0;
+        if (e < NXY && t < kw && b < m) {
+          const typename Ops::TRef T = Ops::tref(sm, sg);
+          const Row* row = (xy ? lrow : rrow) + ((size_t)sg * cs + t0 + t) * MP;
+          V acc[GP];
+#pragma unroll
+          for (int q = 0; q < GP; ++q) acc[q] = Ops::zero();
+#pragma unroll
+          for (int a = 0; a < MT; ++a)
+            if (a < m) {
+              if (xy) Ops::accT(acc[a % GP], T.ld(b * MP + a), row[a]);
+              else Ops::acc(acc[a % GP], row[a], T.ld(a * MP + b));
+            }
+          V v = Ops::finish(acc[0]);
+#pragma unroll
+          for (int q = 1; q < GP; ++q) v = Ops::add(v, Ops::finish(acc[q]));
+          (xy ? Yb(sg) : Xb(sg))[t * MP + b] = v;
+        }
+      }
+      __syncthreads();
+      if (leader) {
+        const int h = lane >> 4, hl = lane & 15;
+        const int m = h ? m1 : m0;
+        const int u = hl >> 2, v = hl & 3;
+        V* Gw = Gb(h);
+        V* cw = cb(h);
+        // B: G[u][v] = x_u . L~_v of this half's spin
+        {
+          const V* xr = Xb(h) + u * MP;
+          const Row* lr = lrow + ((size_t)h * cs + t0 + v) * MP;
+          V acc[GP];
+#pragma unroll
+          for (int q = 0; q < GP; ++q) acc[q] = Ops::zero();
+#pragma unroll
+          for (int b = 0; b < MT; ++b)
+            if (b < m) Ops::accT(acc[b % GP], xr[b], lr[b]);
+          V g = Ops::finish(acc[0]);
+#pragma unroll
+          for (int q = 1; q < GP; ++q) g = Ops::add(g, Ops::finish(acc[q]));
+          if (u < kw && v < kw) Gw[u * KP + v] = g;
+        }
+        __syncwarp();
+        // C: the serial chain of both spins
+        const bool upd = m > 0 && C.lambda != 0.0;
+        const int sp = C.charge ? 1 : (h == 0 ? 1 : -1);
+        const V d_p = Ops::delta(C, true), d_m = Ops::delta(C, false);
+        const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
+        for (int t = 0; t < kw; ++t) {
+          const int ii = t0 + t;
+          const int s = sf[ii];
+          const V d = (sp * s > 0) ? d_p : d_m;
+          const V g = m > 0 ? Gw[t * KP + t] : Ops::zero();
+          const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt of this half's spin
+          const V c = Ops::div(d, rs);       // used if accepted
+          const V ro = Ops::xor_(rs, 16);    // the other spin's factor
+          V r = h ? Ops::mul(ro, rs) : Ops::mul(rs, ro);  // (up factor) x (down factor) in both halves
+          if (C.charge) r = Ops::mul(r, s > 0 ? cf_p : cf_m);
+          bool neg, bad;
+          const bool acc = Ops::accept(r, uni[ii], &neg, &bad);
+          const bool flip = acc && upd;
+          if (hl == 0) cw[t] = flip ? c : Ops::zero();
+          if (flip && u > t && v > t && u < kw && v < kw)
+            Gw[u * KP + v] = Ops::fnma(Ops::mul(c, Gw[u * KP + t]), Gw[t * KP + v], Gw[u * KP + v]);
+          if (lane == 0) {
+            af[ii] = acc ? 1 : 0;
+            racc[ii] = Ops::pack(r);
+            nbad += bad;
+            if (acc) {
+              wsign = neg ? -wsign : wsign;
+              ++nacc;
+            }
+          }
+          __syncwarp();
+        }
+        // c-scaled factors of the recurrences: CG[j][t] = c_t G[j][t] (j > t), CG[t][j] = c_t G[t][j]
+        {
+          V val = Ops::zero();
+          if (u > v && u < kw) val = Ops::mul(cw[v], Gw[u * KP + v]);
+          else if (u < v && v < kw) val = Ops::mul(cw[u], Gw[u * KP + v]);
+          CGb(h)[u * K + v] = val;
+        }
+      }
+      __syncthreads();
+      // D: x_j -= c_t G[j][t] x_t and y_j -= c_t G[t][j] y_t (j > t), t ascending; then y_t <- c_t y_t.
+      // Warp w < 4 takes spin w >> 1, x (even w) or y (odd w), element (j, b)
+      if (warp < 4) {
+        const int sg = warp >> 1, xy = warp & 1, m = sg ? m1 : m0;
+        V* Wm = xy ? Yb(sg) : Xb(sg);
+        const V* CG = CGb(sg);
+        constexpr int RE = (K * MT + 31) / 32;
+        for (int t = 0; t + 1 < kw; ++t) {
+#pragma unroll
+          for (int it = 0; it < RE; ++it) {
+            const int e = lane + 32 * it, j = e / MT, b = e % MT;
+            if (e < K * MT && j > t && j < kw && b < m)
+              Wm[j * MP + b] = Ops::fnma(xy ? CG[t * K + j] : CG[j * K + t], Wm[t * MP + b], Wm[j * MP + b]);
+          }
+          __syncwarp();
+        }
+        if (xy) {
+          const V* cw = cb(sg);
+#pragma unroll
+          for (int it = 0; it < RE; ++it) {
+            const int e = lane + 32 * it, j = e / MT, b = e % MT;
+            if (e < K * MT && j < kw && b < m) Wm[j * MP + b] = Ops::mul(cw[j], Wm[j * MP + b]);
+          }
+        }
+      }
+      __syncthreads();
+      // E: T <- T - sum_t (c_t y_t) x_t^T, element (sg, a, b)
+#pragma unroll
+      for (int e0 = 0; e0 < NT; e0 += LQ_THREADS) {
+        const int e = e0 + TID;
+        const int b = e % MT, a = (e / MT) % MT, sg = e / (MT * MT);
+        const int m = sg ? m1 : m0;
+        if (e < NT && a < m && b < m) {
+          const typename Ops::TRef T = Ops::tref(sm, sg);
+          const V* Xs = Xb(sg);
+          const V* Ys = Yb(sg);
+          V tv = T.ld(a * MP + b);
+#pragma unroll
+          for (int t = 0; t < K; ++t)
+            if (t < kw) tv = Ops::fnma(Ys[t * MP + a], Xs[t * MP + b], tv);
+          T.st(a * MP + b, tv);
+        }
+      }
+      __syncthreads();
+    }
+    if (leader) {
+      // product of the chunk's accepted ratios, lane-parallel
+      typename Ops::Prod wp;
+      wp.init();
+      for (int ii = lane; ii < cn; ii += 32)
+        if (af[ii]) wp.mul(Ops::unpack(racc[ii]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wp.combine_xor(o);
+      if (lane == 0) {
+        C.cnt[0] += cn;
+        C.cnt[1] += nacc;
+        C.logw += wp.log_value();
+        if (wsign < 0) C.sign = -C.sign;
+        if (nbad) C.err |= LQ_ERR_NONFINITE;
+      }
+    }
+    __syncthreads();
+    // rows back to the panel; accepted sites scale their row by 1 + Delta_sigma
+    for (int sg = 0; sg < 2; ++sg) {
+      const int m = sg ? m1 : m0;
+      const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
+      R* rp = sg ? Rp1 : Rp0;
+      const Row* rr = rrow + (size_t)sg * cs * MP;
+      for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
+        const int a = TID % MT;
+        if (a < m) {
+          Row v = rr[(size_t)ii * MP + a];
+          if (af[ii]) v *= (sp * sf[ii] > 0) ? opf_p : opf_m;
+          rp[(size_t)(i0 + ii) * m + a] = (R)v;
+        }
+      }
+    }
+    for (int ii = TID; ii < cn; ii += LQ_THREADS)
+      if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ void bar_group(int sg) { asm volatile("bar.sync %0, 128;" ::"r"(2 + sg) : "memory"); }
 
 // ---------------------------------------------------------------------------
@@ -1215,9 +1534,9 @@ template <class R, class Ops, bool BIG>
 __device__ void flip_slice_any(LqChainDev& C, int l, R* a, R* b, const R* c, const R* d, uint32_t tag, Smem& sm) {
   const int m = max(C.ns[0], C.ns[1]);
   if (BIG && m > LQ_NS_SMALL) flip_slice_big<R, Ops>(C, l, a, b, c, d, tag, sm);
-  else if (m <= 4) flip_slice_win<R, Ops, 4>(C, l, a, b, c, d, tag, sm);
-  else if (m <= 8) flip_slice_win<R, Ops, 8>(C, l, a, b, c, d, tag, sm);
-  else if (m <= 16) flip_slice_win<R, Ops, 16>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 4) flip_slice_pair<R, Ops, 4>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 8) flip_slice_pair<R, Ops, 8>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 16) flip_slice_pair<R, Ops, 16>(C, l, a, b, c, d, tag, sm);
   else flip_slice_win<R, Ops, 32>(C, l, a, b, c, d, tag, sm);
 }
 
@@ -1989,6 +2308,7 @@ __global__ void __launch_bounds__(LQ_THREADS, BIG ? 1 : 2)
       if (C.left_swaps) swap_phase<R>(C, sm, 1);
       if (TID == 0) {
         const long long t_now = global_ns();
+        C.sweep_ns_ring[C.sweep % LQ_SWEEP_RING] = t_now - t_prev;
         C.sweep++;
         C.sweep_ns_last = t_now - t_prev;
         C.sweep_ns_sum += t_now - t_prev;

@@ -17,6 +17,8 @@ LQ_MIXED = 1
 LQ_MIXED_DW = 2
 LQ_SWAP_UNIFORM = 0
 LQ_SWAP_NEIGHBOUR = 1
+LQ_CHECKERBOARD = 0
+LQ_EXACT = 1
 LQ_NOBS = 9
 OBS_NAMES = ["sign", "n_up", "n_dn", "docc", "ekin", "szz_00", "szz_11", "szz_01", "s_par"]
 LQ_MAX_PARTICLES = 512
@@ -35,7 +37,7 @@ EXPORTS = [
     "lq_sim_device_bytes", "lq_sim_destroy", "lq_sim_measure", "lq_sim_check_drift", "lq_server_create",
     "lq_server_submit",
     "lq_server_poll", "lq_server_stats", "lq_server_set_tick_target", "lq_server_destroy", "lq_sweep_noalloc",
-    "lq_device_fp64_rate",
+    "lq_device_fp64_rate", "lq_test_quotient", "lq_request_footprint",
     "lq_last_error", "lq_version",
 ]
 
@@ -49,7 +51,7 @@ class LqError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("U", C.c_double), ("beta", C.c_double), ("dtau", C.c_double), ("n_up", C.c_int32),
                 ("n_dn", C.c_int32), ("n_stab", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64),
-                ("swap_mode", C.c_int32), ("left_swaps", C.c_int32)]
+                ("swap_mode", C.c_int32), ("left_swaps", C.c_int32), ("kinetic", C.c_int32)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -64,7 +66,8 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_records", C.c_int32), ("obs_mean", C.c_double * 9),
                 ("obs_err", C.c_double * 9), ("log_weight", C.c_double), ("sign", C.c_int32),
                 ("counts", C.c_int64 * 4), ("queue_ms", C.c_double), ("total_ms", C.c_double),
-                ("sweep_ms_mean", C.c_double)]
+                ("sweep_ms_mean", C.c_double), ("wall_ms_per_sweep", C.c_double), ("active_at_admit", C.c_int32),
+                ("waited_for_memory", C.c_int32)]
 
 
 class ServerStats(C.Structure):
@@ -72,7 +75,8 @@ class ServerStats(C.Structure):
                 ("p99_tick_ms", C.c_double), ("updates_per_s", C.c_double), ("busy_s", C.c_double),
                 ("wall_s", C.c_double), ("admit_s", C.c_double), ("retire_s", C.c_double), ("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
                 ("rejected", C.c_int64), ("active", C.c_int64), ("queued", C.c_int64), ("ticks", C.c_int64),
-                ("hbm_in_use", C.c_size_t)]
+                ("hbm_in_use", C.c_size_t), ("p50_wall_sweep_ms", C.c_double), ("p99_wall_sweep_ms", C.c_double),
+                ("sweeps", C.c_int64)]
 
 
 class Allocator(C.Structure):
@@ -141,6 +145,8 @@ def load(build_if_missing=True):
         "lq_server_set_tick_target": [P, dbl],
         "lq_server_destroy": [P],
         "lq_device_fp64_rate": [dbl, pdbl, pdbl],
+        "lq_test_quotient": [i32, pdbl, pdbl, pdbl, pdbl],
+        "lq_request_footprint": [P, C.POINTER(Params), C.POINTER(C.c_size_t)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -285,6 +291,19 @@ def device_fp64_rate(ms=200.0):
     cyc = np.zeros(3)
     _check(_lib.lq_device_fp64_rate(float(ms), C.byref(t), _p(cyc, C.c_double)))
     return t.value, dict(dfma_1lane=float(cyc[0]), dfma_32lanes=float(cyc[1]), ffma_32lanes=float(cyc[2]))
+
+
+def flip_quotient(d, r):
+    """The flip loop's FP64 quotient d/r and the IEEE quotient, evaluated on
+    the device (lq_test_quotient)."""
+    load()
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    q = np.zeros_like(d)
+    qi = np.zeros_like(d)
+    _check(_lib.lq_test_quotient(len(d), _p(d, C.c_double), _p(r, C.c_double), _p(q, C.c_double),
+                                 _p(qi, C.c_double)))
+    return q, qi
 
 
 def _torch_allocator():
@@ -485,7 +504,8 @@ class Sim:
 def _params_struct(p):
     return Params(float(p["U"]), float(p["beta"]), float(p["dtau"]), int(p["n_up"]), int(p["n_dn"]),
                   int(p["n_stab"]), int(p.get("precision", LQ_FP64)), int(p.get("seed", 0)) & (2**64 - 1),
-                  int(p.get("swap_mode", LQ_SWAP_UNIFORM)), int(p.get("left_swaps", 0)))
+                  int(p.get("swap_mode", LQ_SWAP_UNIFORM)), int(p.get("left_swaps", 0)),
+                  int(p.get("kinetic", LQ_CHECKERBOARD)))
 
 
 class Server:
@@ -515,7 +535,17 @@ class Server:
         return dict(status=r.status, n_records=r.n_records, obs_mean=np.array(r.obs_mean[:]),
                     obs_err=np.array(r.obs_err[:]), log_weight=r.log_weight, sign=r.sign,
                     counts=np.array(r.counts[:]), queue_ms=r.queue_ms, total_ms=r.total_ms,
-                    sweep_ms_mean=r.sweep_ms_mean)
+                    sweep_ms_mean=r.sweep_ms_mean, wall_ms_per_sweep=r.wall_ms_per_sweep,
+                    active_at_admit=r.active_at_admit, waited_for_memory=r.waited_for_memory)
+
+    @staticmethod
+    def footprint(lattice, params):
+        """Device bytes a request holds while admitted (lq_request_footprint)."""
+        load()
+        b = C.c_size_t()
+        p = _params_struct(params)
+        _check(_lib.lq_request_footprint(lattice.h, C.byref(p), C.byref(b)))
+        return b.value
 
     def set_tick_target(self, ms):
         _check(_lib.lq_server_set_tick_target(self.h, float(ms)))

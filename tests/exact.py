@@ -51,6 +51,15 @@ def dense_BK(lat, dtau):
     return B
 
 
+def exact_BK_eigh(lat, dtau):
+    """e^{-dtau K} from the eigendecomposition of the dense K (V diag(e^{-dtau
+    k}) V^T): independent of the Pade approximant behind scipy's expm."""
+    from oracle.lattices import dense_K
+
+    k, V = np.linalg.eigh(dense_K(lat))
+    return (V * np.exp(-dtau * k)) @ V.T
+
+
 def hs_lambda(U, dtau):
     return float(np.arccosh(np.exp(dtau * abs(U) / 2.0)))
 
@@ -67,9 +76,11 @@ def dense_B(lat, U, dtau, s, spin, BK=None):
     return B
 
 
-def log_weight(lat, U, dtau, s, occ_up, occ_dn):
-    """log|W| and sign of W = prod_sigma det[P^T B_sigma P] (times e^{-lambda sum s} for U < 0)."""
-    BK = dense_BK(lat, dtau)
+def log_weight(lat, U, dtau, s, occ_up, occ_dn, BK=None):
+    """log|W| and sign of W = prod_sigma det[P^T B_sigma P] (times e^{-lambda sum s} for U < 0);
+    BK: the kinetic propagator (default: the checkerboard product)."""
+    if BK is None:
+        BK = dense_BK(lat, dtau)
     lw, sg = 0.0, 1.0
     for spin, occ in ((0, occ_up), (1, occ_dn)):
         B = dense_B(lat, U, dtau, s, spin, BK)
@@ -165,13 +176,14 @@ def hop(states, N, i, j):
 class TrotterED:
     """Trotterized canonical ensemble on the (N_up, N_dn) sector."""
 
-    def __init__(self, lat, U, dtau, L, n_up, n_dn):
+    def __init__(self, lat, U, dtau, L, n_up, n_dn, BK=None):
         self.lat = lat
         N = lat["N"]
         self.N = N
         self.bu = basis(N, n_up)
         self.bd = basis(N, n_dn)
-        BK = dense_BK(lat, dtau)
+        if BK is None:
+            BK = dense_BK(lat, dtau)
         Cu = compound(BK, self.bu)
         Cd = compound(BK, self.bd)
         self.nu = np.array([[1.0 if i in S else 0.0 for i in range(N)] for S in self.bu]).reshape(len(self.bu), N)

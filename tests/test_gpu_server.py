@@ -152,3 +152,47 @@ def test_large_request_alone_and_in_mix(lq):
     assert ra["status"] == 0 and rb["status"] == 0 and all(r["status"] == 0 for r in res.values())
     assert np.array_equal(ra["counts"], rb["counts"])
     assert np.max(np.abs(ra["obs_mean"] - rb["obs_mean"])) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_request_admitted_mid_run_after_memory_frees(lq, prec):
+    """Continuous batching: a long request A and a medium one B are on the
+    device when the tested request C arrives.  The budget holds A with either
+    B or C but not all three, so C waits at the head of the queue until B
+    retires, then runs beside A.  C's result equals the same request run
+    alone (FP64 1e-10, LQ_MIXED 1e-5; the kernels draw counter-based random
+    numbers, so identical in practice)."""
+    la, lb, lc = lq.Lattice.square(8, 8), lq.Lattice.square(6, 6), lq.Lattice.square(4, 4)
+    pa = dict(U=4.0, beta=2.0, dtau=0.1, n_up=4, n_dn=4, n_stab=5, seed=31, precision=prec)
+    pb = dict(U=-2.0, beta=2.0, dtau=0.1, n_up=6, n_dn=6, n_stab=5, seed=32, precision=prec)
+    pc = dict(U=4.0, beta=1.0, dtau=0.1, n_up=3, n_dn=2, n_stab=4, seed=21, precision=prec)
+    fa, fb, fc = (lq.Server.footprint(l, p) for l, p in ((la, pa), (lb, pb), (lc, pc)))
+    budget = fa + max(fb, fc)
+    assert fa + fb + fc > budget
+    alone = lq.Server(hbm_budget=1 << 30, precision=prec)
+    rid = alone.submit(lc, pc, 8, chain_id=77)
+    ref = wait(alone, [rid])[rid]
+    alone.close()
+
+    srv = lq.Server(hbm_budget=budget, precision=prec)
+    ida = srv.submit(la, pa, 600, chain_id=1)
+    idb = srv.submit(lb, pb, 150, chain_id=2)
+    t0 = time.time()
+    while srv.stats()["active"] < 2:
+        assert time.time() - t0 < 60, "A and B were not both admitted"
+        time.sleep(0.001)
+    assert srv.poll(idb) is None  # B still runs when C arrives
+    idc = srv.submit(lc, pc, 8, chain_id=77)
+    rc = wait(srv, [idc], timeout=300)[idc]
+    a_running = srv.poll(ida) is None  # A outlives C
+    rest = wait(srv, [ida, idb], timeout=300)
+    st = srv.stats()
+    srv.close()
+    assert rc["status"] == 0 and all(r["status"] == 0 for r in rest.values())
+    assert rc["waited_for_memory"] == 1 and rc["active_at_admit"] >= 1 and a_running
+    assert rc["queue_ms"] > 0 and rc["wall_ms_per_sweep"] > 0
+    assert np.array_equal(ref["counts"], rc["counts"]) and ref["n_records"] == rc["n_records"] == 8
+    tol = 1e-10 if prec == 0 else 1e-5
+    assert np.max(np.abs(ref["obs_mean"] - rc["obs_mean"])) < tol
+    assert ref["sign"] == rc["sign"] and abs(ref["log_weight"] - rc["log_weight"]) < tol * max(1, abs(ref["log_weight"]))
+    assert st["sweeps"] == 600 + 150 + 8 and st["p99_wall_sweep_ms"] >= st["p50_wall_sweep_ms"] > 0

@@ -27,6 +27,7 @@ CASES = {
                                    dict(U=4.0, beta=0.8, dtau=0.1, n_up=3, n_dn=2, n_stab=4, swap_mode=1)),
     "square4x4_left_swaps": (("square", 4, 4), dict(U=4.0, beta=1.0, dtau=0.1, n_up=3, n_dn=2, n_stab=4, left_swaps=1)),
     "gas32x32_one_chain": (("square", 32, 32), dict(U=4.0, beta=10.0, dtau=0.05, n_up=8, n_dn=8, n_stab=8)),
+    "flat6_exact_kinetic": (("flatband", 6), dict(U=2.0, beta=1.0, dtau=0.1, n_up=3, n_dn=2, n_stab=5, kinetic=1)),
 }
 
 
