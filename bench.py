@@ -463,6 +463,37 @@ def time_steps(torch, sim, steps, stream):
     return per
 
 
+def nsigma_scan(lq, torch, stream, sizes=(16, 32, 33, 48, 64, 96, 128, 192, 256, 384), cells=256, L_slices=40):
+    """Cost of a sweep against N_sigma: 152 flat-band chains (one per SM) of
+    `cells` cells (N = 2 cells, BCL t1 = t2 = t3 = t4 = 1, periodic), U = 2,
+    dtau = 0.05, L = L_slices, QR every 8, FP64; one untimed and one timed
+    sweep per N_sigma.  Reports microseconds per site and chain (the sweep
+    time over 2 L N sites) and the phase shares, with the swap removal and
+    addition sub-phases."""
+    out = []
+    for ns in sizes:
+        if ns > cells:
+            continue
+        lat = lq.Lattice.flatband(cells, 1.0, 1.0, 1.0, 1.0, True)
+        p = dict(U=2.0, beta=L_slices * 0.05, dtau=0.05, n_up=ns, n_dn=ns, n_stab=8, precision=0, seed=1)
+        n = 152
+        sim = lq.Sim([lat] * n, [p] * n, stream=stream.cuda_stream)
+        sim.init()
+        sim.sweep(1, measure=False)
+        sim.sync()
+        pr0 = sum(sim.profile(c) for c in range(n))
+        per = time_steps(torch, sim, 1, stream)
+        pr = sum(sim.profile(c) for c in range(n)) - pr0
+        tot = max(float(pr[:6].sum()), 1.0)
+        out.append(dict(n_sigma=ns, us_per_site=1e3 * per[0] / (2 * L_slices * lat.N),
+                        flips=round(float(pr[0]) / tot, 3), propagation=round(float(pr[1]) / tot, 3),
+                        qr=round(float(pr[2] + pr[3]) / tot, 3), swaps=round(float(pr[4]) / tot, 3),
+                        swap_removal=round(float(pr[6]) / tot, 3), swap_addition=round(float(pr[7]) / tot, 3)))
+        sim.close()
+    return dict(workload="152 BCL flat-band chains of %d cells (N = %d), U = 2, dtau = 0.05, L = %d, QR every 8, "
+                         "FP64, one sweep" % (cells, 2 * cells, L_slices), rows=out)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,6 +508,8 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-gas64", action="store_true", help="skip the 64x64 mixed-precision leg (512 chains)")
+    ap.add_argument("--nsigma-scan", action="store_true",
+                    help="only the cost-against-N_sigma study (flat-band chains, one sweep per N_sigma)")
     ap.add_argument("--serving-window", type=float, default=10.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=["gas32x32", "gas64x64"],
                     help="gas64x64: the 64x64 mixed-precision comparison (512 chains, ~10 s per sweep)")
@@ -500,7 +533,7 @@ def main():
 
     # the CPU baseline runs first, in spawned processes, before any GPU work
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.nsigma_scan:
         cpu = cpu_baseline(spec, n_chains)
 
     import torch
@@ -514,6 +547,9 @@ def main():
     import paper_2601_08552_gb300 as lq
 
     stream = torch.cuda.current_stream()
+    if args.nsigma_scan:
+        print(json.dumps(dict(study="cost against N_sigma", **nsigma_scan(lq, torch, stream))), flush=True)
+        return
     lat = lq.Lattice.square(spec["lattice"][1], spec["lattice"][2])
     N = lat.N
     L = round(spec["beta"] / spec["dtau"])

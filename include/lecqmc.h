@@ -354,6 +354,46 @@ lq_status lq_server_set_tick_target(lq_server* srv, double ms);
 /* Finishes every admitted request, drops the queued ones, joins the thread. */
 lq_status lq_server_destroy(lq_server* srv);
 
+/* ---- constrained-path inner loop (SM Sec. VI) ------------------------------
+ * For the Fock state eta given by its occupied sites (host arrays of n_up and
+ * n_dn sites), walkers sample the Hubbard-Stratonovich fields slice by slice
+ * against the trial Psi_l^T = P^T e^{-(beta - tau_l) H_0} (everything after
+ * the fields of slice l, with the fields off).  At site i the overlap ratio
+ * of field value s is r(s) = prod_sigma [1 + Delta_sigma(s) Phi_i (Psi^T
+ * Phi)^{-1} Psi_i^T] (times e^{-lambda s} for U < 0); s is drawn with
+ * probability proportional to (1/2) max(0, r(s)) and the walker's weight
+ * takes the factor (1/2) sum_s max(0, r(s)); a walker at factor 0 has crossed
+ * the trial's node and is dropped.  Without truncation the mean weight is
+ * R(eta) = sum_s 2^{-LN} <eta|U(s)|eta> / <eta|e^{-beta H_0}|eta>, whose ratio
+ * between Fock states corrects the free-fermion weight W_T(eta) that a U = 0
+ * chain of lq_sim samples.  The paper fixes neither the field law nor the
+ * population control: this is the plainest choice whose mean weight is
+ * R(eta) when nothing is truncated.  params: the model (U, beta, dtau, n_up,
+ * n_dn, kinetic, seed = Philox key); precision must be LQ_FP64
+ * (LQ_EUNSUPPORTED otherwise); n_stab, swap_mode and left_swaps are not used.
+ * Both calls allocate their device memory and synchronize.  Errors:
+ * LQ_EINVAL (bad arguments or occupations), LQ_EUNSUPPORTED, LQ_ENOMEM,
+ * LQ_ECUDA. */
+/* n_walkers independent walkers; host_log_weights[k] = log of walker k's
+ * final weight (-inf when dropped), host_dropped (nullable) the number
+ * dropped.  Random numbers: Philox counter (k, sweep_word, 7<<24 | slice,
+ * site). */
+lq_status lq_cp_walk(const lq_lattice* lattice, const lq_params* params, const int32_t* host_occ_up,
+                     const int32_t* host_occ_dn, int32_t n_walkers, uint32_t sweep_word, double* host_log_weights,
+                     int32_t* host_dropped);
+/* A branching population of n_walkers: after every comb_every slices (0: only
+ * at the end) and after the last, the population's mean weight joins the
+ * estimate and n_walkers new walkers (weight 1) are drawn from the old ones
+ * by systematic (comb) resampling (Kitagawa 1996), probabilities
+ * proportional to the weights.  *host_log_estimate = log of the product of
+ * the mean weights (-inf if every walker was dropped), an unbiased estimate
+ * of R(eta) when nothing is truncated.  Random numbers: Philox counters (slot,
+ * run, 8<<24 | slice, site) for the fields and (run, 0xFFFFFFFD, 9<<24 | last
+ * slice of the interval, 0) for the comb's uniform. */
+lq_status lq_cp_population(const lq_lattice* lattice, const lq_params* params, const int32_t* host_occ_up,
+                           const int32_t* host_occ_dn, int32_t n_walkers, int32_t comb_every, uint32_t run,
+                           double* host_log_estimate);
+
 /* ---- allocation-free single-chain sweep ----------------------------------
  * No counterpart in the paper: this entry point exists for callers that
  * cannot allocate device memory themselves, for example a plug-in that must

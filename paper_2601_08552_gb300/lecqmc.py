@@ -37,7 +37,7 @@ EXPORTS = [
     "lq_sim_device_bytes", "lq_sim_destroy", "lq_sim_measure", "lq_sim_check_drift", "lq_server_create",
     "lq_server_submit",
     "lq_server_poll", "lq_server_stats", "lq_server_set_tick_target", "lq_server_destroy", "lq_sweep_noalloc",
-    "lq_device_fp64_rate", "lq_test_quotient", "lq_request_footprint",
+    "lq_device_fp64_rate", "lq_test_quotient", "lq_request_footprint", "lq_cp_walk", "lq_cp_population",
     "lq_last_error", "lq_version",
 ]
 
@@ -147,6 +147,8 @@ def load(build_if_missing=True):
         "lq_device_fp64_rate": [dbl, pdbl, pdbl],
         "lq_test_quotient": [i32, pdbl, pdbl, pdbl, pdbl],
         "lq_request_footprint": [P, C.POINTER(Params), C.POINTER(C.c_size_t)],
+        "lq_cp_walk": [P, C.POINTER(Params), pi32, pi32, i32, u32, pdbl, pi32],
+        "lq_cp_population": [P, C.POINTER(Params), pi32, pi32, i32, i32, u32, pdbl],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -304,6 +306,35 @@ def flip_quotient(d, r):
     _check(_lib.lq_test_quotient(len(d), _p(d, C.c_double), _p(r, C.c_double), _p(q, C.c_double),
                                  _p(qi, C.c_double)))
     return q, qi
+
+
+def cp_walk(lattice, params, occ_up, occ_dn, n_walkers, sweep_word=0):
+    """Constrained-path inner loop (lq_cp_walk): log of each walker's final
+    weight (-inf when dropped) and the number dropped."""
+    load()
+    p = _params_struct(dict(params, precision=LQ_FP64))
+    u = np.ascontiguousarray(occ_up, dtype=np.int32)
+    d = np.ascontiguousarray(occ_dn, dtype=np.int32)
+    lw = np.zeros(max(int(n_walkers), 1))
+    dropped = C.c_int32()
+    _check(_lib.lq_cp_walk(lattice.h, C.byref(p), _p(u, C.c_int32) if len(u) else None,
+                           _p(d, C.c_int32) if len(d) else None, int(n_walkers), int(sweep_word),
+                           _p(lw, C.c_double), C.byref(dropped)))
+    return lw[: int(n_walkers)].copy(), dropped.value
+
+
+def cp_population(lattice, params, occ_up, occ_dn, n_walkers, comb_every, run=0):
+    """Branching constrained-path population (lq_cp_population): log of its
+    estimate of R(eta)."""
+    load()
+    p = _params_struct(dict(params, precision=LQ_FP64))
+    u = np.ascontiguousarray(occ_up, dtype=np.int32)
+    d = np.ascontiguousarray(occ_dn, dtype=np.int32)
+    est = C.c_double()
+    _check(_lib.lq_cp_population(lattice.h, C.byref(p), _p(u, C.c_int32) if len(u) else None,
+                                 _p(d, C.c_int32) if len(d) else None, int(n_walkers), int(comb_every), int(run),
+                                 C.byref(est)))
+    return est.value
 
 
 def _torch_allocator():

@@ -136,10 +136,10 @@ def test_exact_with_checkerboard_chains_in_one_launch(lq):
 
 def test_exact_rejects_large_dtau_norm_and_bad_mode(lq):
     L = lq.Lattice.square(4, 4)
-    base = dict(U=4.0, beta=1.0, dtau=0.6, n_up=2, n_dn=2, n_stab=4)  # theta = 0.6 * 4 > 2
+    base = dict(U=4.0, beta=1.2, dtau=0.6, n_up=2, n_dn=2, n_stab=4)  # theta = 0.6 * 4 > 2
     with pytest.raises(lq.LqError) as e:
         lq.Sim([L], [dict(base, kinetic=lq.LQ_EXACT)])
     assert e.value.status == 8
     with pytest.raises(lq.LqError) as e:
-        lq.Sim([L], [dict(base, dtau=0.1, kinetic=7)])
+        lq.Sim([L], [dict(base, beta=1.2, dtau=0.1, kinetic=7)])
     assert e.value.status == 1
