@@ -436,6 +436,38 @@ def gas64_leg(lq, inputs, torch, stream, fp64_peak, warmup=1, steps=2, n_chains=
     return out
 
 
+def cp_leg(lq, inputs, torch, n_walkers=304, comb_every=8):
+    """The constrained-path inner loop on the headline lattice: for a seeded
+    Fock state of the 32x32 gas (N_up = N_dn = 8, U = +4, beta = 10, dtau =
+    0.05, L = 200), n_walkers independent walkers (lq_cp_walk) and a
+    branching population of the same size combed every comb_every slices
+    (lq_cp_population).  A walker samples one field per site and slice, so the
+    rate is field samples per second (walkers x L x N over the call's wall
+    time, set-up included)."""
+    from paper_2601_08552_gb300.lecqmc import cp_population, cp_walk
+
+    rng = np.random.default_rng(inputs.SEED0 + 7)
+    lat = lq.Lattice.square(32, 32)
+    up, dn = inputs.fock(rng, 1024, 8), inputs.fock(rng, 1024, 8)
+    p = dict(U=4.0, beta=10.0, dtau=0.05, n_up=8, n_dn=8, n_stab=8, seed=inputs.SEED0)
+    samples = n_walkers * 200 * 1024
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lw, dropped = cp_walk(lat, p, up, dn, n_walkers)
+    t_walk = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    est = cp_population(lat, p, up, dn, n_walkers, comb_every, run=1)
+    t_pop = time.perf_counter() - t0
+    alive = np.isfinite(lw)
+    return dict(walkers=n_walkers, field_samples_per_s=samples / t_walk, walk_s=t_walk, dropped=int(dropped),
+                log_mean_weight=float(np.log(np.mean(np.exp(lw[alive] - lw[alive].max()))) + lw[alive].max())
+                if alive.any() else None,
+                population_field_samples_per_s=samples / t_pop, population_s=t_pop, comb_every=comb_every,
+                population_log_estimate=est, precision="FP64",
+                workload="32x32 periodic square, U=+4, beta=10, dtau=0.05 (L=200), N_up=N_dn=8, one seeded Fock "
+                         "state; one CTA per walker")
+
+
 def observable_deviation(a, b):
     """Chain-mean observables of two runs from the same seeded states: the
     largest |difference| over the measured observables in units of the
@@ -494,6 +526,23 @@ def nsigma_scan(lq, torch, stream, sizes=(16, 32, 33, 48, 64, 96, 128, 192, 256,
                          "FP64, one sweep" % (cells, 2 * cells, L_slices), rows=out)
 
 
+def gram_scan(lq, sizes=((1024, 16), (1024, 64), (4096, 16), (4096, 64), (4096, 128), (16384, 64)), n_panels=304):
+    """The sweep's Gram contraction W = A^T B of two N x m panels, one per CTA
+    (304 CTAs: two per SM, as the sweep runs), on the FP64 CUDA cores, the
+    FP64 tensor cores (DMMA), FP32 panels with FP64 CUDA-core accumulation,
+    and FP32 panels on the TF32 tensor cores with the three-product split."""
+    from paper_2601_08552_gb300.lecqmc import GRAM_VARIANTS, probe_gram
+
+    rows = []
+    for N, m in sizes:
+        r = dict(N=N, m=m)
+        for v, name in enumerate(GRAM_VARIANTS):
+            us, err = probe_gram(N, m, v, n_panels)
+            r[name] = dict(us=us, gflops=2.0 * N * m * m * n_panels / (us * 1e-6) / 1e9, max_rel_err=err)
+        rows.append(r)
+    return dict(panels_per_launch=n_panels, rows=rows)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,6 +557,10 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-gas64", action="store_true", help="skip the 64x64 mixed-precision leg (512 chains)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the headline FP64 leg and its e2e (small profiling cases)")
+    ap.add_argument("--gram-scan", action="store_true",
+                    help="only the Gram study: CUDA cores against tensor cores (DMMA, 3xTF32)")
     ap.add_argument("--nsigma-scan", action="store_true",
                     help="only the cost-against-N_sigma study (flat-band chains, one sweep per N_sigma)")
     ap.add_argument("--serving-window", type=float, default=10.0)
@@ -516,6 +569,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.headline_only:
+        args.no_mixed = args.no_serving = args.no_uneven = args.no_gas64 = True
 
     from paper_2601_08552_gb300 import inputs
 
@@ -533,7 +588,7 @@ def main():
 
     # the CPU baseline runs first, in spawned processes, before any GPU work
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.nsigma_scan:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.nsigma_scan or args.gram_scan):
         cpu = cpu_baseline(spec, n_chains)
 
     import torch
@@ -549,6 +604,9 @@ def main():
     stream = torch.cuda.current_stream()
     if args.nsigma_scan:
         print(json.dumps(dict(study="cost against N_sigma", **nsigma_scan(lq, torch, stream))), flush=True)
+        return
+    if args.gram_scan:
+        print(json.dumps(dict(study="Gram contractions: CUDA cores and tensor cores", **gram_scan(lq))), flush=True)
         return
     lat = lq.Lattice.square(spec["lattice"][1], spec["lattice"][2])
     N = lat.N
@@ -666,7 +724,7 @@ def main():
 
     # the second run of the 32x32 gas: attractive U = -4 (charge-channel fields)
     attractive = None
-    if args.workload + "_attractive" in inputs.WORKLOADS:
+    if not args.headline_only and args.workload + "_attractive" in inputs.WORKLOADS:
         wa = inputs.WORKLOADS[args.workload + "_attractive"]
         spa = {k: wa[k] for k in ("lattice", "U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
         asim, aper, atotal, _, astat, aphases = run(0, spa)
@@ -683,7 +741,7 @@ def main():
 
     # nearest-neighbour Fock-swap proposals on the same workload (FP64)
     neighbour = None
-    if args.workload == WORKLOAD:
+    if not args.headline_only and args.workload == WORKLOAD:
         spn = dict(spec, swap_mode=1)
         nsim, nper, ntotal, _, nstat, nphases = run(0, spn)
         neighbour = dict(value=world * upd_per_step * args.steps / (ntotal * 1e-3), unit=UNIT,
@@ -697,7 +755,7 @@ def main():
     # a second swap phase per sweep at tau = 0 on the left chain (FP64): twice
     # the Fock-swap attempts, at the cost of one more swap phase
     left = None
-    if args.workload == WORKLOAD:
+    if not args.headline_only and args.workload == WORKLOAD:
         spl = dict(spec, left_swaps=1)
         lsim, lper, ltotal, _, lstat, lphases = run(0, spl)
         left = dict(value=world * upd_per_step * args.steps / (ltotal * 1e-3), unit=UNIT,
@@ -708,6 +766,10 @@ def main():
                     swaps="N_up + N_dn attempts after the up pass (tau = beta, right chain) and again after the "
                           "down pass (tau = 0, left chain)", precision="FP64")
         lsim.close()
+
+    cp = None
+    if not args.headline_only and args.workload == WORKLOAD:
+        cp = cp_leg(lq, inputs, torch)
 
     gas64 = None
     if not args.no_gas64 and args.workload == WORKLOAD:
@@ -739,7 +801,7 @@ def main():
                     swap_accept=float(dstat[3] / max(dstat[2], 1)), phase_cycle_share=phases,
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
                     reduced_precision=mixed, attractive=attractive, neighbour_swaps=neighbour, left_swaps=left,
-                    uneven_flatband=uneven, gas64x64=gas64,
+                    uneven_flatband=uneven, gas64x64=gas64, constrained_path=cp,
                     serving=serving)
         print(json.dumps(line), flush=True)
     if dist is not None:

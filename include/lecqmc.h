@@ -440,12 +440,30 @@ lq_status lq_sweep_noalloc(const lq_lattice* lattice, const lq_params* params, u
  * reported against is the device's FP64 FMA rate.  This measures it on the
  * current device: a kernel of independent FMA chains on every SM, grown until
  * one launch takes about `ms` milliseconds and timed with CUDA events, gives
- * *host_tflops (2 flops per FMA).  host_cycles3 (nullable, 3 doubles) receives
+ * *host_tflops (2 flops per FMA).  host_cycles4 (nullable, 4 doubles) receives
  * the sub-partition cycles of one FP64 FMA warp instruction with 1 and with 32
- * active lanes and of one FP32 FMA warp instruction (one warp, clock64).
+ * active lanes (eight independent chains), of one FP32 FMA warp instruction,
+ * and the latency of one FP64 FMA that depends on the previous one (one warp,
+ * clock64).
  * Allocates and frees a small device buffer; synchronous.
  * Errors: LQ_EINVAL (ms outside (0, 60000] or a null output), LQ_ECUDA. */
-lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles3);
+lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles4);
+/* Gram probe (build-side, no counterpart in the paper): the sweep's dense
+ * contractions are Grams W = A^T B of two N x m panels (the block Green's
+ * function and the CholeskyQR2 Grams).  This times one Gram per CTA for
+ * n_panels pairs of panels (the layout of the sweep: a CTA per chain) in one
+ * of four forms: 0 the sweep's FP64 CUDA-core routine on FP64 panels, 1 the
+ * FP64 tensor cores (DMMA, mma.sync m8n8k4) on FP64 panels, 2 the sweep's
+ * CUDA-core routine on FP32 panels with FP64 accumulation (LQ_MIXED), 3 the
+ * TF32 tensor cores with each FP32 operand split in two TF32 parts (three
+ * products, FP32 accumulation) on FP32 panels.  *host_us = microseconds per
+ * launch of n_panels Grams (CUDA events, mean of 5 after a warm-up);
+ * *host_max_rel_err = the largest |W - W_ref| over the Gram's largest |entry|
+ * against the FP64 CUDA-core Gram of the same values.  N >= 8, m a multiple
+ * of 16 up to 128.  Allocates device memory; synchronous.  Errors:
+ * LQ_EINVAL, LQ_ECUDA. */
+lq_status lq_probe_gram(int32_t N, int32_t m, int32_t variant, int32_t n_panels, double* host_us,
+                        double* host_max_rel_err);
 /* Test hook (no counterpart in the paper): the field-flip loop divides by
  * 1 + Delta G_tt with a hardware reciprocal seed and one third-order
  * Newton-Raphson step instead of the IEEE division sequence.  This evaluates

@@ -15,7 +15,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblecqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lq_sweep_d_small.cu", "lq_sweep_f_small.cu", "lq_sweep_d_big.cu", "lq_sweep_f_big.cu", "lq_kernels.cu",
-           "lq_api.cpp", "lq_noalloc.cu", "lq_server.cpp", "lq_probe.cu", "lq_cp.cu"]
+           "lq_api.cpp", "lq_noalloc.cu", "lq_server.cpp", "lq_probe.cu", "lq_cp.cu",
+           "lq_gram_probe.cu"]
 
 
 def _nvcc():

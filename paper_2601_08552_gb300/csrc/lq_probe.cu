@@ -48,6 +48,34 @@ __global__ void fma_issue_kernel(T* out, long long* cyc, int active, T a, T b) {
   if (lane == 0) *cyc = t1 - t0;
 }
 
+// Latency of a dependent FP64 FMA: one lane, one chain of ITERS steps.
+__global__ void fma_latency_kernel(double* out, long long* cyc, double a, double b) {
+  double x = threadIdx.x;
+  __syncwarp();
+  const long long t0 = clock64();
+  if (threadIdx.x == 0)
+    for (int it = 0; it < kIters; ++it) x = fma(x, a, b);
+  __syncwarp();
+  const long long t1 = clock64();
+  out[threadIdx.x] = x;
+  if (threadIdx.x == 0) *cyc = t1 - t0;
+}
+
+cudaError_t latency_cycles(void* scratch, double* out) {
+  double* o = (double*)scratch;
+  long long* cyc = (long long*)((char*)scratch + 32 * sizeof(double));
+  long long h = 0;
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+    fma_latency_kernel<<<1, 32>>>(o, cyc, 0.999, 0.001);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, cyc, sizeof(h), cudaMemcpyDeviceToHost);
+  *out = (double)h / kIters;
+  return e;
+}
+
 template <class T>
 cudaError_t issue_cycles(void* scratch, int active, double* out) {
   T* o = (T*)scratch;
@@ -70,7 +98,7 @@ lq_status probe_fail(cudaError_t e, const char* where) {
 
 }  // namespace
 
-extern "C" lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles3) {
+extern "C" lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles4) {
   if (!(ms > 0) || ms > 60000 || !host_tflops) return lq_internal_fail(LQ_EINVAL, "bad arguments to lq_device_fp64_rate");
   int dev = 0, sms = 1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -101,10 +129,11 @@ extern "C" lq_status lq_device_fp64_rate(double ms, double* host_tflops, double*
   }
   if (e == cudaSuccess && t > 0.f)
     *host_tflops = 2.0 * 8.0 * (double)iters * threads * blocks / (t * 1e-3) / 1e12;
-  if (e == cudaSuccess && host_cycles3) {
-    e = issue_cycles<double>(out, 1, &host_cycles3[0]);
-    if (e == cudaSuccess) e = issue_cycles<double>(out, 32, &host_cycles3[1]);
-    if (e == cudaSuccess) e = issue_cycles<float>(out, 32, &host_cycles3[2]);
+  if (e == cudaSuccess && host_cycles4) {
+    e = issue_cycles<double>(out, 1, &host_cycles4[0]);
+    if (e == cudaSuccess) e = issue_cycles<double>(out, 32, &host_cycles4[1]);
+    if (e == cudaSuccess) e = issue_cycles<float>(out, 32, &host_cycles4[2]);
+    if (e == cudaSuccess) e = latency_cycles(out, &host_cycles4[3]);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

