@@ -648,6 +648,9 @@ def main():
         tot = max(float(pr[:6].sum()), 1.0)
         phases = {k: round(float(pr[i]) / tot, 4) for i, k in
                   enumerate(["flips", "propagation", "qr", "block_inverse", "swaps", "measure"])}
+        if pr[8:12].sum() > 0:  # parts of the flips (paths of up to 16 particles per spin)
+            phases.update({k: round(float(pr[8 + i]) / tot, 4) for i, k in
+                           enumerate(["flip_staging", "flip_xy_products", "flip_serial_chain", "flip_update_T"])})
         # per-chain means of the measured observables (warm-up and timed sweeps)
         if sp is spec:
             run.obs[prec] = np.stack([sim.records(c).mean(axis=0) for c in range(n_chains)])

@@ -258,8 +258,11 @@ lq_status lq_sim_stats(lq_sim* sim, int32_t chain, int64_t* host_counts4);
  * slice propagation, QR restabilization, block-start Gram and inverse,
  * particle-hole swaps, measurement; then two parts of the swap cycles: the
  * removal (Givens rotations, M^-1, downdate, rotated Q panels) and the
- * addition (vector propagation and Gram-Schmidt) (host array of 8). */
-lq_status lq_sim_profile(lq_sim* sim, int32_t chain, int64_t* host_cycles8);
+ * addition (vector propagation and Gram-Schmidt); then four parts of the flip
+ * cycles of chains with at most 16 particles per spin: row staging and
+ * write-back, the window's x/y products, the serial per-site chain (with the
+ * window block), the recurrences and the update of T (host array of 12). */
+lq_status lq_sim_profile(lq_sim* sim, int32_t chain, int64_t* host_cycles12);
 /* Test hook: panel j of the right (side 0) or left (side 1) chain of a spin,
  * as FP64 host arrays Q (N x N_sigma) and V (N_sigma x N_sigma, nullable). */
 lq_status lq_sim_chain_panel(lq_sim* sim, int32_t chain, int32_t side, int32_t spin, int32_t j, double* host_Q,
@@ -440,14 +443,16 @@ lq_status lq_sweep_noalloc(const lq_lattice* lattice, const lq_params* params, u
  * reported against is the device's FP64 FMA rate.  This measures it on the
  * current device: a kernel of independent FMA chains on every SM, grown until
  * one launch takes about `ms` milliseconds and timed with CUDA events, gives
- * *host_tflops (2 flops per FMA).  host_cycles4 (nullable, 4 doubles) receives
+ * *host_tflops (2 flops per FMA).  host_cycles9 (nullable, 9 doubles) receives
  * the sub-partition cycles of one FP64 FMA warp instruction with 1 and with 32
- * active lanes (eight independent chains), of one FP32 FMA warp instruction,
- * and the latency of one FP64 FMA that depends on the previous one (one warp,
- * clock64).
+ * active lanes (eight independent chains) and of one FP32 FMA warp
+ * instruction, then the latency in cycles of an instruction that depends on
+ * the previous one: FP64 FMA, FP64 multiply, the FP64 reciprocal seed
+ * rcp.approx.ftz.f64, an FP32 -> FP64 -> FP32 conversion pair, a 64-bit warp
+ * shuffle, a dependent shared-memory load (one warp, clock64).
  * Allocates and frees a small device buffer; synchronous.
  * Errors: LQ_EINVAL (ms outside (0, 60000] or a null output), LQ_ECUDA. */
-lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles4);
+lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles9);
 /* Gram probe (build-side, no counterpart in the paper): the sweep's dense
  * contractions are Grams W = A^T B of two N x m panels (the block Green's
  * function and the CholeskyQR2 Grams).  This times one Gram per CTA for

@@ -1047,7 +1047,7 @@ extern "C" lq_status lq_sim_profile(lq_sim* S, int32_t c, int64_t* out) {
   if (st != LQ_OK) return st;
   if (!out) return fail(LQ_EINVAL, "null output");
   if ((st = pull(S)) != LQ_OK) return st;
-  for (int k = 0; k < 8; ++k) out[k] = S->h[c].prof[k];
+  for (int k = 0; k < 12; ++k) out[k] = S->h[c].prof[k];
   return LQ_OK;
 }
 

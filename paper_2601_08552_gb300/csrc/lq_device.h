@@ -94,8 +94,11 @@ struct LqChainDev {
   int err;
   long long cnt[4];         // field attempts, field accepts, swap attempts, swap accepts
   double hook[8];           // test-hook outputs
-  long long prof[8];        // cycles per phase: flips, propagation, QR, block inverse, swaps, measurement;
-                            // then two parts of the swaps: removal (with Q streaming), addition
+  long long prof[12];       // cycles per phase: flips, propagation, QR, block inverse, swaps, measurement;
+                            // then two parts of the swaps: removal (with Q streaming), addition; then
+                            // four parts of the flips (paths of up to 16 particles per spin): row staging and
+                            // write-back, the window's x/y products, the serial chain (with the window
+                            // block), the recurrences and the update of T
   long long sweep_ns_last;  // wall time of the chain's most recent sweep (device global timer)
   long long sweep_ns_sum;   // summed wall time of its sweeps (the caller may reset it)
   long long sweep_ns_ring[LQ_SWEEP_RING];  // wall time of sweep k at [k % LQ_SWEEP_RING]

@@ -48,26 +48,59 @@ __global__ void fma_issue_kernel(T* out, long long* cyc, int active, T a, T b) {
   if (lane == 0) *cyc = t1 - t0;
 }
 
-// Latency of a dependent FP64 FMA: one lane, one chain of ITERS steps.
-__global__ void fma_latency_kernel(double* out, long long* cyc, double a, double b) {
-  double x = threadIdx.x;
+// Latency of one instruction that depends on the previous one: one warp, one
+// chain of kIters steps.  op 0: FP64 FMA, 1: FP64 multiply, 2: the FP64
+// reciprocal seed rcp.approx.ftz.f64, 3: an FP32 -> FP64 -> FP32 conversion
+// pair, 4: a 64-bit warp shuffle, 5: a shared-memory load whose address
+// depends on the previous load.
+__global__ void op_latency_kernel(int op, double* out, long long* cyc, double a, double b) {
+  __shared__ int ring[64];
+  ring[threadIdx.x] = (threadIdx.x + 1) & 31;
+  ring[threadIdx.x + 32] = 0;
+  double x = 0.5 + threadIdx.x * 1e-3;
+  float f = 0.5f + threadIdx.x * 1e-3f;
+  int k = threadIdx.x;
   __syncwarp();
   const long long t0 = clock64();
-  if (threadIdx.x == 0)
-    for (int it = 0; it < kIters; ++it) x = fma(x, a, b);
+  switch (op) {
+    case 0:
+      for (int it = 0; it < kIters; ++it) x = fma(x, a, b);
+      break;
+    case 1:
+      for (int it = 0; it < kIters; ++it) x = x * a;
+      break;
+    case 2:
+      for (int it = 0; it < kIters; ++it) asm volatile("rcp.approx.ftz.f64 %0, %0;" : "+d"(x));
+      break;
+    case 3:
+      for (int it = 0; it < kIters; ++it) {
+        double d;
+        asm volatile("cvt.f64.f32 %0, %1;" : "=d"(d) : "f"(f));
+        asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(f) : "d"(d));
+      }
+      x = f;
+      break;
+    case 4:
+      for (int it = 0; it < kIters; ++it) x = __shfl_xor_sync(0xffffffffu, x, 1);
+      break;
+    default:
+      for (int it = 0; it < kIters; ++it) k = ring[k];
+      x = k;
+      break;
+  }
   __syncwarp();
   const long long t1 = clock64();
   out[threadIdx.x] = x;
   if (threadIdx.x == 0) *cyc = t1 - t0;
 }
 
-cudaError_t latency_cycles(void* scratch, double* out) {
+cudaError_t latency_cycles(void* scratch, int op, double* out) {
   double* o = (double*)scratch;
   long long* cyc = (long long*)((char*)scratch + 32 * sizeof(double));
   long long h = 0;
   cudaError_t e = cudaSuccess;
   for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-    fma_latency_kernel<<<1, 32>>>(o, cyc, 0.999, 0.001);
+    op_latency_kernel<<<1, 32>>>(op, o, cyc, 0.999, 0.001);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
@@ -98,7 +131,7 @@ lq_status probe_fail(cudaError_t e, const char* where) {
 
 }  // namespace
 
-extern "C" lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles4) {
+extern "C" lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycles9) {
   if (!(ms > 0) || ms > 60000 || !host_tflops) return lq_internal_fail(LQ_EINVAL, "bad arguments to lq_device_fp64_rate");
   int dev = 0, sms = 1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -129,11 +162,11 @@ extern "C" lq_status lq_device_fp64_rate(double ms, double* host_tflops, double*
   }
   if (e == cudaSuccess && t > 0.f)
     *host_tflops = 2.0 * 8.0 * (double)iters * threads * blocks / (t * 1e-3) / 1e12;
-  if (e == cudaSuccess && host_cycles4) {
-    e = issue_cycles<double>(out, 1, &host_cycles4[0]);
-    if (e == cudaSuccess) e = issue_cycles<double>(out, 32, &host_cycles4[1]);
-    if (e == cudaSuccess) e = issue_cycles<float>(out, 32, &host_cycles4[2]);
-    if (e == cudaSuccess) e = latency_cycles(out, &host_cycles4[3]);
+  if (e == cudaSuccess && host_cycles9) {
+    e = issue_cycles<double>(out, 1, &host_cycles9[0]);
+    if (e == cudaSuccess) e = issue_cycles<double>(out, 32, &host_cycles9[1]);
+    if (e == cudaSuccess) e = issue_cycles<float>(out, 32, &host_cycles9[2]);
+    for (int op = 0; op < 6 && e == cudaSuccess; ++op) e = latency_cycles(out, op, &host_cycles9[3 + op]);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

@@ -1062,6 +1062,15 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   auto Gb = [&](int sg) { return Yb(sg) + K * MP; };
   auto cb = [&](int sg) { return Gb(sg) + K * KP; };
   auto CGb = [&](int sg) { return cb(sg) + K; };
+  // sub-phase cycles (thread 0): staging, window products, serial chain, recurrences and T
+  long long tsub = (TID == 0) ? clock64() : 0;
+  auto lap = [&](int k) {
+    if (TID == 0) {
+      const long long t = clock64();
+      C.prof[k] += t - tsub;
+      tsub = t;
+    }
+  };
   for (int i0 = 0; i0 < N; i0 += cs) {
     const int cn = min(cs, N - i0);
     for (int sg = 0; sg < 2; ++sg) {
@@ -1085,6 +1094,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       sf[ii] = C.s[(size_t)l * N + i0 + ii];
     }
     __syncthreads();
+    lap(8);
     int wsign = 1, nacc = 0, nbad = 0;  // kept by the leader's lane 0
     for (int t0 = 0; t0 < cn; t0 += K) {
       const int kw = min(K, cn - t0);
@@ -1113,6 +1123,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         }
       }
       __syncthreads();
+      lap(9);
       if (leader) {
         const int h = lane >> 4, hl = lane & 15;
         const int m = h ? m1 : m0;
@@ -1176,6 +1187,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         }
       }
       __syncthreads();
+      lap(10);
       // D: x_j -= c_t G[j][t] x_t and y_j -= c_t G[t][j] y_t (j > t), t ascending; then y_t <- c_t y_t.
       // Warp w < 4 takes spin w >> 1, x (even w) or y (odd w), element (j, b)
       if (warp < 4) {
@@ -1220,6 +1232,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         }
       }
       __syncthreads();
+      lap(11);
     }
     if (leader) {
       // product of the chunk's accepted ratios, lane-parallel
@@ -1256,6 +1269,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
     for (int ii = TID; ii < cn; ii += LQ_THREADS)
       if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
     __syncthreads();
+    lap(8);
   }
 }
 

@@ -288,15 +288,16 @@ def _check_noalloc_buffers(torch, lattice, params, dev_fields, dev_occ, n_sweeps
 
 def device_fp64_rate(ms=200.0):
     """Measured FP64 FMA throughput of the current device (lq_device_fp64_rate):
-    (TFLOP/s, {cycles of one FP64 FMA warp instruction with 1 and 32 active
-    lanes, of one FP32 FMA warp instruction, latency of a dependent FP64
-    FMA})."""
+    (TFLOP/s, {issue cycles of FP64 and FP32 FMA warp instructions, latencies
+    of dependent FP64 FMA, multiply, reciprocal seed, conversion pair, 64-bit
+    shuffle and shared-memory load})."""
     load()
     t = C.c_double()
-    cyc = np.zeros(4)
+    cyc = np.zeros(9)
     _check(_lib.lq_device_fp64_rate(float(ms), C.byref(t), _p(cyc, C.c_double)))
-    return t.value, dict(dfma_1lane=float(cyc[0]), dfma_32lanes=float(cyc[1]), ffma_32lanes=float(cyc[2]),
-                         dfma_dependent_latency=float(cyc[3]))
+    names = ["dfma_1lane", "dfma_32lanes", "ffma_32lanes", "latency_dfma", "latency_dmul", "latency_rcp64",
+             "latency_cvt_f32_f64_f32", "latency_shfl64", "latency_lds"]
+    return t.value, {k: float(v) for k, v in zip(names, cyc)}
 
 
 def flip_quotient(d, r):
@@ -522,8 +523,10 @@ class Sim:
         return out
 
     def profile(self, c):
-        """SM cycles per phase: flips, propagation, QR, block inverse, swaps, measurement."""
-        out = np.zeros(8, np.int64)
+        """SM cycles per phase: flips, propagation, QR, block inverse, swaps,
+        measurement; swap removal and addition; flip staging, window
+        products, serial chain, recurrences and T update."""
+        out = np.zeros(12, np.int64)
         _check(_lib.lq_sim_profile(self.h, c, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return out
 
