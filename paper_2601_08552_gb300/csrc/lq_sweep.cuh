@@ -1040,7 +1040,10 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   constexpr int K = 4, KP = K + 1;
   constexpr int NXY = 2 * 2 * K * MT;  // x and y outputs of both spins
   constexpr int NT = 2 * MT * MT;      // T elements of both spins
-  constexpr int GP = MT >= 16 ? 4 : 2; // partial sums of the m-long products
+  // one accumulator per m-long product: on GB300 a dependent FP64 FMA costs
+  // its sub-partition the same 64 cycles as an independent one, so partial
+  // sums would only add instructions
+  constexpr int GP = 1;
   const int N = C.N, MP = sm.MP;
   const int m0 = C.ns[0], m1 = C.ns[1];
   const size_t per_site = (size_t)4 * MP * sizeof(Row) + 8 + sizeof(U) + 4 + 4;
@@ -1063,7 +1066,8 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   auto cb = [&](int sg) { return Gb(sg) + K * KP; };
   auto CGb = [&](int sg) { return cb(sg) + K; };
   // sub-phase cycles (thread 0): staging, window products, serial chain, recurrences and T
-  long long tsub = (TID == 0) ? clock64() : 0;
+  __shared__ long long tsub;
+  if (TID == 0) tsub = clock64();
   auto lap = [&](int k) {
     if (TID == 0) {
       const long long t = clock64();
@@ -1125,64 +1129,72 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       __syncthreads();
       lap(9);
       if (leader) {
+        // lane 16 h + 4 u + v holds G[u][v] of spin h in a register for the
+        // whole window: every read of the serial chain is a shuffle
         const int h = lane >> 4, hl = lane & 15;
         const int m = h ? m1 : m0;
-        const int u = hl >> 2, v = hl & 3;
-        V* Gw = Gb(h);
-        V* cw = cb(h);
-        // B: G[u][v] = x_u . L~_v of this half's spin
-        {
+        const int u = hl >> 2, v = hl & 3, hb = lane & 16;
+        // B: G[u][v] = x_u . L~_v of this half's spin (one dependent chain:
+        // on GB300 a dependent FP64 FMA costs its sub-partition no more than
+        // an independent one)
+        V G = Ops::zero();
+        if (u < kw && v < kw) {
           const V* xr = Xb(h) + u * MP;
           const Row* lr = lrow + ((size_t)h * cs + t0 + v) * MP;
-          V acc[GP];
-#pragma unroll
-          for (int q = 0; q < GP; ++q) acc[q] = Ops::zero();
+          V acc = Ops::zero();
 #pragma unroll
           for (int b = 0; b < MT; ++b)
-            if (b < m) Ops::accT(acc[b % GP], xr[b], lr[b]);
-          V g = Ops::finish(acc[0]);
-#pragma unroll
-          for (int q = 1; q < GP; ++q) g = Ops::add(g, Ops::finish(acc[q]));
-          if (u < kw && v < kw) Gw[u * KP + v] = g;
+            if (b < m) Ops::accT(acc, xr[b], lr[b]);
+          G = Ops::finish(acc);
         }
-        __syncwarp();
-        // C: the serial chain of both spins
+        // C: the serial chain of both spins, sites t0 .. t0 + kw - 1
         const bool upd = m > 0 && C.lambda != 0.0;
         const int sp = C.charge ? 1 : (h == 0 ? 1 : -1);
         const V d_p = Ops::delta(C, true), d_m = Ops::delta(C, false);
         const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
-        for (int t = 0; t < kw; ++t) {
-          const int ii = t0 + t;
-          const int s = sf[ii];
-          const V d = (sp * s > 0) ? d_p : d_m;
-          const V g = m > 0 ? Gw[t * KP + t] : Ops::zero();
-          const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt of this half's spin
-          const V c = Ops::div(d, rs);       // used if accepted
-          const V ro = Ops::xor_(rs, 16);    // the other spin's factor
-          V r = h ? Ops::mul(ro, rs) : Ops::mul(rs, ro);  // (up factor) x (down factor) in both halves
-          if (C.charge) r = Ops::mul(r, s > 0 ? cf_p : cf_m);
-          bool neg, bad;
-          const bool acc = Ops::accept(r, uni[ii], &neg, &bad);
-          const bool flip = acc && upd;
-          if (hl == 0) cw[t] = flip ? c : Ops::zero();
-          if (flip && u > t && v > t && u < kw && v < kw)
-            Gw[u * KP + v] = Ops::fnma(Ops::mul(c, Gw[u * KP + t]), Gw[t * KP + v], Gw[u * KP + v]);
-          if (lane == 0) {
-            af[ii] = acc ? 1 : 0;
-            racc[ii] = Ops::pack(r);
-            nbad += bad;
-            if (acc) {
-              wsign = neg ? -wsign : wsign;
-              ++nacc;
-            }
+        V* cw = cb(h);  // c_t of this half's spin (0 when not flipped)
+        int sacc = 0, sbad = 0, sneg = 0;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+          if (t < kw) {
+            const int ii = t0 + t;
+            const int s = sf[ii];
+            const U uu = uni[ii];
+            const V d = (sp * s > 0) ? d_p : d_m;
+            // G[u][t] and G[t][v] are final for this step (rows and columns
+            // below t only change at later steps)
+            const V gut = Ops::from_lane(G, hb + 4 * u + t);
+            const V gtv = Ops::from_lane(G, hb + 4 * t + v);
+            const V g = m > 0 ? Ops::from_lane(G, hb + 5 * t) : Ops::zero();
+            const V w = Ops::mul(gut, gtv);   // G[u][t] G[t][v], independent of this site's decision
+            const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt of this half's spin
+            const V c = Ops::div(d, rs);       // used if accepted
+            const V ro = Ops::xor_(rs, 16);    // the other spin's factor
+            V r = h ? Ops::mul(ro, rs) : Ops::mul(rs, ro);  // (up factor) x (down factor) in both halves
+            if (C.charge) r = Ops::mul(r, s > 0 ? cf_p : cf_m);
+            bool neg, bad;
+            const bool acc = Ops::accept(r, uu, &neg, &bad);
+            const bool flip = acc && upd;
+            if (flip && u > t && v > t) G = Ops::fnma(c, w, G);
+            if (hl == 0) cw[t] = flip ? c : Ops::zero();
+            sacc |= acc << t;
+            sneg |= neg << t;
+            sbad |= bad << t;
+            if (lane == t) racc[ii] = Ops::pack(r);
           }
-          __syncwarp();
         }
+        if (lane < kw) af[t0 + lane] = (sacc >> lane) & 1;
+        if (lane == 0) {
+          nacc += __popc(sacc);
+          nbad += __popc(sbad);
+          if (__popc(sacc & sneg) & 1) wsign = -wsign;
+        }
+        __syncwarp();
         // c-scaled factors of the recurrences: CG[j][t] = c_t G[j][t] (j > t), CG[t][j] = c_t G[t][j]
         {
           V val = Ops::zero();
-          if (u > v && u < kw) val = Ops::mul(cw[v], Gw[u * KP + v]);
-          else if (u < v && v < kw) val = Ops::mul(cw[u], Gw[u * KP + v]);
+          if (u > v && u < kw) val = Ops::mul(cw[v], G);
+          else if (u < v && v < kw) val = Ops::mul(cw[u], G);
           CGb(h)[u * K + v] = val;
         }
       }
