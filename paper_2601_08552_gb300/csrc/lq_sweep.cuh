@@ -1165,7 +1165,9 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
             // below t only change at later steps)
             const V gut = Ops::from_lane(G, hb + 4 * u + t);
             const V gtv = Ops::from_lane(G, hb + 4 * t + v);
-            const V g = m > 0 ? Ops::from_lane(G, hb + 5 * t) : Ops::zero();
+            // every lane takes part in every shuffle (the halves' spins may differ in m)
+            const V gtt = Ops::from_lane(G, hb + 5 * t);
+            const V g = m > 0 ? gtt : Ops::zero();
             const V w = Ops::mul(gut, gtv);   // G[u][t] G[t][v], independent of this site's decision
             const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt of this half's spin
             const V c = Ops::div(d, rs);       // used if accepted
