@@ -129,3 +129,25 @@ def test_cp_rejects_reduced_precision_and_bad_occupations(lq):
 
     with pytest.raises(LqError):
         cp_walk(L, p, [0, 0], [2], 4)
+
+
+@pytest.mark.parametrize("U,up_dn", [(4.0, (1, 1)), (-3.0, (1, 1))])
+def test_two_stage_partition_ratio_is_exact(lq, U, up_dn):
+    """The outer stage (Fock states from the U = 0 chain, which samples the
+    free weight W_T) and the inner populations together estimate
+    e^{cL} Z_U / Z_0 of the Trotterized ED."""
+    import exact
+    from paper_2601_08552_gb300.constrained import partition_ratio
+
+    lat = lattices.chain(6)
+    beta, dtau = 0.8, 0.1
+    Lsl = int(round(beta / dtau))
+    nu, nd = up_dn
+    ne, N = nu + nd, lat["N"]
+    c = dtau * U * ne / 2.0 if U >= 0 else dtau * abs(U) * (N - ne) / 2.0
+    ref = np.exp(c * Lsl) * exact.TrotterED(lat, U, dtau, Lsl, nu, nd).Z / exact.TrotterED(lat, 0.0, dtau, Lsl, nu,
+                                                                                         nd).Z
+    params = dict(U=U, beta=beta, dtau=dtau, n_up=nu, n_dn=nd, n_stab=4, seed=17)
+    est = partition_ratio(lq.Lattice.chain(6), params, 400, n_walkers=8, comb_every=2, thin=2)
+    print(est["mean"], est["err"], ref)
+    assert abs(est["mean"] - ref) < 5 * est["err"] + 1e-12
