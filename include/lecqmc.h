@@ -211,9 +211,11 @@ lq_status lq_sim_sweep(lq_sim* sim, int32_t n_sweeps, int32_t measure);
  * paper).  A sweep runs one persistent launch per plan class: the chains with
  * at most 32 particles per spin, then the larger ones.  For each class this
  * times sweeps_per_candidate sweeps (without measurement) under each feasible
- * size of the shared-memory staging buffer, which sets the propagation's
- * column chunks, the flip loop's chunk of sites and the CTAs per SM, and keeps
- * the fastest for later sweeps.  The timed sweeps are ordinary sweeps of the
+ * pair of (size of the shared-memory staging buffer, threads per CTA), and
+ * keeps the fastest for later sweeps.  The staging size sets the
+ * propagation's column chunks and the flip loop's chunk of sites; with the
+ * threads per CTA (256, or 128 for the small class) it sets the CTAs, i.e.
+ * the chains, resident per SM.  The timed sweeps are ordinary sweeps of the
  * chains of that class (they advance its chains; use them as warm-up), so a
  * class's chains advance by sweeps_per_candidate times the number of
  * candidates tried.  Choices are cached per (precision, class, N_sigma, N,
@@ -221,6 +223,10 @@ lq_status lq_sim_sweep(lq_sim* sim, int32_t n_sweeps, int32_t measure);
  * cached choice is applied.  host_buf2 (nullable) receives the staging bytes
  * chosen for the two classes (0 for an empty class).  Synchronous. */
 lq_status lq_sim_autotune(lq_sim* sim, int32_t sweeps_per_candidate, int32_t* host_buf2);
+/* The launch of each plan class as it stands (after lq_sim_create or
+ * lq_sim_autotune): host_cfg8 = for the small then the large class, its
+ * chains, staging bytes, threads per CTA and grid (zeros for an empty class). */
+lq_status lq_sim_launch_config(const lq_sim* sim, int32_t* host_cfg8);
 /* One stateless batch call on host buffers: upload every chain's fields
  * (host_fields: chains concatenated, each L x N) and Fock state (host_occ:
  * each chain's n_up then n_dn sites), rebuild the QR chains, run n_sweeps

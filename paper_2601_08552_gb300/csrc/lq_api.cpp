@@ -298,7 +298,7 @@ struct lq_sim {
   // particles per spin (shared-memory plan), then the larger ones (global
   // workspace); d_order holds the small class first, each by decreasing cost
   struct PlanClass {
-    int n = 0, off = 0, M = 1, Nmax = 1, buf = 0, grid = 1, pcols = 1;
+    int n = 0, off = 0, M = 1, Nmax = 1, buf = 0, grid = 1, pcols = 1, threads = LQ_THREADS;
   } cls[2];
   char* ws = nullptr;            // global workspace of big plans (grid x per-CTA slab)
   size_t ws_bytes = 0;
@@ -754,10 +754,11 @@ extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) 
     const bool forked = e == cudaSuccess;
     if (e == cudaSuccess)
       e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + large.off, large.n, S->d_queue2, n_sweeps, measure,
-                           large.M, large.Nmax, large.buf, large.grid, S->st2, S->ws, S->ws_bytes);
+                           large.M, large.Nmax, large.buf, large.grid, S->st2, S->ws, S->ws_bytes, nullptr, 0,
+                           large.threads);
     if (e == cudaSuccess)
       e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + small.off, small.n, S->d_queue, n_sweeps, measure,
-                           small.M, small.Nmax, small.buf, small.grid, S->st, nullptr, 0);
+                           small.M, small.Nmax, small.buf, small.grid, S->st, nullptr, 0, nullptr, 0, small.threads);
     if (forked) {
       // join even after a failed launch, so that nothing later on the
       // caller's stream overtakes the second stream's work
@@ -771,7 +772,8 @@ extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) 
       const lq_sim::PlanClass& pc = S->cls[k];
       if (pc.n)
         e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + pc.off, pc.n, S->d_queue, n_sweeps, measure, pc.M,
-                             pc.Nmax, pc.buf, pc.grid, S->st, S->ws, S->ws_bytes);
+                             pc.Nmax, pc.buf, pc.grid, S->st, S->ws, S->ws_bytes, nullptr, 0,
+                             pc.threads);
     }
   }
   if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
@@ -787,7 +789,7 @@ extern "C" lq_status lq_sim_sweep(lq_sim* S, int32_t n_sweeps, int32_t measure) 
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;  // -> (staging bytes, threads)
 int chain_bucket(int n) {
   int b = 0;
   while ((1 << b) < n) ++b;
@@ -807,12 +809,12 @@ extern "C" lq_status lq_sim_autotune(lq_sim* S, int32_t sweeps_per_candidate, in
     if (!pc.n) continue;
     const auto key = std::make_tuple(S->prec, k, pc.M, pc.Nmax, chain_bucket(pc.n));
     const int need = lq::staging_min_bytes(pc.M, pc.Nmax, pc.pcols);
-    // a feasible (grid, fits) for a candidate buffer
-    auto feasible = [&](int buf, int* grid) {
+    // a feasible (grid, fits) for a candidate (staging buffer, threads per CTA)
+    auto feasible = [&](int buf, int threads, int* grid) {
       if (buf < need) return false;
       const size_t smem = lq::smem_bytes(pc.M, pc.Nmax, buf);
       if (smem > 227 * 1024) return false;
-      const int per_sm = lq::max_active_sweep_ctas(S->prec, pc.M, smem);
+      const int per_sm = lq::max_active_sweep_ctas(S->prec, pc.M, smem, threads);
       if (per_sm < 1) return false;
       *grid = std::min(pc.n, sms * per_sm);
       return (size_t)(*grid) * lq::workspace_bytes(pc.M, pc.Nmax, buf) <= S->ws_bytes;
@@ -821,53 +823,66 @@ extern "C" lq_status lq_sim_autotune(lq_sim* S, int32_t sweeps_per_candidate, in
       std::lock_guard<std::mutex> g(g_tune_mu);
       auto it = g_tune_cache.find(key);
       int grid = 0;
-      if (it != g_tune_cache.end() && feasible(it->second, &grid)) {
-        pc.buf = it->second;
+      if (it != g_tune_cache.end() && feasible(it->second.first, it->second.second, &grid)) {
+        pc.buf = it->second.first;
+        pc.threads = it->second.second;
         pc.grid = grid;
         if (host_buf2) host_buf2[k] = pc.buf;
         continue;
       }
     }
     if (sweeps_per_candidate == 0) continue;
-    std::vector<int> cand = {pc.buf, 32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024, 128 * 1024, 160 * 1024, 200 * 1024};
+    std::vector<int> cand = {pc.buf, 24 * 1024, 32 * 1024, 40 * 1024, 48 * 1024, 64 * 1024, 96 * 1024, 128 * 1024,
+                             160 * 1024, 200 * 1024};
     std::sort(cand.begin(), cand.end());
     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    // half-size CTAs (more chains per SM) for plans of at most LQ_NS_SMALL particles per spin
+    std::vector<int> tcand = {LQ_THREADS};
+    if (!(pc.M > LQ_NS_SMALL)) tcand.push_back(LQ_THREADS / 2);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best_ms = 0.f;
-    int best_buf = pc.buf, best_grid = pc.grid;
+    int best_buf = pc.buf, best_grid = pc.grid, best_threads = pc.threads;
     bool have = false;
-    for (int buf : cand) {
-      int grid = 0;
-      if (!feasible(buf, &grid)) continue;
-      cudaError_t e = cudaEventRecord(e0, S->st);
-      if (e == cudaSuccess)
-        e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + pc.off, pc.n, S->d_queue, sweeps_per_candidate, 0,
-                             pc.M, pc.Nmax, buf, grid, S->st, S->ws, S->ws_bytes);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, S->st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return cuda_fail(e, "autotune sweep");
-      }
-      if (!have || ms < best_ms) {
-        best_ms = ms;
-        best_buf = buf;
-        best_grid = grid;
-        have = true;
+    for (int threads : tcand) {
+      int last_grid = -1;
+      for (int buf : cand) {
+        int grid = 0;
+        if (!feasible(buf, threads, &grid)) continue;
+        // with half-size CTAs only the staging sizes that change the CTAs per SM are worth a sweep
+        if (threads != LQ_THREADS && grid == last_grid) continue;
+        last_grid = grid;
+        cudaError_t e = cudaEventRecord(e0, S->st);
+        if (e == cudaSuccess)
+          e = lq::launch_sweep(S->prec, S->d_chains, S->d_order + pc.off, pc.n, S->d_queue, sweeps_per_candidate, 0,
+                               pc.M, pc.Nmax, buf, grid, S->st, S->ws, S->ws_bytes, nullptr, 0, threads);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, S->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return cuda_fail(e, "autotune sweep");
+        }
+        if (!have || ms < best_ms) {
+          best_ms = ms;
+          best_buf = buf;
+          best_grid = grid;
+          best_threads = threads;
+          have = true;
+        }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     pc.buf = best_buf;
     pc.grid = best_grid;
+    pc.threads = best_threads;
     if (host_buf2) host_buf2[k] = pc.buf;
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune_cache[key] = pc.buf;
+    g_tune_cache[key] = std::make_pair(pc.buf, pc.threads);
   }
   return LQ_OK;
 }
@@ -914,6 +929,18 @@ extern "C" lq_status lq_sim_run_host(lq_sim* S, const int8_t* hf, const int32_t*
     fo += nf;
   }
   CK(cudaStreamSynchronize(S->st));
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sim_launch_config(const lq_sim* S, int32_t* host_cfg8) {
+  if (!S || !host_cfg8) return fail(LQ_EINVAL, "bad arguments to lq_sim_launch_config");
+  for (int k = 0; k < 2; ++k) {
+    const lq_sim::PlanClass& pc = S->cls[k];
+    host_cfg8[4 * k + 0] = pc.n;
+    host_cfg8[4 * k + 1] = pc.n ? pc.buf : 0;
+    host_cfg8[4 * k + 2] = pc.n ? pc.threads : 0;
+    host_cfg8[4 * k + 3] = pc.n ? pc.grid : 0;
+  }
   return LQ_OK;
 }
 

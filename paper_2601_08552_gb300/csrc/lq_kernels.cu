@@ -156,7 +156,7 @@ static cudaError_t bind_ws(SmemPlan& p, void* ws, size_t ws_bytes, int grid) {
 
 cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
                          int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st, void* ws,
-                         size_t ws_bytes, const int* caps, long long budget_ns) {
+                         size_t ws_bytes, const int* caps, long long budget_ns, int threads) {
   SmemPlan p = plan_smem(M, Nmax, buf_bytes);
   cudaError_t e = bind_ws(p, ws, ws_bytes, grid);
   if (e != cudaSuccess) return e;
@@ -164,13 +164,15 @@ cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_o
   if (e != cudaSuccess) return e;
   const void* fn = sweep_fn(prec, p.big);
   if ((e = set_attr<double>(fn, p.total)) != cudaSuccess) return e;
+  // big plans flip with four-warp groups per spin: always a full CTA
+  const int nt = (p.big || threads != LQ_THREADS / 2) ? LQ_THREADS : LQ_THREADS / 2;
   if (prec == 0 && !p.big)
-    return sweep_launch_d_small(grid, st, chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
+    return sweep_launch_d_small(grid, nt, st, chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
   if (prec == 0)
-    return sweep_launch_d_big(grid, st, chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
+    return sweep_launch_d_big(grid, nt, st, chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
   if (!p.big)
-    return sweep_launch_f_small(grid, st, chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
-  return sweep_launch_f_big(grid, st, chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
+    return sweep_launch_f_small(grid, nt, st, chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
+  return sweep_launch_f_big(grid, nt, st, chains, order, n_order, queue, n_sweeps, caps, budget_ns, do_measure, p);
 }
 
 cudaError_t launch_build(int prec, LqChainDev* chains, const int* order, int n_order, int M, int Nmax, int buf_bytes,
@@ -243,11 +245,13 @@ cudaError_t launch_quotient(const double* d, const double* r, int n, double* q_o
   return cudaGetLastError();
 }
 
-int max_active_sweep_ctas(int prec, int M, size_t smem) {
+int max_active_sweep_ctas(int prec, int M, size_t smem, int threads) {
   int n = 0;
-  const void* fn = sweep_fn(prec, M > LQ_NS_SMALL);
+  const bool big = M > LQ_NS_SMALL;
+  const void* fn = sweep_fn(prec, big);
+  const int nt = (big || threads != LQ_THREADS / 2) ? LQ_THREADS : LQ_THREADS / 2;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, LQ_THREADS, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, nt, smem) != cudaSuccess) return 0;
   return n;
 }
 }  // namespace lq

@@ -18,7 +18,8 @@ int staging_bytes(int M, int Nmax, int prop_cols = 1);
 int staging_min_bytes(int M, int Nmax, int prop_cols = 1);  // the smallest staging buffer a plan can run with
 cudaError_t launch_sweep(int prec, LqChainDev* chains, const int* order, int n_order, int* queue, int n_sweeps,
                          int do_measure, int M, int Nmax, int buf_bytes, int grid, cudaStream_t st, void* ws,
-                         size_t ws_bytes, const int* caps = nullptr, long long budget_ns = 0);
+                         size_t ws_bytes, const int* caps = nullptr, long long budget_ns = 0,
+                         int threads = LQ_THREADS);
 cudaError_t launch_build(int prec, LqChainDev* chains, const int* order, int n_order, int M, int Nmax, int buf_bytes,
                          int grid, cudaStream_t st, void* ws, size_t ws_bytes);
 cudaError_t launch_clear_records(LqChainDev* chains, int n, cudaStream_t st);
@@ -27,7 +28,9 @@ cudaError_t launch_field_ratio(int prec, LqChainDev* chains, int c, int l, int i
                                cudaStream_t st, void* ws, size_t ws_bytes);
 cudaError_t launch_swap_ratio(int prec, LqChainDev* chains, int c, int sg, int k, int j, int M, int Nmax,
                               int buf_bytes, cudaStream_t st, void* ws, size_t ws_bytes);
-int max_active_sweep_ctas(int prec, int M, size_t smem);
+// threads: LQ_THREADS, or LQ_THREADS / 2 for plans of at most LQ_NS_SMALL
+// particles per spin (anything else, and every big plan, runs LQ_THREADS)
+int max_active_sweep_ctas(int prec, int M, size_t smem, int threads = LQ_THREADS);
 // the flip loop's FP64 quotient d/r and the IEEE one, elementwise (device arrays of n)
 cudaError_t launch_quotient(const double* d, const double* r, int n, double* q_ours, double* q_ieee, cudaStream_t st);
 }  // namespace lq

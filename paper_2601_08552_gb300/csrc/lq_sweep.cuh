@@ -142,6 +142,10 @@ __device__ inline Smem carve(const SmemPlan& p, char* base) {
 }
 
 #define TID ((int)threadIdx.x)
+// threads of the running CTA: LQ_THREADS (256), or 128 for sweep launches of
+// plans with at most LQ_NS_SMALL particles per spin that the autotuner runs
+// four CTAs per SM
+#define NTHR ((int)blockDim.x)
 #define FULL 0xffffffffu
 
 // Device global timer in nanoseconds.
@@ -235,7 +239,7 @@ static __device__ double cta_sum(double v, Smem& sm) {
   if ((TID & 31) == 0) sm.red[TID >> 5] = v;
   __syncthreads();
   if (TID < 32) {
-    double t = (TID < LQ_THREADS / 32) ? sm.red[TID] : 0.0;
+    double t = (TID < NTHR / 32) ? sm.red[TID] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
     if (TID == 0) sm.red[40] = t;
@@ -348,7 +352,7 @@ __device__ void prop_exact(const LqChainDev& C, int sigma, R* dst, const S* src,
     const int tot = N * cw;
     R* y0 = buf;
     R* y1 = buf + tot;
-    for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+    for (int idx = TID; idx < tot; idx += NTHR) {
       const int i = idx / cw, a = idx - i * cw;
       R v = (R)src[(size_t)i * ld + c0 + a];
       if (spre) v *= (R)dfac(C, sigma, spre[i]);
@@ -357,7 +361,7 @@ __device__ void prop_exact(const LqChainDev& C, int sigma, R* dst, const S* src,
     __syncthreads();
     for (int k = lat.taylor_q; k >= 1; --k) {
       const R ck = (R)(lat.mdtau / (double)k);
-      for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+      for (int idx = TID; idx < tot; idx += NTHR) {
         const int i = idx / cw, a = idx - i * cw;
         R acc = (R)0;
         for (int p = ko[i]; p < ko[i + 1]; ++p) acc += kv[p] * y0[kc[p] * cw + a];
@@ -368,7 +372,7 @@ __device__ void prop_exact(const LqChainDev& C, int sigma, R* dst, const S* src,
       __syncthreads();
       R* t = y0; y0 = y1; y1 = t;
     }
-    for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+    for (int idx = TID; idx < tot; idx += NTHR) {
       const int i = idx / cw, a = idx - i * cw;
       R v = y0[idx];
       if (spost) v *= (R)dfac(C, sigma, spost[i]);
@@ -400,7 +404,7 @@ __device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m
   for (int c0 = 0; c0 < m; c0 += cmax) {
     const int cw = min(cmax, m - c0);
     const int tot = N * cw;
-    for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+    for (int idx = TID; idx < tot; idx += NTHR) {
       int i = idx / cw, a = idx - i * cw;
       R v = (R)src[(size_t)i * ld + c0 + a];
       if (spre) v *= (R)dfac(C, sigma, spre[i]);
@@ -412,7 +416,7 @@ __device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m
       for (int gg = 0; gg < lat.G; ++gg) {
         const int g = (op == 1) ? gg : lat.G - 1 - gg;
         const int b0 = lat.fam_off[g], work = (lat.fam_off[g + 1] - b0) * cw;
-        for (int idx = TID; idx < work; idx += LQ_THREADS) {
+        for (int idx = TID; idx < work; idx += NTHR) {
           int bb = idx / cw, a = idx - bb * cw;
           int b = b0 + bb;
           int i = lat.bond_i[b], j = lat.bond_j[b];
@@ -424,7 +428,7 @@ __device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m
         __syncthreads();
       }
     }
-    for (int idx = TID; idx < tot; idx += LQ_THREADS) {
+    for (int idx = TID; idx < tot; idx += NTHR) {
       int i = idx / cw, a = idx - i * cw;
       R v = buf[idx];
       if (op == 2 && ceps) v *= ceps[i];
@@ -442,11 +446,11 @@ __device__ void gram(const RA* A, int lda, int ma, const RB* B, int ldb, int mb,
                      const int* sub = nullptr, int mval = 0) {
   const int nout = ma * mb;
   if (nout > 0) {
-    int tpo = LQ_THREADS / nout;
+    int tpo = NTHR / nout;
     if (tpo > 32) tpo = 32;
     if (tpo < 1) tpo = 1;
     while (tpo & (tpo - 1)) tpo &= tpo - 1;  // power of two
-    const int per = LQ_THREADS / tpo;
+    const int per = NTHR / tpo;
     for (int o0 = 0; o0 < nout; o0 += per) {
       const int o = o0 + TID / tpo, part = TID % tpo;
       Acc acc = 0;
@@ -468,7 +472,7 @@ __device__ void gram(const RA* A, int lda, int ma, const RB* B, int ldb, int mb,
 // Returns log|det W| and its sign; a zero pivot sets LQ_ERR_SINGULAR.
 static __device__ void inverse(double* W, int ldw, double* T, int ldt, int m, Smem& sm, double* logabs, int* sgn) {
   double* fac = sm.vec + 9 * sm.M;
-  for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+  for (int idx = TID; idx < m * m; idx += NTHR) {
     int r = idx / m, c = idx - r * m;
     T[r * ldt + c] = (r == c) ? 1.0 : 0.0;
   }
@@ -494,7 +498,7 @@ static __device__ void inverse(double* W, int ldw, double* T, int ldt, int m, Sm
     if (sm.ip[1]) break;
     const int p = sm.ip[2];
     if (p != col) {
-      for (int c = TID; c < m; c += LQ_THREADS) {
+      for (int c = TID; c < m; c += NTHR) {
         double t = W[col * ldw + c]; W[col * ldw + c] = W[p * ldw + c]; W[p * ldw + c] = t;
         t = T[col * ldt + c]; T[col * ldt + c] = T[p * ldt + c]; T[p * ldt + c] = t;
       }
@@ -506,9 +510,9 @@ static __device__ void inverse(double* W, int ldw, double* T, int ldt, int m, Sm
       if (d < 0) sm.ip[0] = -sm.ip[0];
       sm.red[41] += log(fabs(d));
     }
-    for (int r = TID; r < m; r += LQ_THREADS) fac[r] = (r == col) ? 0.0 : W[r * ldw + col] / d;
+    for (int r = TID; r < m; r += NTHR) fac[r] = (r == col) ? 0.0 : W[r * ldw + col] / d;
     __syncthreads();
-    for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+    for (int idx = TID; idx < m * m; idx += NTHR) {
       int r = idx / m, c = idx - r * m;
       if (r != col) {
         T[r * ldt + c] -= fac[r] * T[col * ldt + c];
@@ -516,14 +520,14 @@ static __device__ void inverse(double* W, int ldw, double* T, int ldt, int m, Sm
       }
     }
     __syncthreads();
-    for (int c = TID; c < m; c += LQ_THREADS) {
+    for (int c = TID; c < m; c += NTHR) {
       T[col * ldt + c] /= d;
       if (c > col) W[col * ldw + c] /= d;
     }
     __syncthreads();
   }
   if (sm.ip[1]) {
-    for (int idx = TID; idx < m * m; idx += LQ_THREADS) T[(idx / m) * ldt + idx % m] = NAN;
+    for (int idx = TID; idx < m * m; idx += NTHR) T[(idx / m) * ldt + idx % m] = NAN;
     if (TID == 0) { sm.C->err |= LQ_ERR_SINGULAR; sm.red[41] = -INFINITY; sm.ip[0] = 0; }
   }
   __syncthreads();
@@ -541,10 +545,10 @@ static __device__ void cholesky(double* W, int ld, int m, Smem& sm) {
       W[k * ld + k] = sqrt(d);
     }
     __syncthreads();
-    for (int j = k + 1 + TID; j < m; j += LQ_THREADS) W[k * ld + j] /= W[k * ld + k];
+    for (int j = k + 1 + TID; j < m; j += NTHR) W[k * ld + j] /= W[k * ld + k];
     __syncthreads();
     const int rem = m - k - 1;
-    for (int idx = TID; idx < rem * rem; idx += LQ_THREADS) {
+    for (int idx = TID; idx < rem * rem; idx += NTHR) {
       int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
       if (j >= i) W[i * ld + j] -= W[k * ld + i] * W[k * ld + j];
     }
@@ -565,11 +569,11 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
     gram<double>(X, m, m, X, m, m, N, W, MP);
     cholesky(W, MP, m, sm);
     double* rdiag = sm.vec + 8 * sm.M;
-    for (int j = TID; j < m; j += LQ_THREADS) rdiag[j] = 1.0 / W[j * MP + j];
+    for (int j = TID; j < m; j += NTHR) rdiag[j] = 1.0 / W[j * MP + j];
     __syncthreads();
     if (m <= LQ_NS_SMALL) {
       // X <- X R^{-1}, row by row (forward substitution on the row vector)
-      for (int i = TID; i < N; i += LQ_THREADS) {
+      for (int i = TID; i < N; i += NTHR) {
         R* row = X + (size_t)i * m;
         double y[LQ_NS_SMALL];
 #pragma unroll 1
@@ -585,7 +589,7 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
       // thread; then X <- X R^{-1} with one warp per row, the row staged in
       // shared memory
       double* Ri = sm.S + 2 * sm.M * MP;
-      for (int j = TID; j < m; j += LQ_THREADS) {
+      for (int j = TID; j < m; j += NTHR) {
         Ri[j * MP + j] = rdiag[j];
         for (int i = j - 1; i >= 0; --i) {
           double acc = 0.0;
@@ -596,7 +600,7 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
       __syncthreads();
       const int warp = TID >> 5, lane = TID & 31;
       double* rowbuf = (double*)sm.buf + (size_t)warp * m;
-      for (int i = warp; i < N; i += LQ_THREADS / 32) {
+      for (int i = warp; i < N; i += NTHR / 32) {
         R* row = X + (size_t)i * m;
         for (int a = lane; a < m; a += 32) rowbuf[a] = (double)row[a];
         __syncwarp();
@@ -610,7 +614,7 @@ __device__ void chol_qr2(const LqChainDev& C, R* X, int m, double* Vout, Smem& s
     }
     __syncthreads();
   }
-  for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+  for (int idx = TID; idx < m * m; idx += NTHR) {
     int a = idx / m, b = idx - a * m;
     double acc = 0.0;
     if (b >= a)
@@ -819,7 +823,7 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
       const R* lp = sg ? Lp1 : Lp0;
       Row* rr = rrow + (size_t)sg * cs * MP;
       Row* ll = lrow + (size_t)sg * cs * MP;
-      for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
+      for (int ii = TID / MT; ii < cn; ii += NTHR / MT) {
         const int a = TID % MT;
         if (a < m) {
           rr[(size_t)ii * MP + a] = (Row)rp[(size_t)(i0 + ii) * m + a];
@@ -827,7 +831,7 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
         }
       }
     }
-    for (int ii = TID; ii < cn; ii += LQ_THREADS) {
+    for (int ii = TID; ii < cn; ii += NTHR) {
       uint32_t w[4];
       philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
       uni[ii] = Ops::make_u(u53(w[0], w[1]));
@@ -995,7 +999,7 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
       const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
       R* rp = sg ? Rp1 : Rp0;
       const Row* rr = rrow + (size_t)sg * cs * MP;
-      for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
+      for (int ii = TID / MT; ii < cn; ii += NTHR / MT) {
         const int a = TID % MT;
         if (a < m) {
           Row v = rr[(size_t)ii * MP + a];
@@ -1004,7 +1008,7 @@ __device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
         }
       }
     }
-    for (int ii = TID; ii < cn; ii += LQ_THREADS)
+    for (int ii = TID; ii < cn; ii += NTHR)
       if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
     __syncthreads();
   }
@@ -1083,7 +1087,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       const R* lp = sg ? Lp1 : Lp0;
       Row* rr = rrow + (size_t)sg * cs * MP;
       Row* ll = lrow + (size_t)sg * cs * MP;
-      for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
+      for (int ii = TID / MT; ii < cn; ii += NTHR / MT) {
         const int a = TID % MT;
         if (a < m) {
           rr[(size_t)ii * MP + a] = (Row)rp[(size_t)(i0 + ii) * m + a];
@@ -1091,7 +1095,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         }
       }
     }
-    for (int ii = TID; ii < cn; ii += LQ_THREADS) {
+    for (int ii = TID; ii < cn; ii += NTHR) {
       uint32_t w[4];
       philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
       uni[ii] = Ops::make_u(u53(w[0], w[1]));
@@ -1104,7 +1108,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       const int kw = min(K, cn - t0);
       // A: x_t = R_t T (xy = 0) and y_t = T L_t (xy = 1), element (sg, xy, t, b)
 #pragma unroll
-      for (int e0 = 0; e0 < NXY; e0 += LQ_THREADS) {
+      for (int e0 = 0; e0 < NXY; e0 += NTHR) {
         const int e = e0 + TID;
         const int b = e % MT, t = (e / MT) % K, xy = (e / (MT * K)) & 1, sg = e / (2 * MT * K);
         const int m = sg ? m1 : m0;
@@ -1230,7 +1234,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       __syncthreads();
       // E: T <- T - sum_t (c_t y_t) x_t^T, element (sg, a, b)
 #pragma unroll
-      for (int e0 = 0; e0 < NT; e0 += LQ_THREADS) {
+      for (int e0 = 0; e0 < NT; e0 += NTHR) {
         const int e = e0 + TID;
         const int b = e % MT, a = (e / MT) % MT, sg = e / (MT * MT);
         const int m = sg ? m1 : m0;
@@ -1271,7 +1275,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
       R* rp = sg ? Rp1 : Rp0;
       const Row* rr = rrow + (size_t)sg * cs * MP;
-      for (int ii = TID / MT; ii < cn; ii += LQ_THREADS / MT) {
+      for (int ii = TID / MT; ii < cn; ii += NTHR / MT) {
         const int a = TID % MT;
         if (a < m) {
           Row v = rr[(size_t)ii * MP + a];
@@ -1280,7 +1284,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         }
       }
     }
-    for (int ii = TID; ii < cn; ii += LQ_THREADS)
+    for (int ii = TID; ii < cn; ii += NTHR)
       if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
     __syncthreads();
     lap(8);
@@ -1373,13 +1377,13 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
       const R* lp = s2 ? Lp1 : Lp0;
       Row* rr = rrow + (size_t)s2 * cs * MP;
       Row* ll = lrow + (size_t)s2 * cs * MP;
-      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
+      for (int idx = TID; idx < cn * m; idx += NTHR) {
         const int ii = idx / m, a = idx - ii * m;
         rr[(size_t)ii * MP + a] = (Row)rp[(size_t)(i0 + ii) * m + a];
         ll[(size_t)ii * MP + a] = (Row)lp[(size_t)(i0 + ii) * m + a];
       }
     }
-    for (int ii = TID; ii < cn; ii += LQ_THREADS) {
+    for (int ii = TID; ii < cn; ii += NTHR) {
       uint32_t w[4];
       philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
       uni[ii] = Ops::make_u(u53(w[0], w[1]));
@@ -1543,14 +1547,14 @@ __device__ void flip_slice_big(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp
       const int sp2 = C.charge ? 1 : (s2 == 0 ? 1 : -1);
       R* rp = s2 ? Rp1 : Rp0;
       const Row* rr = rrow + (size_t)s2 * cs * MP;
-      for (int idx = TID; idx < cn * m; idx += LQ_THREADS) {
+      for (int idx = TID; idx < cn * m; idx += NTHR) {
         const int ii = idx / m, a = idx - ii * m;
         Row v = rr[(size_t)ii * MP + a];
         if (af[ii]) v *= (sp2 * sf[ii] > 0) ? opf_p : opf_m;
         rp[(size_t)(i0 + ii) * m + a] = (R)v;
       }
     }
-    for (int ii = TID; ii < cn; ii += LQ_THREADS)
+    for (int ii = TID; ii < cn; ii += NTHR)
       if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
     __syncthreads();
   }
@@ -1574,11 +1578,11 @@ static __device__ void t_to_dw(Smem& sm, int sg, int m) {
   const int MP = sm.MP;
   __syncthreads();
   double* tmp = sm.W;  // staging copy
-  for (int idx = TID; idx < m * MP; idx += LQ_THREADS) tmp[idx] = T[idx];
+  for (int idx = TID; idx < m * MP; idx += NTHR) tmp[idx] = T[idx];
   __syncthreads();
   float* Th = (float*)T;
   float* Tl = Th + (size_t)sm.M * MP;
-  for (int idx = TID; idx < m * MP; idx += LQ_THREADS) {
+  for (int idx = TID; idx < m * MP; idx += NTHR) {
     const dw v = dw_from(tmp[idx]);
     Th[idx] = v.h;
     Tl[idx] = v.l;
@@ -1616,9 +1620,9 @@ __device__ __forceinline__ int bnd(const LqChainDev& C, int j) { return min(j * 
 
 template <class R> __device__ void fill_P(const LqChainDev& C, int sg, R* P) {
   const int m = C.ns[sg];
-  for (int idx = TID; idx < C.N * m; idx += LQ_THREADS) P[idx] = (R)0;
+  for (int idx = TID; idx < C.N * m; idx += NTHR) P[idx] = (R)0;
   __syncthreads();
-  for (int a = TID; a < m; a += LQ_THREADS) P[(size_t)C.occ[sg][a] * m + a] = (R)1;
+  for (int a = TID; a < m; a += NTHR) P[(size_t)C.occ[sg][a] * m + a] = (R)1;
   __syncthreads();
 }
 
@@ -1655,13 +1659,13 @@ template <class R> __device__ void log_weight(LqChainDev& C, Smem& sm, double* o
   for (int sg = 0; sg < 2; ++sg) {
     const int m = C.ns[sg], cb = C.cur[sg], MP = sm.MP;
     double part = 0.0;
-    for (int idx = TID; idx < C.n * m; idx += LQ_THREADS) {
+    for (int idx = TID; idx < C.n * m; idx += NTHR) {
       int j = 1 + idx / m, a = idx % m;
       part += log(vr_mat(C, sg, cb, j)[a * m + a]);
     }
     lw += cta_sum(part, sm);
     const R* Qn = qr_panel<R>(C, sg, cb, C.n);
-    for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+    for (int idx = TID; idx < m * m; idx += NTHR) {
       int a = idx / m, b = idx - a * m;
       sm.W[a * MP + b] = (double)Qn[(size_t)C.occ[sg][a] * m + b];
     }
@@ -1674,7 +1678,7 @@ template <class R> __device__ void log_weight(LqChainDev& C, Smem& sm, double* o
   }
   if (C.charge) {
     double part = 0.0;
-    for (int idx = TID; idx < C.L * C.N; idx += LQ_THREADS) part += (double)C.s[idx];
+    for (int idx = TID; idx < C.L * C.N; idx += NTHR) part += (double)C.s[idx];
     lw += -C.lambda * cta_sum(part, sm);
   }
   *out_log = lw;
@@ -1742,7 +1746,7 @@ template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
     inverse(sm.W, MP, sm.T[sg], MP, m, sm, &la, &s1);
     sgn *= s1;
     const double* Tm = sm.T[sg];
-    for (int idx = TID; idx < N * m; idx += LQ_THREADS) {
+    for (int idx = TID; idx < N * m; idx += NTHR) {
       int i = idx / m, b = idx - i * m;
       double acc = 0.0;
       for (int a = 0; a < m; ++a) acc += (double)QRb[sg][(size_t)i * m + a] * Tm[a * MP + b];
@@ -1753,7 +1757,7 @@ template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
   const int m0 = C.ns[0], m1 = C.ns[1];
   // densities, double occupancy, onsite energy, sublattice densities
   double nu = 0, nd = 0, docc = 0, eon = 0, na[2][2] = {{0, 0}, {0, 0}};
-  for (int i = TID; i < N; i += LQ_THREADS) {
+  for (int i = TID; i < N; i += NTHR) {
     double du = 0, dd = 0;
     for (int b = 0; b < m0; ++b) du += A[0][(size_t)i * m0 + b] * (double)QLb[0][(size_t)i * m0 + b];
     for (int b = 0; b < m1; ++b) dd += A[1][(size_t)i * m1 + b] * (double)QLb[1][(size_t)i * m1 + b];
@@ -1763,7 +1767,7 @@ template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
     na[0][a] += du; na[1][a] += dd;
   }
   double ekin = 0.0;
-  for (int b = TID; b < lat.nb; b += LQ_THREADS) {
+  for (int b = TID; b < lat.nb; b += NTHR) {
     int i = lat.bond_i[b], j = lat.bond_j[b];
     double t = 0.0;
     for (int sg = 0; sg < 2; ++sg) {
@@ -1787,7 +1791,7 @@ template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
     for (int a = 0; a < 2; ++a)
       for (int b = 0; b < 2; ++b) {
         double part = 0.0;
-        for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+        for (int idx = TID; idx < m * m; idx += NTHR) {
           int p = idx / m, q = idx - p * m;
           part += Ms[a * M * MP + p * MP + q] * Ms[b * M * MP + q * MP + p];
         }
@@ -1798,7 +1802,7 @@ template <class R> __device__ void measure(LqChainDev& C, int jb, Smem& sm) {
   gram<double>(A[1], m1, m1, QLb[0], m0, m0, N, Ms + 2 * M * MP, MP);
   gram<double>(A[0], m0, m0, QLb[1], m1, m1, N, Ms + 3 * M * MP, MP);
   double part = 0.0;
-  for (int idx = TID; idx < m1 * m0; idx += LQ_THREADS) {
+  for (int idx = TID; idx < m1 * m0; idx += NTHR) {
     int p = idx / m0, q = idx - p * m0;
     part += Ms[2 * M * MP + p * MP + q] * Ms[3 * M * MP + q * MP + p];
   }
@@ -2000,7 +2004,7 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
   __syncthreads();
   // Q_i' = Q_i G_i^T for all blocks, streamed row by row
   {
-    for (size_t idx = TID; idx < (size_t)n * N; idx += LQ_THREADS) {
+    for (size_t idx = TID; idx < (size_t)n * N; idx += NTHR) {
       const int i = 1 + (int)(idx / N), row = (int)(idx % N);
       const R* src = qsrc + (size_t)six(i) * pn + (size_t)row * m;
       R* dst = qtrial + (size_t)six(i) * pn + (size_t)row * m;
@@ -2025,7 +2029,7 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
   // --- addition of site j on the reduced chain ------------------------------
   double* q = C.vec;
   double* w = C.vec + N;
-  for (int i = TID; i < N; i += LQ_THREADS) q[i] = (i == j) ? 1.0 : 0.0;
+  for (int i = TID; i < N; i += NTHR) q[i] = (i == j) ? 1.0 : 0.0;
   __syncthreads();
   double logrho = 0.0;
   int valid = sm.ip[9];
@@ -2044,7 +2048,7 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
     for (int pass = 0; pass < 2; ++pass) {
       double* vv = pass ? v2 : v1;
       gram<double>(Qi, m, mr, w, 1, 1, N, vv, 1);
-      for (int r = TID; r < N; r += LQ_THREADS) {
+      for (int r = TID; r < N; r += NTHR) {
         double acc = 0.0;
         for (int a = 0; a < mr; ++a) acc += (double)Qi[(size_t)r * m + a] * vv[a];
         w[r] -= acc;
@@ -2052,16 +2056,16 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
       __syncthreads();
     }
     double part = 0.0;
-    for (int r = TID; r < N; r += LQ_THREADS) part += w[r] * w[r];
+    for (int r = TID; r < N; r += NTHR) part += w[r] * w[r];
     const double rho = sqrt(cta_sum(part, sm));
     if (!(rho > 0.0)) { valid = 0; break; }
-    for (int r = TID; r < N; r += LQ_THREADS) {
+    for (int r = TID; r < N; r += NTHR) {
       const double qq = w[r] / rho;
       q[r] = qq;
       Qi[(size_t)r * m + (m - 1)] = (R)qq;
     }
     double* Vt = vtrial + (size_t)six(i) * m * m;
-    for (int a = TID; a < mr; a += LQ_THREADS) {
+    for (int a = TID; a < mr; a += NTHR) {
       Vt[a * m + (m - 1)] = v1[a] + v2[a];
       Vt[(m - 1) * m + a] = 0.0;
     }
@@ -2123,11 +2127,11 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
   __syncthreads();
   if (sm.ip[10]) {
     const int removed = sm.ip[11];
-    for (int a = TID; a < m; a += LQ_THREADS) C.occ[sg][a] = occr[a];
+    for (int a = TID; a < m; a += NTHR) C.occ[sg][a] = occr[a];
     R* P = qtrial + (size_t)six(0) * pn;
-    for (size_t idx = TID; idx < pn; idx += LQ_THREADS) P[idx] = (R)0;
+    for (size_t idx = TID; idx < pn; idx += NTHR) P[idx] = (R)0;
     __syncthreads();
-    for (int a = TID; a < m; a += LQ_THREADS) P[(size_t)occr[a] * m + a] = (R)1;
+    for (int a = TID; a < m; a += NTHR) P[(size_t)occr[a] * m + a] = (R)1;
     if (TID == 0) {
       sm.bits[removed >> 5] &= ~(1u << (removed & 31));
       sm.bits[j >> 5] |= 1u << (j & 31);
@@ -2150,12 +2154,12 @@ __device__ void swap_attempt(LqChainDev& C, int sg, int k, int j, double u, int 
 // (P^T Q^L_0)^{-1} (left = 1) into sm.T[sg].
 template <class R> __device__ void swap_setup(LqChainDev& C, int sg, Smem& sm, int left = 0) {
   const int N = C.N, m = C.ns[sg], MP = sm.MP;
-  for (int w = TID; w < N / 32 + 1; w += LQ_THREADS) sm.bits[w] = 0u;
+  for (int w = TID; w < N / 32 + 1; w += NTHR) sm.bits[w] = 0u;
   __syncthreads();
   if (TID == 0)
     for (int a = 0; a < m; ++a) sm.bits[C.occ[sg][a] >> 5] |= 1u << (C.occ[sg][a] & 31);
   const R* Qn = left ? ql_panel<R>(C, sg, 0) : qr_panel<R>(C, sg, C.cur[sg], C.n);
-  for (int idx = TID; idx < m * m; idx += LQ_THREADS) {
+  for (int idx = TID; idx < m * m; idx += NTHR) {
     int a = idx / m, b = idx - a * m;
     sm.W[a * MP + b] = (double)Qn[(size_t)C.occ[sg][a] * m + b];
   }
@@ -2263,13 +2267,13 @@ template <class R> __device__ void swap_phase(LqChainDev& C, Smem& sm, int left 
 __device__ inline void load_chain(LqChainDev* g, Smem& sm) {
   if (TID == 0) { prof_shared()->C = sm.C; prof_shared()->depth = 0; }
   const int words = (int)(sizeof(LqChainDev) / 4);
-  for (int w = TID; w < words; w += LQ_THREADS) ((int*)sm.C)[w] = ((const int*)g)[w];
+  for (int w = TID; w < words; w += NTHR) ((int*)sm.C)[w] = ((const int*)g)[w];
   __syncthreads();
 }
 __device__ inline void store_chain(LqChainDev* g, Smem& sm) {
   __syncthreads();
   const int words = (int)(sizeof(LqChainDev) / 4);
-  for (int w = TID; w < words; w += LQ_THREADS) ((int*)g)[w] = ((const int*)sm.C)[w];
+  for (int w = TID; w < words; w += NTHR) ((int*)g)[w] = ((const int*)sm.C)[w];
   __syncthreads();
 }
 
@@ -2295,7 +2299,7 @@ static __device__ void pick_flip_warps(int* sm_ctr, Smem& sm) {
   __syncthreads();
   if (TID == 0) {
     int f0 = -1, f1 = -1;
-    for (int w = 0; w < LQ_THREADS / 32; ++w) {
+    for (int w = 0; w < NTHR / 32; ++w) {
       if (f0 < 0 && wsub[w] == 2 * pair) f0 = w;
       else if (f1 < 0 && wsub[w] == 2 * pair + 1) f1 = w;
     }
@@ -2362,10 +2366,10 @@ __global__ void __launch_bounds__(LQ_THREADS, 2)
     // input check: fields +-1, occupied sites distinct and in range
     if (TID == 0) sm.ip[12] = 0;
     __syncthreads();
-    for (int idx = TID; idx < C.L * C.N; idx += LQ_THREADS)
+    for (int idx = TID; idx < C.L * C.N; idx += NTHR)
       if (C.s[idx] != 1 && C.s[idx] != -1) sm.ip[12] = 1;
     for (int sg = 0; sg < 2; ++sg) {
-      for (int w = TID; w < C.N / 32 + 1; w += LQ_THREADS) sm.bits[w] = 0u;
+      for (int w = TID; w < C.N / 32 + 1; w += NTHR) sm.bits[w] = 0u;
       __syncthreads();
       if (TID == 0)
         for (int a = 0; a < C.ns[sg]; ++a) {
@@ -2395,17 +2399,17 @@ __global__ void __launch_bounds__(LQ_THREADS, 2)
 // through two host functions: its address (attributes, occupancy) and a launch.
 #define LQ_SWEEP_INSTANCE_DECL(NAME)                                                                              \
   const void* sweep_fn_##NAME();                                                                                \
-  cudaError_t sweep_launch_##NAME(int grid, cudaStream_t st, LqChainDev* chains, const int* order, int n_order, \
-                                  int* queue, int n_sweeps, const int* caps, long long budget_ns, int do_measure, \
-                                  SmemPlan plan);
+  cudaError_t sweep_launch_##NAME(int grid, int threads, cudaStream_t st, LqChainDev* chains, const int* order,  \
+                                  int n_order, int* queue, int n_sweeps, const int* caps, long long budget_ns,    \
+                                  int do_measure, SmemPlan plan);
 #define LQ_SWEEP_INSTANCE(R, BIG, NAME)                                                                           \
   namespace lq {                                                                                                \
   const void* sweep_fn_##NAME() { return (const void*)sweep_kernel<R, BIG>; }                                   \
-  cudaError_t sweep_launch_##NAME(int grid, cudaStream_t st, LqChainDev* chains, const int* order, int n_order, \
-                                  int* queue, int n_sweeps, const int* caps, long long budget_ns, int do_measure, \
-                                  SmemPlan plan) {                                                              \
-    sweep_kernel<R, BIG><<<grid, LQ_THREADS, plan.total, st>>>(chains, order, n_order, queue, n_sweeps, caps,   \
-                                                              budget_ns, do_measure, plan);                    \
+  cudaError_t sweep_launch_##NAME(int grid, int threads, cudaStream_t st, LqChainDev* chains, const int* order,  \
+                                  int n_order, int* queue, int n_sweeps, const int* caps, long long budget_ns,    \
+                                  int do_measure, SmemPlan plan) {                                              \
+    sweep_kernel<R, BIG><<<grid, threads, plan.total, st>>>(chains, order, n_order, queue, n_sweeps, caps,      \
+                                                           budget_ns, do_measure, plan);                       \
     return cudaGetLastError();                                                                                  \
   }                                                                                                             \
   }
