@@ -468,6 +468,58 @@ def cp_leg(lq, inputs, torch, n_walkers=304, comb_every=8):
                          "state; one CTA per walker")
 
 
+def uneven_full_leg(lq, inputs, torch, stream, beta_scale=0.1, n_chains=1024, check_chains=2):
+    """The paper-shaped uneven batch in one lq_sim_sweep call: 1024 BCL
+    flat-band chains, cells U[64, 512] (N = 128 to 1024), filling U[1/4, 3/4]
+    of the flat band split by spin (N_sigma = f N_cells, up to 384), U = 2,
+    half periodic, with beta drawn from U[4, 40] and then scaled by beta_scale
+    (rounded to whole slices): the work of a chain grows linearly with its
+    slices, so the full-beta sweep time is the measured one over beta_scale.
+    One autotuned sweep is timed; the check_chains cheapest chains are re-run
+    by the oracle from the same seeds (fields, occupations and counts
+    bit-exact)."""
+    from oracle import OracleSim, lattices
+
+    rng = np.random.default_rng(inputs.SEED0 + 4)
+    specs = inputs.flatband_batch(rng, n_chains, cells=(64, 512), beta_range=(4.0, 40.0))
+    for sp in specs:
+        sp["beta"] = max(0.05, round(sp["beta"] * beta_scale / 0.05) * 0.05)
+    lats = [lq.Lattice.flatband(*sp["lattice"][1:]) for sp in specs]
+    params = [dict({k: sp[k] for k in ("U", "beta", "dtau", "n_up", "n_dn", "n_stab")}, precision=0,
+                   seed=inputs.SEED0) for sp in specs]
+    sim = lq.Sim(lats, params, stream=stream.cuda_stream)
+    sim.init()
+    cfg0 = sim.launch_config()
+    per = time_steps(torch, sim, 1, stream)
+    sim.sync()
+    ns = np.array([p["n_up"] for p in params])
+    Ns = np.array([L.N for L in lats])
+    Ls = np.array([round(p["beta"] / p["dtau"]) for p in params])
+    upd = int(np.sum(2 * Ls * Ns))
+    cost = Ls * Ns * ns.astype(float) ** 2
+    parity = []
+    for c in np.argsort(cost)[:check_chains]:
+        sp = specs[c]
+        lat = lattices.flatband(*sp["lattice"][1:])
+        o = OracleSim(lat, sp["U"], sp["beta"], sp["dtau"], sp["n_up"], sp["n_dn"], sp["n_stab"], seed=inputs.SEED0,
+                      chain=int(c))
+        o.sweep(1)
+        gu, gd = sim.get_fock(int(c))
+        ou, od = o.get_fock()
+        parity.append(dict(chain=int(c), N=int(Ns[c]), n_sigma=int(ns[c]), L=int(Ls[c]),
+                           fields=bool(np.array_equal(sim.get_fields(int(c)), o.get_fields())),
+                           fock=bool(np.array_equal(gu, ou) and np.array_equal(gd, od)),
+                           counts=bool(np.array_equal(sim.stats(int(c)), o.stats()))))
+    sim.close()
+    return dict(chains=n_chains, ms_per_sweep=per[0], beta_scale=beta_scale,
+                full_beta_ms_per_sweep_estimate=per[0] / beta_scale, value=upd / (per[0] * 1e-3), unit=UNIT,
+                n_sigma_range=[int(ns.min()), int(ns.max())], chains_above_32=int((ns > 32).sum()),
+                N_range=[int(Ns.min()), int(Ns.max())], L_range=[int(Ls.min()), int(Ls.max())],
+                launch=cfg0, oracle_parity=parity, precision="FP64",
+                mix="BCL flat-band chains, cells U[64, 512], filling U[1/4, 3/4] of the flat band split by spin "
+                    "(N_sigma = f N_cells), beta U[4, 40] x %g, dtau 0.05, U=2, half periodic" % beta_scale)
+
+
 def observable_deviation(a, b):
     """Chain-mean observables of two runs from the same seeded states: the
     largest |difference| over the measured observables in units of the
@@ -561,6 +613,8 @@ def main():
                     help="only the headline FP64 leg and its e2e (small profiling cases)")
     ap.add_argument("--gram-scan", action="store_true",
                     help="only the Gram study: CUDA cores against tensor cores (DMMA, 3xTF32)")
+    ap.add_argument("--uneven-full", action="store_true",
+                    help="only the paper-shaped uneven flat-band batch (1024 chains, N_sigma up to 384), beta scaled")
     ap.add_argument("--nsigma-scan", action="store_true",
                     help="only the cost-against-N_sigma study (flat-band chains, one sweep per N_sigma)")
     ap.add_argument("--serving-window", type=float, default=10.0)
@@ -588,7 +642,8 @@ def main():
 
     # the CPU baseline runs first, in spawned processes, before any GPU work
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.nsigma_scan or args.gram_scan):
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.nsigma_scan or args.gram_scan or
+                                                                      args.uneven_full):
         cpu = cpu_baseline(spec, n_chains)
 
     import torch
@@ -604,6 +659,10 @@ def main():
     stream = torch.cuda.current_stream()
     if args.nsigma_scan:
         print(json.dumps(dict(study="cost against N_sigma", **nsigma_scan(lq, torch, stream))), flush=True)
+        return
+    if args.uneven_full:
+        print(json.dumps(dict(study="paper-shaped uneven batch", **uneven_full_leg(lq, inputs, torch, stream))),
+              flush=True)
         return
     if args.gram_scan:
         print(json.dumps(dict(study="Gram contractions: CUDA cores and tensor cores", **gram_scan(lq))), flush=True)
@@ -648,7 +707,7 @@ def main():
         tot = max(float(pr[:6].sum()), 1.0)
         phases = {k: round(float(pr[i]) / tot, 4) for i, k in
                   enumerate(["flips", "propagation", "qr", "block_inverse", "swaps", "measure"])}
-        if pr[8:12].sum() > 0:  # parts of the flips (paths of up to 16 particles per spin)
+        if pr[8:12].sum() > 0:  # parts of the flips (chains of up to 32 particles per spin)
             phases.update({k: round(float(pr[8 + i]) / tot, 4) for i, k in
                            enumerate(["flip_staging", "flip_xy_products", "flip_serial_chain", "flip_update_T"])})
         # per-chain means of the measured observables (warm-up and timed sweeps)

@@ -265,7 +265,7 @@ lq_status lq_sim_stats(lq_sim* sim, int32_t chain, int64_t* host_counts4);
  * particle-hole swaps, measurement; then two parts of the swap cycles: the
  * removal (Givens rotations, M^-1, downdate, rotated Q panels) and the
  * addition (vector propagation and Gram-Schmidt); then four parts of the flip
- * cycles of chains with at most 16 particles per spin: row staging and
+ * cycles of chains with at most 32 particles per spin: row staging and
  * write-back, the window's x/y products, the serial per-site chain (with the
  * window block), the recurrences and the update of T (host array of 12). */
 lq_status lq_sim_profile(lq_sim* sim, int32_t chain, int64_t* host_cycles12);

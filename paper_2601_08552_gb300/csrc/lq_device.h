@@ -96,7 +96,7 @@ struct LqChainDev {
   double hook[8];           // test-hook outputs
   long long prof[12];       // cycles per phase: flips, propagation, QR, block inverse, swaps, measurement;
                             // then two parts of the swaps: removal (with Q streaming), addition; then
-                            // four parts of the flips (paths of up to 16 particles per spin): row staging and
+                            // four parts of the flips (chains of up to 32 particles per spin): row staging and
                             // write-back, the window's x/y products, the serial chain (with the window
                             // block), the recurrences and the update of T
   long long sweep_ns_last;  // wall time of the chain's most recent sweep (device global timer)

@@ -1107,9 +1107,8 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
     for (int t0 = 0; t0 < cn; t0 += K) {
       const int kw = min(K, cn - t0);
       // A: x_t = R_t T (xy = 0) and y_t = T L_t (xy = 1), element (sg, xy, t, b)
-#pragma unroll
-      for (int e0 = 0; e0 < NXY; e0 += NTHR) {
-        const int e = e0 + TID;
+#pragma unroll 1
+      for (int e = TID; e < NXY; e += NTHR) {
         const int b = e % MT, t = (e / MT) % K, xy = (e / (MT * K)) & 1, sg = e / (2 * MT * K);
         const int m = sg ? m1 : m0;
         if (e < NXY && t < kw && b < m) {
@@ -1158,25 +1157,34 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
         V* cw = cb(h);  // c_t of this half's spin (0 when not flipped)
         int sacc = 0, sbad = 0, sneg = 0;
+        // the window's fields and uniforms, loaded before the chain starts
+        int sw[K];
+        U uw[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+          sw[t] = t < kw ? sf[t0 + t] : 1;
+          uw[t] = uni[t0 + (t < kw ? t : 0)];
+        }
 #pragma unroll
         for (int t = 0; t < K; ++t) {
           if (t < kw) {
             const int ii = t0 + t;
-            const int s = sf[ii];
-            const U uu = uni[ii];
+            const int s = sw[t];
+            const U uu = uw[t];
             const V d = (sp * s > 0) ? d_p : d_m;
             // G[u][t] and G[t][v] are final for this step (rows and columns
             // below t only change at later steps)
             const V gut = Ops::from_lane(G, hb + 4 * u + t);
             const V gtv = Ops::from_lane(G, hb + 4 * t + v);
-            // every lane takes part in every shuffle (the halves' spins may differ in m)
-            const V gtt = Ops::from_lane(G, hb + 5 * t);
-            const V g = m > 0 ? gtt : Ops::zero();
+            // every lane takes part in every shuffle (the halves' spins may differ
+            // in m; an empty spin's block is zero)
+            const V g = Ops::from_lane(G, hb + 5 * t);
             const V w = Ops::mul(gut, gtv);   // G[u][t] G[t][v], independent of this site's decision
             const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt of this half's spin
             const V c = Ops::div(d, rs);       // used if accepted
             const V ro = Ops::xor_(rs, 16);    // the other spin's factor
-            V r = h ? Ops::mul(ro, rs) : Ops::mul(rs, ro);  // (up factor) x (down factor) in both halves
+            const V rup = h ? ro : rs, rdn = h ? rs : ro;
+            V r = Ops::mul(rup, rdn);          // (up factor) x (down factor), the same in both halves
             if (C.charge) r = Ops::mul(r, s > 0 ? cf_p : cf_m);
             bool neg, bad;
             const bool acc = Ops::accept(r, uu, &neg, &bad);
@@ -1233,9 +1241,8 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       }
       __syncthreads();
       // E: T <- T - sum_t (c_t y_t) x_t^T, element (sg, a, b)
-#pragma unroll
-      for (int e0 = 0; e0 < NT; e0 += NTHR) {
-        const int e = e0 + TID;
+#pragma unroll 1
+      for (int e = TID; e < NT; e += NTHR) {
         const int b = e % MT, a = (e / MT) % MT, sg = e / (MT * MT);
         const int m = sg ? m1 : m0;
         if (e < NT && a < m && b < m) {
@@ -1569,7 +1576,7 @@ __device__ void flip_slice_any(LqChainDev& C, int l, R* a, R* b, const R* c, con
   else if (m <= 4) flip_slice_pair<R, Ops, 4>(C, l, a, b, c, d, tag, sm);
   else if (m <= 8) flip_slice_pair<R, Ops, 8>(C, l, a, b, c, d, tag, sm);
   else if (m <= 16) flip_slice_pair<R, Ops, 16>(C, l, a, b, c, d, tag, sm);
-  else flip_slice_win<R, Ops, 32>(C, l, a, b, c, d, tag, sm);
+  else flip_slice_pair<R, Ops, 32>(C, l, a, b, c, d, tag, sm);
 }
 
 // T (FP64, ld MP) -> double-word halves in place of T[sg]
