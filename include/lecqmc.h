@@ -227,6 +227,12 @@ lq_status lq_sim_autotune(lq_sim* sim, int32_t sweeps_per_candidate, int32_t* ho
  * lq_sim_autotune): host_cfg8 = for the small then the large class, its
  * chains, staging bytes, threads per CTA and grid (zeros for an empty class). */
 lq_status lq_sim_launch_config(const lq_sim* sim, int32_t* host_cfg8);
+/* Pin the launch of plan class plan_class (0: at most 32 particles per spin,
+ * 1: more) instead of the autotuner: staging bytes (at least the plan's
+ * minimum) and threads per CTA (256; 128 allowed for class 0).  Errors:
+ * LQ_EINVAL (bad class, empty class, bad sizes), LQ_EUNSUPPORTED (the
+ * launch does not fit an SM or the simulation's workspace). */
+lq_status lq_sim_set_launch_config(lq_sim* sim, int32_t plan_class, int32_t staging_bytes, int32_t threads);
 /* One stateless batch call on host buffers: upload every chain's fields
  * (host_fields: chains concatenated, each L x N) and Fock state (host_occ:
  * each chain's n_up then n_dn sites), rebuild the QR chains, run n_sweeps

@@ -932,6 +932,30 @@ extern "C" lq_status lq_sim_run_host(lq_sim* S, const int8_t* hf, const int32_t*
   return LQ_OK;
 }
 
+extern "C" lq_status lq_sim_set_launch_config(lq_sim* S, int32_t plan_class, int32_t staging_bytes,
+                                             int32_t threads) {
+  if (!S || plan_class < 0 || plan_class > 1) return fail(LQ_EINVAL, "bad arguments to lq_sim_set_launch_config");
+  lq_sim::PlanClass& pc = S->cls[plan_class];
+  if (!pc.n) return fail(LQ_EINVAL, "the plan class has no chains");
+  if (threads != LQ_THREADS && !(threads == LQ_THREADS / 2 && pc.M <= LQ_NS_SMALL))
+    return fail(LQ_EINVAL, "threads must be 256 (or 128 for the class of at most 32 particles per spin)");
+  if (staging_bytes < lq::staging_min_bytes(pc.M, pc.Nmax, pc.pcols))
+    return fail(LQ_EINVAL, "staging buffer below the plan's minimum");
+  const size_t smem = lq::smem_bytes(pc.M, pc.Nmax, staging_bytes);
+  const int per_sm = smem > 227 * 1024 ? 0 : lq::max_active_sweep_ctas(S->prec, pc.M, smem, threads);
+  if (per_sm < 1) return fail(LQ_EUNSUPPORTED, "the launch does not fit one CTA per SM");
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(pc.n, sms * per_sm);
+  if ((size_t)grid * lq::workspace_bytes(pc.M, pc.Nmax, staging_bytes) > S->ws_bytes)
+    return fail(LQ_EUNSUPPORTED, "the launch needs more workspace than the simulation holds");
+  pc.buf = staging_bytes;
+  pc.threads = threads;
+  pc.grid = grid;
+  return LQ_OK;
+}
+
 extern "C" lq_status lq_sim_launch_config(const lq_sim* S, int32_t* host_cfg8) {
   if (!S || !host_cfg8) return fail(LQ_EINVAL, "bad arguments to lq_sim_launch_config");
   for (int k = 0; k < 2; ++k) {

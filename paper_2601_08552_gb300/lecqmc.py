@@ -31,6 +31,7 @@ EXPORTS = [
     "lq_lattice_cross_stitch", "lq_lattice_info", "lq_lattice_bonds", "lq_lattice_destroy",
     "lq_sim_create", "lq_sim_init", "lq_sim_set_fields", "lq_sim_get_fields", "lq_sim_set_fock",
     "lq_sim_get_fock", "lq_sim_set_sweep_index", "lq_sim_sweep", "lq_sim_autotune", "lq_sim_launch_config",
+    "lq_sim_set_launch_config",
     "lq_sim_run_host", "lq_sim_sync",
     "lq_sim_log_weight",
     "lq_sim_tracked_weight", "lq_sim_field_ratio", "lq_sim_swap_ratio", "lq_sim_records",
@@ -124,6 +125,7 @@ def load(build_if_missing=True):
         "lq_sim_sweep": [P, i32, i32],
         "lq_sim_autotune": [P, i32, pi32],
         "lq_sim_launch_config": [P, pi32],
+        "lq_sim_set_launch_config": [P, i32, i32, i32],
         "lq_sim_run_host": [P, C.POINTER(C.c_int8), pi32, i32, i32, C.POINTER(C.c_int8), pi32, pdbl],
         "lq_sim_sync": [P],
         "lq_sim_log_weight": [P, i32, pdbl, pi32],
@@ -480,6 +482,10 @@ class Sim:
         _check(_lib.lq_sim_launch_config(self.h, _p(out, C.c_int32)))
         keys = ("chains", "staging_bytes", "threads", "grid")
         return [dict(zip(keys, (int(x) for x in out[4 * k:4 * k + 4]))) for k in range(2)]
+
+    def set_launch_config(self, plan_class, staging_bytes, threads=256):
+        """Pin a plan class's launch (staging bytes, threads per CTA)."""
+        _check(_lib.lq_sim_set_launch_config(self.h, int(plan_class), int(staging_bytes), int(threads)))
 
     def run_host(self, fields, occ, n_sweeps, measure=True, fields_out=None, occ_out=None, records_out=None):
         """Batch call on host arrays (ideally pinned): fields int8 (all chains

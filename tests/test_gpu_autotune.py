@@ -83,3 +83,32 @@ def test_autotune_cache(lq):
     assert np.array_equal(sim2.stats(0), before)
     with pytest.raises(lq.LqError):
         sim2.autotune(-1)
+
+
+@pytest.mark.parametrize("staging,threads", [(24576, 128), (65536, 128), (24576, 256), (204800, 256)])
+def test_pinned_launch_configs_keep_the_trajectory(lq, staging, threads):
+    """Every launch the autotuner may pick for the small plan class (half-size
+    CTAs, four per SM, or full ones; small and large staging buffers) gives
+    the oracle's trajectory on the dilute-gas chains."""
+    spec = dict(lattice=("square", 16, 16), U=4.0, beta=2.0, dtau=0.05, n_up=8, n_dn=8, n_stab=8)
+    n = 64
+    lat = lq.Lattice.square(16, 16)
+    sim = lq.Sim([lat] * n, [dict(spec, precision=0, seed=5)] * n)
+    sim.init()
+    for c in (0, 33):
+        sim.log_weight(c)
+    sim.set_launch_config(0, staging, threads)
+    cfg = sim.launch_config()[0]
+    assert cfg["threads"] == threads and cfg["staging_bytes"] == staging
+    sim.sweep(2)
+    sim.sync()
+    for c in (0, n - 1):
+        o = OracleSim(lattices.square(16, 16), 4.0, 2.0, 0.05, 8, 8, 8, seed=5, chain=c)
+        o.sweep(2)
+        assert np.array_equal(sim.get_fields(c), o.get_fields())
+        assert np.array_equal(sim.stats(c), o.stats())
+        assert elem_rel(sim.records(c), o.records()) < TOL
+    with pytest.raises(lq.LqError):
+        sim.set_launch_config(0, 1024, 256)  # below the plan's minimum
+    with pytest.raises(lq.LqError):
+        sim.set_launch_config(0, staging, 96)
