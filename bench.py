@@ -520,6 +520,45 @@ def uneven_full_leg(lq, inputs, torch, stream, beta_scale=0.1, n_chains=1024, ch
                     "(N_sigma = f N_cells), beta U[4, 40] x %g, dtau 0.05, U=2, half periodic" % beta_scale)
 
 
+def chain16_leg(lq, inputs, torch, stream, warm=200, sweeps=1000):
+    """The single-chain FP64 run on the 16-site Hubbard chain (N_up = N_dn = 2,
+    U = 4, beta = 4, dtau = 0.1, QR every 10): `warm` unmeasured sweeps, then
+    `sweeps` measured sweeps in one launch timed by CUDA events; beside it the
+    oracle on one host core (a spawned process) on the same chain for about
+    5 s of sweeps.  One chain occupies one CTA, so this is the latency of a
+    sweep, not a throughput figure."""
+    w = inputs.WORKLOADS["chain16"]
+    spec = {k: w[k] for k in ("lattice", "U", "beta", "dtau", "n_up", "n_dn", "n_stab")}
+    N = spec["lattice"][1]
+    L = round(spec["beta"] / spec["dtau"])
+    lat = lq.Lattice.chain(N)
+    sim = lq.Sim([lat], [dict(spec, precision=0, seed=inputs.SEED0)], stream=stream.cuda_stream)
+    sim.init()
+    sim.sweep(warm, measure=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.sweep(sweeps, measure=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = sim.stats(0)
+    sim.close()
+    upd = 2 * L * N
+    out = dict(value=upd * sweeps / (ms * 1e-3), unit=UNIT, sweeps_per_s=sweeps / (ms * 1e-3), ms_per_sweep=ms / sweeps,
+               field_accept=float(st[1] / max(st[0], 1)), swap_accept=float(st[3] / max(st[2], 1)),
+               sweeps=sweeps, warm=warm, precision="FP64",
+               workload="1D periodic Hubbard chain N=16, t=1, N_up=N_dn=2, U=4, beta=4, dtau=0.1 (L=40), QR every 10, "
+                        "1 chain, %d + %d sweeps" % (warm, sweeps))
+    pool = OraclePool(spec, inputs.SEED0, 1)
+    dt1, _ = pool.step(1)
+    k = max(2, min(5000, int(5.0 / max(dt1, 1e-4))))
+    dt, _ = pool.step(k)
+    pool.close()
+    out["oracle_1core"] = dict(value=upd * k / dt, unit=UNIT, sweeps_per_s=k / dt, cores=1, kind="oracle",
+                               sample="the same chain, %d timed sweeps after one untimed, %.1f s wall" % (k, dt))
+    return out
+
+
 def observable_deviation(a, b):
     """Chain-mean observables of two runs from the same seeded states: the
     largest |difference| over the measured observables in units of the
@@ -833,6 +872,10 @@ def main():
     if not args.headline_only and args.workload == WORKLOAD:
         cp = cp_leg(lq, inputs, torch)
 
+    chain16 = None
+    if not args.headline_only and args.workload == WORKLOAD:
+        chain16 = chain16_leg(lq, inputs, torch, stream)
+
     gas64 = None
     if not args.no_gas64 and args.workload == WORKLOAD:
         gas64 = gas64_leg(lq, inputs, torch, stream, roofline["peak"])
@@ -863,7 +906,7 @@ def main():
                     swap_accept=float(dstat[3] / max(dstat[2], 1)), phase_cycle_share=phases,
                     roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=args.steps, clocks=clocks,
                     reduced_precision=mixed, attractive=attractive, neighbour_swaps=neighbour, left_swaps=left,
-                    uneven_flatband=uneven, gas64x64=gas64, constrained_path=cp,
+                    uneven_flatband=uneven, gas64x64=gas64, constrained_path=cp, chain16=chain16,
                     serving=serving)
         print(json.dumps(line), flush=True)
     if dist is not None:

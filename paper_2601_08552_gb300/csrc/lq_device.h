@@ -13,11 +13,11 @@ static inline void lq_dw_split(double x, float out[2]) {
 
 #define LQ_NOBS 9          // sign, n_up, n_dn, docc, ekin, szz_00, szz_11, szz_01, s_par
 #define LQ_NS_MAX 512      // particles per spin (the C ABI's LQ_MAX_PARTICLES)
-#define LQ_NS_SMALL 32     // up to this many per spin, one warp per spin flips with one lane per column and
-                           // the m x m matrices live in shared memory; above it, a four-warp group per spin
+#define LQ_NS_SMALL 32     // up to this many per spin, one leader warp runs both spins' flip chains and the
+                           // m x m matrices live in shared memory; above it, a four-warp group per spin
                            // flips and those matrices live in a global workspace per CTA
 #define LQ_THREADS 256     // threads per CTA (one CTA per chain)
-#define LQ_WIN 8           // sites per field-flip window (submatrix update)
+#define LQ_WIN 8           // sites per field-flip window of the four-warp path (the pair path uses 4)
 #define LQ_SWEEP_RING 32   // per-sweep wall times a chain descriptor keeps
 // 8-byte elements of one spin's window: x rows, y rows (K x MP each), G (K x (K+1)), c (K),
 // c-scaled G factors of the x/y recurrences (K x K)

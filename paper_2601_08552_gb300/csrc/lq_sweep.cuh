@@ -16,11 +16,11 @@
 //     submatrix update over windows of K sites: the window's dense products
 //     are batched, and the serial chain of a site is its diagonal block
 //     element, the ratio and a K x K rank-1 update.  Up to 32 particles per
-//     spin one warp per spin does it (the spins exchange their factors through
-//     shared memory once per site, and two resident chains per SM put the four
-//     flip warps on four FP64 pipes); above 32 a four-warp group per spin
-//     shares the window's dense work and the m x m matrices sit in a global
-//     workspace per CTA;
+//     spin one leader warp runs the chain of both spins (K = 4, one block
+//     element per lane, the spins' factors exchanged by one shuffle) and the
+//     whole CTA shares the window's dense work; above 32 a four-warp group per
+//     spin (K = 8) shares it and the m x m matrices sit in a global workspace
+//     per CTA;
 //   * particle-hole swaps: removal by permutation + Givens retriangulation
 //     (Eqs. S9-S12), addition by propagating one vector and orthogonalising
 //     it twice against each Q_i (Eqs. S1-S8, Eq. 4); the target is uniform
@@ -667,6 +667,16 @@ template <class RowT> struct OpsF64 {
     const double y0 = d * x0;
     return fma(y0, p, y0);
   }
+  // 1 / r by the same seed and third-order step: x0 (1 + e + e^2), three FP64
+  // instructions after the seed
+  __device__ static V rcp(V r) {
+    double x0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x0) : "d"(r));
+    const double e = fma(-r, x0, 1.0);
+    const double p = fma(e, e, e);
+    return fma(x0, p, x0);
+  }
+  __device__ static V of(double x) { return x; }
   __device__ static double pack(V v) { return v; }
   __device__ static V unpack(double v) { return v; }
   __device__ static U make_u(double u) { return u; }
@@ -728,6 +738,8 @@ struct OpsDW {
   __device__ static V from_lane(V a, int src) { return dw_shfl(a, src); }
   __device__ static V one_plus(V d, V g) { return dw_add(dw{1.f, 0.f}, dw_mul(d, g)); }
   __device__ static V div(V d, V r) { return dw_div(d, r); }
+  __device__ static V rcp(V r) { return dw_div(dw{1.f, 0.f}, r); }
+  __device__ static V of(double x) { return dw_from(x); }
   __device__ static double pack(V v) {
     return __longlong_as_double(((long long)__float_as_int(v.l) << 32) | (unsigned)__float_as_int(v.h));
   }
@@ -784,240 +796,9 @@ struct OpsDW {
 // two spins' factors and one K x K rank-1 update; the m-length dot products
 // are batched per window, the x/y recurrences run after the window's sites,
 // and T takes the window's rank-1 terms at its end.
-// One warp per spin.  MT is a compile-time bound on m (a power of two <= 32)
-// so that every lane-to-element map is a shift and every element loop
-// unrolls.  Rp: right panels (rows scaled on accept), Lp: left panels (L~
-// transposed), T: (L~ R~)^{-1} in shared memory.
-// ---------------------------------------------------------------------------
-template <class R, class Ops, int MT>
-__device__ void flip_slice_win(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag,
-                               Smem& sm) {
-  PhaseTimer pt_(PH_FLIP);
-  typedef typename Ops::V V;
-  typedef typename Ops::Row Row;
-  typedef typename Ops::U U;
-  constexpr int K = LQ_WIN, KP = LQ_WIN + 1;
-  constexpr int XE = (K * MT + 31) / 32;         // x/y elements per lane
-  constexpr int GE = (K * K) / 32;               // window-block elements per lane
-  constexpr int TE = (MT * MT + 31) / 32;        // T elements per lane
-  constexpr int XU = XE < 2 ? XE : 2, TU = TE < 2 ? TE : 2;  // unroll of the per-lane element loops
-  const int N = C.N, MP = sm.MP;
-  const int m0 = C.ns[0], m1 = C.ns[1];
-  const size_t per_site = (size_t)4 * MP * sizeof(Row) + 8 + sizeof(U) + 4 + 4;
-  int cs = (int)(sm.buf_bytes / per_site);
-  if (cs > 512) cs = 512;
-  Row* rrow = (Row*)sm.buf;
-  Row* lrow = rrow + (size_t)2 * cs * MP;
-  double* racc = (double*)(lrow + (size_t)2 * cs * MP);  // accepted ratios (packed), multiplied per chunk
-  U* uni = (U*)(racc + cs);
-  int* sf = (int*)(uni + cs);
-  int* af = sf + cs;
-  const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
-  const int warp = TID >> 5, lane = TID & 31;
-  const int role = (warp == sm.ip[14]) ? 0 : (warp == sm.ip[15]) ? 1 : -1;
-  for (int i0 = 0; i0 < N; i0 += cs) {
-    const int cn = min(cs, N - i0);
-    for (int sg = 0; sg < 2; ++sg) {
-      const int m = sg ? m1 : m0;
-      const R* rp = sg ? Rp1 : Rp0;
-      const R* lp = sg ? Lp1 : Lp0;
-      Row* rr = rrow + (size_t)sg * cs * MP;
-      Row* ll = lrow + (size_t)sg * cs * MP;
-      for (int ii = TID / MT; ii < cn; ii += NTHR / MT) {
-        const int a = TID % MT;
-        if (a < m) {
-          rr[(size_t)ii * MP + a] = (Row)rp[(size_t)(i0 + ii) * m + a];
-          ll[(size_t)ii * MP + a] = (Row)lp[(size_t)(i0 + ii) * m + a];
-        }
-      }
-    }
-    for (int ii = TID; ii < cn; ii += NTHR) {
-      uint32_t w[4];
-      philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
-      uni[ii] = Ops::make_u(u53(w[0], w[1]));
-      sf[ii] = C.s[(size_t)l * N + i0 + ii];
-    }
-    __syncthreads();
-    if (role >= 0) {
-      const int sg = role, m = sg ? m1 : m0;
-      const typename Ops::TRef T = Ops::tref(sm, sg);
-      const bool upd = m > 0 && C.lambda != 0.0;
-      const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
-      const V d_p = Ops::delta(C, true), d_m = Ops::delta(C, false);
-      const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
-      V* Xw = (V*)sm.win + (size_t)sg * LQ_WIN_ELEMS(MP);
-      V* Yw = Xw + K * MP;
-      V* Gw = Yw + K * MP;
-      V* cw = Gw + K * KP;
-      V* CG = cw + K;  // c_t G[j][t] (j > t) and c_t G[t][j] (t < j)
-      const Row* rbase = rrow + (size_t)sg * cs * MP;
-      const Row* lbase = lrow + (size_t)sg * cs * MP;
-      int wsign = 1, nacc = 0, nbad = 0;
-      for (int t0 = 0; t0 < cn; t0 += K) {
-        const int kw = min(K, cn - t0);
-        // window set-up: x_t = R_t T, y_t = T L_t   (element (t, b), b = lane % MT)
-#pragma unroll XU
-        for (int it = 0; it < XE; ++it) {
-          const int e = lane + 32 * it, t = e / MT, b = e % MT;
-          if (e < K * MT && t < kw && b < m) {
-            const Row* rw = rbase + (size_t)(t0 + t) * MP;
-            const Row* lr = lbase + (size_t)(t0 + t) * MP;
-            V xa = Ops::zero(), ya = Ops::zero();
-#pragma unroll
-            for (int a = 0; a < MT; ++a)
-              if (a < m) {
-                Ops::acc(xa, rw[a], T.ld(a * MP + b));
-                Ops::accT(ya, T.ld(b * MP + a), lr[a]);
-              }
-            Xw[t * MP + b] = Ops::finish(xa);
-            Yw[t * MP + b] = Ops::finish(ya);
-          }
-        }
-        __syncwarp();
-        // G[u][v] = x_u . L_v   (element (u, v), v = lane % K)
-#pragma unroll
-        for (int it = 0; it < GE; ++it) {
-          const int e = lane + 32 * it, u = e / K, v = e % K;
-          if (u < kw && v < kw) {
-            const Row* lr = lbase + (size_t)(t0 + v) * MP;
-            V ga = Ops::zero();
-#pragma unroll
-            for (int b = 0; b < MT; ++b)
-              if (b < m) Ops::accT(ga, Xw[u * MP + b], lr[b]);
-            Gw[u * KP + v] = Ops::finish(ga);
-          }
-        }
-        __syncwarp();
-        for (int t = 0; t < kw; ++t) {
-          const int ii = t0 + t;
-          const int s = sf[ii];
-          const bool pos = sp * s > 0;
-          const V d = pos ? d_p : d_m;
-          const V g = m > 0 ? Gw[t * KP + t] : Ops::zero();
-          const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt
-          const V c = Ops::div(d, rs);       // used if accepted
-          const int par = (i0 + ii) & 1;
-          if (lane == 0) sm.gx[par * 2 + sg] = Ops::pack(rs);
-          bar_pair();
-          V r = Ops::mul(Ops::unpack(sm.gx[par * 2]), Ops::unpack(sm.gx[par * 2 + 1]));
-          if (C.charge) r = Ops::mul(r, s > 0 ? cf_p : cf_m);
-          bool neg, bad;
-          const bool acc = Ops::accept(r, uni[ii], &neg, &bad);
-          const bool flip = acc && upd;
-          if (lane == 0) cw[t] = flip ? c : Ops::zero();
-          if (flip) {
-            // c G[u][t] once per row u (lane u), then G[u][v] -= (c G[u][t]) G[t][v];
-            // column t is not written at this step, so the factors are current
-            const V cu = Ops::mul(c, Gw[(lane & (K - 1)) * KP + t]);
-#pragma unroll
-            for (int it = 0; it < GE; ++it) {
-              const int e = lane + 32 * it, u = e / K, v = e % K;
-              const V cuu = Ops::from_lane(cu, u);
-              if (u > t && v > t && u < kw && v < kw) Gw[u * KP + v] = Ops::fnma(cuu, Gw[t * KP + v], Gw[u * KP + v]);
-            }
-          }
-          if (sg == 0) {
-            if (lane == 0) {
-              af[ii] = acc ? 1 : 0;
-              racc[ii] = Ops::pack(r);
-            }
-            nbad += bad;
-            if (acc) {
-              wsign = neg ? -wsign : wsign;
-              ++nacc;
-            }
-          }
-          __syncwarp();
-        }
-        // c-scaled factors of the recurrences: CG[j][t] = c_t G[j][t] (j > t),
-        // CG[t][j] = c_t G[t][j] (t < j)
-#pragma unroll
-        for (int it = 0; it < GE; ++it) {
-          const int e = lane + 32 * it, u = e / K, v = e % K;
-          V val = Ops::zero();
-          if (u > v && u < kw) val = Ops::mul(cw[v], Gw[u * KP + v]);
-          else if (u < v && v < kw) val = Ops::mul(cw[u], Gw[u * KP + v]);
-          CG[u * K + v] = val;
-        }
-        __syncwarp();
-        // the window's x_j, y_j at their flip times: column t and row t of the
-        // block are frozen once site t is done, so the recurrences
-        //   x_j -= c_t G[j][t] x_t,  y_j -= c_t G[t][j] y_t  (j > t)
-        // run here, t ascending, parallel over (j, b)
-        for (int t = 0; t + 1 < kw; ++t) {
-#pragma unroll XU
-          for (int it = 0; it < XE; ++it) {
-            const int e = lane + 32 * it, j = e / MT, b = e % MT;
-            if (e < K * MT && j > t && j < kw && b < m) {
-              Xw[j * MP + b] = Ops::fnma(CG[j * K + t], Xw[t * MP + b], Xw[j * MP + b]);
-              Yw[j * MP + b] = Ops::fnma(CG[t * K + j], Yw[t * MP + b], Yw[j * MP + b]);
-            }
-          }
-          __syncwarp();
-        }
-        // y_t <- c_t y_t, then T <- T - sum_t (c_t y_t) x_t^T  (element (a, b), b = lane % MT)
-#pragma unroll XU
-        for (int it = 0; it < XE; ++it) {
-          const int e = lane + 32 * it, t = e / MT, b = e % MT;
-          if (e < K * MT && t < kw && b < m) Yw[t * MP + b] = Ops::mul(cw[t], Yw[t * MP + b]);
-        }
-        __syncwarp();
-#pragma unroll TU
-        for (int it = 0; it < TE; ++it) {
-          const int e = lane + 32 * it, a = e / MT, b = e % MT;
-          if (e < MT * MT && a < m && b < m) {
-            V tv = T.ld(a * MP + b);
-#pragma unroll
-            for (int t = 0; t < K; ++t)
-              if (t < kw) tv = Ops::fnma(Yw[t * MP + a], Xw[t * MP + b], tv);
-            T.st(a * MP + b, tv);
-          }
-        }
-        __syncwarp();
-      }
-      if (sg == 0) {
-        // product of the chunk's accepted ratios, lane-parallel
-        typename Ops::Prod wp;
-        wp.init();
-        for (int ii = lane; ii < cn; ii += 32)
-          if (af[ii]) wp.mul(Ops::unpack(racc[ii]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wp.combine_xor(o);
-        if (lane == 0) {
-          C.cnt[0] += cn;
-          C.cnt[1] += nacc;
-          C.logw += wp.log_value();
-          if (wsign < 0) C.sign = -C.sign;
-          if (nbad) C.err |= LQ_ERR_NONFINITE;
-        }
-      }
-    }
-    __syncthreads();
-    // rows back to the panel; accepted sites scale their row by 1 + Delta_sigma
-    for (int sg = 0; sg < 2; ++sg) {
-      const int m = sg ? m1 : m0;
-      const int sp = C.charge ? 1 : (sg == 0 ? 1 : -1);
-      R* rp = sg ? Rp1 : Rp0;
-      const Row* rr = rrow + (size_t)sg * cs * MP;
-      for (int ii = TID / MT; ii < cn; ii += NTHR / MT) {
-        const int a = TID % MT;
-        if (a < m) {
-          Row v = rr[(size_t)ii * MP + a];
-          if (af[ii]) v *= (sp * sf[ii] > 0) ? opf_p : opf_m;
-          rp[(size_t)(i0 + ii) * m + a] = (R)v;
-        }
-      }
-    }
-    for (int ii = TID; ii < cn; ii += NTHR)
-      if (af[ii]) C.s[(size_t)l * N + i0 + ii] = (int8_t)(-sf[ii]);
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Field flips for m <= 16 particles per spin: the same submatrix update in
-// windows of K = 4 sites, with the work of a window spread over the CTA and
-// the serial chain of BOTH spins on one leader warp:
+// For m <= 32 particles per spin the window is K = 4 sites, the work of a
+// window is spread over the CTA and the serial chain of BOTH spins runs on one
+// leader warp:
 //   A  (all warps)  x_t = R~_t T and y_t = T L~_t of both spins, one output
 //                   per thread;
 //   B  (leader)     the window blocks G = X L~_W of both spins, one element
@@ -1060,6 +841,21 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   int* sf = (int*)(uni + cs);
   int* af = sf + cs;
   const Row opf_p = (Row)C.opd_p, opf_m = (Row)C.opd_m;
+  // The ratio of a flip at site t is dd(s) (1/Delta_up + G_up[t][t]) (1/Delta_dn + G_dn[t][t]) with
+  // dd(s) = Delta_up Delta_dn (times the charge channel's constant), and c = Delta/(1 + Delta G[t][t])
+  // = 1/(1/Delta + G[t][t]).  So the chain forms 1/Delta + G[t][t] (one add), its reciprocal and the
+  // product of the two spins' factors; |dd(s)| moves into the Metropolis threshold (u/|dd(s)|, formed
+  // at staging), its sign into the sign bit and its magnitude into the chunk's weight product.  Without
+  // an interaction (lambda = 0) 1/Delta and dd are replaced by 1 and the window block by 0, so that
+  // every ratio is exactly 1.
+  const bool lam0 = C.lambda == 0.0;
+  // dd(s) for s > 0 (dd_p) and s < 0 (dd_m)
+  const double dd_p = lam0 ? 1.0 : C.charge ? C.delta_p * C.delta_p * C.cfac_p : C.delta_p * C.delta_m;
+  const double dd_m = lam0 ? 1.0 : C.charge ? C.delta_m * C.delta_m * C.cfac_m : C.delta_p * C.delta_m;
+  const double thr_p = 1.0 / fabs(dd_p), thr_m = 1.0 / fabs(dd_m);
+  const int ddn = (dd_p < 0.0 ? 1 : 0) | (dd_m < 0.0 ? 2 : 0);
+  // 1/Delta for s sp > 0 and < 0, formed once per slice (an IEEE division is a dozen FP64 instructions)
+  const V id_p = Ops::of(lam0 ? 1.0 : 1.0 / C.delta_p), id_m = Ops::of(lam0 ? 1.0 : 1.0 / C.delta_m);
   const int warp = TID >> 5, lane = TID & 31;
   const bool leader = warp == sm.ip[14];
   V* const win0 = (V*)sm.win;
@@ -1069,8 +865,9 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   auto Gb = [&](int sg) { return Yb(sg) + K * MP; };
   auto cb = [&](int sg) { return Gb(sg) + K * KP; };
   auto CGb = [&](int sg) { return cb(sg) + K; };
-  // sub-phase cycles (thread 0): staging, window products, serial chain, recurrences and T
-  __shared__ long long tsub;
+  // sub-phase cycles: staging, window products, recurrences and T (thread 0's clock between the
+  // barriers) and the serial chain (the leader's own clock from the window block to its last store)
+  __shared__ long long tsub, tchain;
   if (TID == 0) tsub = clock64();
   auto lap = [&](int k) {
     if (TID == 0) {
@@ -1098,8 +895,9 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
     for (int ii = TID; ii < cn; ii += NTHR) {
       uint32_t w[4];
       philox(C.chain_id, C.sweep, (tag << 24) | (uint32_t)l, (uint32_t)(i0 + ii), C.key0, C.key1, w);
-      uni[ii] = Ops::make_u(u53(w[0], w[1]));
-      sf[ii] = C.s[(size_t)l * N + i0 + ii];
+      const int s = C.s[(size_t)l * N + i0 + ii];
+      uni[ii] = Ops::make_u(u53(w[0], w[1]) * (s > 0 ? thr_p : thr_m));
+      sf[ii] = s;
     }
     __syncthreads();
     lap(8);
@@ -1132,16 +930,18 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       __syncthreads();
       lap(9);
       if (leader) {
+        const long long tl0 = clock64();
         // lane 16 h + 4 u + v holds G[u][v] of spin h in a register for the
         // whole window: every read of the serial chain is a shuffle
         const int h = lane >> 4, hl = lane & 15;
         const int m = h ? m1 : m0;
         const int u = hl >> 2, v = hl & 3, hb = lane & 16;
+        const bool upd = m > 0 && !lam0;
         // B: G[u][v] = x_u . L~_v of this half's spin (one dependent chain:
         // on GB300 a dependent FP64 FMA costs its sub-partition no more than
         // an independent one)
         V G = Ops::zero();
-        if (u < kw && v < kw) {
+        if (u < kw && v < kw && upd) {
           const V* xr = Xb(h) + u * MP;
           const Row* lr = lrow + ((size_t)h * cs + t0 + v) * MP;
           V acc = Ops::zero();
@@ -1151,10 +951,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
           G = Ops::finish(acc);
         }
         // C: the serial chain of both spins, sites t0 .. t0 + kw - 1
-        const bool upd = m > 0 && C.lambda != 0.0;
         const int sp = C.charge ? 1 : (h == 0 ? 1 : -1);
-        const V d_p = Ops::delta(C, true), d_m = Ops::delta(C, false);
-        const V cf_p = Ops::cfac(C, true), cf_m = Ops::cfac(C, false);
         V* cw = cb(h);  // c_t of this half's spin (0 when not flipped)
         int sacc = 0, sbad = 0, sneg = 0;
         // the window's fields and uniforms, loaded before the chain starts
@@ -1171,7 +968,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
             const int ii = t0 + t;
             const int s = sw[t];
             const U uu = uw[t];
-            const V d = (sp * s > 0) ? d_p : d_m;
+            const V idd = (sp * s > 0) ? id_p : id_m;
             // G[u][t] and G[t][v] are final for this step (rows and columns
             // below t only change at later steps)
             const V gut = Ops::from_lane(G, hb + 4 * u + t);
@@ -1180,14 +977,14 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
             // in m; an empty spin's block is zero)
             const V g = Ops::from_lane(G, hb + 5 * t);
             const V w = Ops::mul(gut, gtv);   // G[u][t] G[t][v], independent of this site's decision
-            const V rs = Ops::one_plus(d, g);  // 1 + Delta_sigma G_tt of this half's spin
-            const V c = Ops::div(d, rs);       // used if accepted
+            const V rs = Ops::add(idd, g);     // 1/Delta_sigma + G_tt of this half's spin
+            const V c = Ops::rcp(rs);          // Delta/(1 + Delta G_tt), used if accepted
             const V ro = Ops::xor_(rs, 16);    // the other spin's factor
             const V rup = h ? ro : rs, rdn = h ? rs : ro;
-            V r = Ops::mul(rup, rdn);          // (up factor) x (down factor), the same in both halves
-            if (C.charge) r = Ops::mul(r, s > 0 ? cf_p : cf_m);
+            const V r = Ops::mul(rup, rdn);    // ratio / dd(s), the same in both halves
             bool neg, bad;
             const bool acc = Ops::accept(r, uu, &neg, &bad);
+            neg ^= (ddn >> (s > 0 ? 0 : 1)) & 1;
             const bool flip = acc && upd;
             if (flip && u > t && v > t) G = Ops::fnma(c, w, G);
             if (hl == 0) cw[t] = flip ? c : Ops::zero();
@@ -1211,9 +1008,17 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
           else if (u < v && v < kw) val = Ops::mul(cw[u], G);
           CGb(h)[u * K + v] = val;
         }
+        __syncwarp();
+        if (lane == 0) tchain = clock64() - tl0;
       }
       __syncthreads();
-      lap(10);
+      if (TID == 0) {
+        // the leader's chain time, and the rest of this stretch (the hand-over at the barrier) with D and E
+        const long long t = clock64();
+        C.prof[10] += tchain;
+        C.prof[11] += (t - tsub) - tchain;
+        tsub = t;
+      }
       // D: x_j -= c_t G[j][t] x_t and y_j -= c_t G[t][j] y_t (j > t), t ascending; then y_t <- c_t y_t.
       // Warp w < 4 takes spin w >> 1, x (even w) or y (odd w), element (j, b)
       if (warp < 4) {
@@ -1263,8 +1068,9 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       // product of the chunk's accepted ratios, lane-parallel
       typename Ops::Prod wp;
       wp.init();
+      const V add_p = Ops::of(fabs(dd_p)), add_m = Ops::of(fabs(dd_m));
       for (int ii = lane; ii < cn; ii += 32)
-        if (af[ii]) wp.mul(Ops::unpack(racc[ii]));
+        if (af[ii]) wp.mul(Ops::mul(Ops::unpack(racc[ii]), sf[ii] > 0 ? add_p : add_m));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) wp.combine_xor(o);
       if (lane == 0) {

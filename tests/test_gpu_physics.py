@@ -30,5 +30,40 @@ def test_flatband_low_temperature_limits(lq):
     for r in rows:
         assert r["sum_rule_max_abs"] < 1e-9
         assert abs(r["szz_11"] - r["szz_00"]) < 1e-9 and abs(r["szz_01"] + r["szz_00"]) < 1e-9
+    # 2e-4 bounds the finite-temperature shift of S^zz_00 above its T -> 0 value 1/16 at beta = 16: the
+    # exact Trotterized ED of the 4-cell chain (below) puts it at 1.5e-4 at beta = 16, 1.2e-4 at beta = 32
+    # and 2e-5 at beta = 128 (low-lying spin waves of the ferromagnet), the same for dtau = 0.1, 0.05 and
+    # 0.025, so it is not a Trotter error
     assert abs(cold["szz_00"] - 1.0 / 16.0) < 5.0 * cold["szz_00_err"] + 2e-4
     assert cold["s_par"] > hot["s_par"] + 0.1
+
+
+def test_flatband_4cells_matches_trotter_ed(lq):
+    """The same ferromagnet at 4 cells (N = 8, N_up = N_dn = 2), where the
+    canonical Trotterized ensemble is solvable exactly: 64 chains x 1000
+    sweeps at beta = 16 against the ED, within 4 standard errors and no
+    other slack; and the ED itself pins the T -> 0 statement (S^zz_00 -> 1/16)
+    and the size of its finite-temperature shift used above."""
+    import exact
+    from oracle import OBS_NAMES, lattices
+    from stats import jackknife_ratio
+
+    lat_o = lattices.flatband(4)
+    U, dtau, beta = 2.0, 0.05, 16.0
+    ed = exact.TrotterED(lat_o, U, dtau, round(beta / dtau), 2, 2).observables()
+    assert 1.0e-4 < ed["szz_00"] - 1.0 / 16.0 < 2.0e-4
+    ed_cold = exact.TrotterED(lat_o, U, 0.1, 1280, 2, 2).observables()  # beta = 128
+    assert abs(ed_cold["szz_00"] - 1.0 / 16.0) < 3.0e-5
+    n = 64
+    L = lq.Lattice.flatband(4)
+    sim = lq.Sim([L] * n, [dict(U=U, beta=beta, dtau=dtau, n_up=2, n_dn=2, n_stab=8, precision=lq.LQ_FP64,
+                                seed=20260108)] * n)
+    sim.init()
+    sim.sweep(100, measure=False)
+    sim.sweep(1000, measure=True)
+    sim.sync()
+    recs = np.concatenate([sim.records(c) for c in range(n)])
+    sim.close()
+    for name in ("docc", "szz_00", "szz_01", "s_par"):
+        est, err = jackknife_ratio(recs, OBS_NAMES.index(name), nbins=64)
+        assert abs(est - ed[name]) < 4.0 * err + 1e-12, (name, est, err, ed[name])
