@@ -200,7 +200,10 @@ class ClockSampler:
 def algorithmic_fp64_flops(spec, n_chains, accepts, attempts, G_bonds, prec):
     """FP64 flops of one sweep of all chains: field-flip algebra (Sherman-
     Morrison ratio and rank-1 update), and for FP64 panels the slice
-    propagation, the block Gram matrices and CholeskyQR2."""
+    propagation, the block Gram matrices and CholeskyQR2.  The square
+    lattice's checkerboard families share one cosh each and hold every site
+    once, so a bond costs two FMAs per column (x_i + t x_j, x_j + t x_i) and
+    the cosh product and the field factor one multiply per element."""
     N = spec["lattice"][1] * spec["lattice"][2]
     L = round(spec["beta"] / spec["dtau"])
     n = -(-L // spec["n_stab"])
@@ -209,7 +212,7 @@ def algorithmic_fp64_flops(spec, n_chains, accepts, attempts, G_bonds, prec):
     per_attempt = sum(2 * m * m + 2 * m for m in ms) + a * sum(4 * m * m + m for m in ms)
     flips = 2 * L * N * per_attempt
     if prec == 0:
-        prop = sum(4 * L * (6 * G_bonds * m + N * m) for m in ms)
+        prop = sum(4 * L * (4 * G_bonds * m + 2 * N * m) for m in ms)
         qr = sum(2 * n * 6 * N * m * m for m in ms)
         gram = sum(2 * n * 2 * N * m * m for m in ms)
     else:

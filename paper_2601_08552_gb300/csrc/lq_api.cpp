@@ -498,6 +498,14 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
       vcf[t] = (float)vc[t]; vsf[t] = (float)vs[t];
     }
     for (int i = 0; i < ci.N; ++i) { ep[i] = Lt->eps[i]; ce[i] = lq_onsite_factor(p.dtau, Lt->eps[i]); cef[i] = (float)ce[i]; }
+    // families whose bonds share one cosh and hold every site once take the
+    // two-FMA form on FP64 panels: -tanh in the FP64 table, the cosh product
+    // applied once per slice (FP32 panels keep the four-term form)
+    double cprod = 1.0;
+    const unsigned unif = lq_uniform_families(lq_lattice_get_view(Lt), p.dtau, &cprod);
+    for (int g = 0; g < ci.G && g < 32; ++g)
+      if ((unif >> g) & 1u)
+        for (int t = fo[g]; t < fo[g + 1]; ++t) vs[t] = lq_bond_tanh(p.dtau, vk[t]);
     auto up = [&](void* dst, const void* src, size_t bytes) {
       return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S->st);
     };
@@ -548,6 +556,7 @@ static lq_status create_impl(const lq_lattice* const* lats, const lq_params* par
     D.lat.N = ci.N; D.lat.nb = ci.nb; D.lat.G = ci.G;
     D.lat.fam_off = d_fo; D.lat.bond_i = d_bi; D.lat.bond_j = d_bj;
     D.lat.bond_c = d_bc; D.lat.bond_s = d_bs; D.lat.bond_cf = d_bcf; D.lat.bond_sf = d_bsf; D.lat.bond_k = d_bk;
+    D.lat.unif = unif; D.lat.cprod = cprod;
     D.lat.ceps = Lt->has_eps ? d_ce : nullptr;
     D.lat.cepsf = Lt->has_eps ? d_cef : nullptr;
     D.lat.eps = Lt->has_eps ? d_ep : nullptr;

@@ -37,9 +37,15 @@ struct LqLatticeDev {
   const int* bond_i;        // nb
   const int* bond_j;        // nb
   const double* bond_c;     // cosh(dtau k_b)
-  const double* bond_s;     // -sinh(dtau k_b)
-  const float* bond_cf;     // the same in FP32 (mixed-precision panels)
+  const double* bond_s;     // -sinh(dtau k_b); -tanh(dtau k_b) in the families of `unif`
+  const float* bond_cf;     // cosh and -sinh in FP32 (FP32 panels, always the four-term form)
   const float* bond_sf;
+  // bit g: every bond of family g has the same cosh c_g and the family holds
+  // every site exactly once, so on FP64 panels its factor is applied as
+  // [[1, t], [t, 1]] blocks (t = -tanh(dtau k_b)) and the scalar c_g waits
+  // until the end of the slice; cprod is the product of those c_g
+  unsigned unif;
+  double cprod;
   const double* bond_k;     // k_b (kinetic-energy measurement)
   const double* ceps;       // exp(-dtau eps_i), or nullptr when eps == 0
   const float* cepsf;

@@ -39,6 +39,34 @@ static inline void lq_bond_factors(double dtau, double k, double* c, double* s) 
 }
 static inline double lq_onsite_factor(double dtau, double eps) { return std::exp(-dtau * eps); }
 
+// Checkerboard families in the two-FMA form: bit g is set when every bond of
+// family g has the same cosh c_g and the family holds N/2 bonds.  Families
+// never repeat a site, so such a family holds every site exactly once and its
+// factor is c_g times [[1, t], [t, 1]] blocks with t = -tanh(dtau k_b); the
+// scalar c_g commutes with everything and is applied once per slice.
+// *cprod is the product of those c_g.  Only the first 32 families qualify.
+static inline unsigned lq_uniform_families(const lq_lattice_view& v, double dtau, double* cprod) {
+  unsigned mask = 0;
+  *cprod = 1.0;
+  if (v.N & 1) return 0;
+  for (int g = 0; g < v.G && g < 32; ++g) {
+    const int b0 = v.fam_off[g], b1 = v.fam_off[g + 1];
+    if (2 * (b1 - b0) != v.N) continue;
+    double c0, s0, c, s;
+    lq_bond_factors(dtau, v.sorted_k[b0], &c0, &s0);
+    bool ok = true;
+    for (int b = b0; b < b1 && ok; ++b) {
+      lq_bond_factors(dtau, v.sorted_k[b], &c, &s);
+      ok = c == c0 && v.sorted_i[b] != v.sorted_j[b];
+    }
+    if (!ok) continue;
+    mask |= 1u << g;
+    *cprod *= c0;
+  }
+  return mask;
+}
+static inline double lq_bond_tanh(double dtau, double k) { return -std::tanh(dtau * k); }
+
 // Degree of the Taylor polynomial that stands for e^{-dtau K} in the exact
 // kinetic mode, for theta = dtau max_i sum_j |K_ij| >= ||dtau K||: the
 // smallest q whose remainder bound theta^{q+1} / (q+1)! / (1 - theta/(q+2))

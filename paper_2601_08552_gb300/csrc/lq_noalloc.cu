@@ -43,12 +43,17 @@ cudaError_t upload_factors(const lq_lattice_view& v, double dtau, unsigned char*
   double c[CH], s[CH];
   float cf[CH], sf[CH];
   cudaError_t e = cudaSuccess;
+  double cprod;
+  const unsigned unif = lq_uniform_families(v, dtau, &cprod);
+  int g = 0;
   for (int b0 = 0; b0 < v.nb && e == cudaSuccess; b0 += CH) {
     const int n = std::min(CH, v.nb - b0);
     for (int t = 0; t < n; ++t) {
       lq_bond_factors(dtau, v.sorted_k[b0 + t], &c[t], &s[t]);
       cf[t] = (float)c[t];
       sf[t] = (float)s[t];
+      while (g + 1 < v.G && b0 + t >= v.fam_off[g + 1]) ++g;
+      if (g < 32 && ((unif >> g) & 1u)) s[t] = lq_bond_tanh(dtau, v.sorted_k[b0 + t]);
     }
     e = cudaMemcpyAsync(base + o_bc + (size_t)b0 * 8, c, (size_t)n * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_bs + (size_t)b0 * 8, s, (size_t)n * 8, cudaMemcpyHostToDevice, st);
@@ -184,6 +189,8 @@ extern "C" lq_status lq_sweep_noalloc(const lq_lattice* lat, const lq_params* p,
   D.lat.bond_j = (const int*)(base + o_bj);
   D.lat.bond_c = (const double*)(base + o_bc);
   D.lat.bond_s = (const double*)(base + o_bs);
+  D.lat.cprod = 1.0;
+  D.lat.unif = lq_uniform_families(v, p->dtau, &D.lat.cprod);
   D.lat.bond_cf = (const float*)(base + o_bcf);
   D.lat.bond_sf = (const float*)(base + o_bsf);
   D.lat.bond_k = (const double*)(base + o_bk);

@@ -118,6 +118,20 @@ struct Smem {
   int buf_bytes, M, MP;
 };
 
+// The dynamic shared memory as an array.  A pointer rebased on it is known
+// to the compiler to point into shared memory, so accesses through it are
+// shared loads and stores rather than generic ones (which cost a generic
+// address resolution each).  Only for buffers that the plan keeps in shared
+// memory: every buffer of a small plan (BIG = false).
+extern __shared__ __align__(16) char lq_dyn_smem[];
+template <class T> __device__ __forceinline__ T* sh_rebase(T* p) {
+  return (T*)(lq_dyn_smem + ((size_t)__cvta_generic_to_shared(p) - (size_t)__cvta_generic_to_shared(lq_dyn_smem)));
+}
+template <bool BIG, class T> __device__ __forceinline__ T* plan_ptr(T* p) {
+  if (BIG) return p;
+  return sh_rebase(p);
+}
+
 __device__ inline Smem carve(const SmemPlan& p, char* base) {
   Smem s;
   char* mb = p.big ? p.ws + (size_t)blockIdx.x * p.ws_cta : base;
@@ -393,7 +407,7 @@ __device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m
   }
   const int N = C.N;
   const LqLatticeDev& lat = C.lat;
-  R* buf = (R*)sm.buf;
+  R* buf = sh_rebase((R*)sm.buf);  // the staging buffer is in shared memory in every plan
   int cmax = sm.buf_bytes / (int)(sizeof(R) * N);
   if (cmax > m) cmax = m;
   const int8_t* spre = preD >= 0 ? C.s + (size_t)preD * N : nullptr;
@@ -416,21 +430,37 @@ __device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m
       for (int gg = 0; gg < lat.G; ++gg) {
         const int g = (op == 1) ? gg : lat.G - 1 - gg;
         const int b0 = lat.fam_off[g], work = (lat.fam_off[g + 1] - b0) * cw;
-        for (int idx = TID; idx < work; idx += NTHR) {
-          int bb = idx / cw, a = idx - bb * cw;
-          int b = b0 + bb;
-          int i = lat.bond_i[b], j = lat.bond_j[b];
-          R c = bcv[b], s = bsv[b];
-          R xi = buf[i * cw + a], xj = buf[j * cw + a];
-          buf[i * cw + a] = c * xi + s * xj;
-          buf[j * cw + a] = s * xi + c * xj;
+        if (sizeof(R) == 8 && g < 32 && ((lat.unif >> g) & 1u)) {
+          // FP64 panels: c_g [[1, t], [t, 1]] with the scalar c_g deferred to the store
+          for (int idx = TID; idx < work; idx += NTHR) {
+            int bb = idx / cw, a = idx - bb * cw;
+            int b = b0 + bb;
+            int i = lat.bond_i[b], j = lat.bond_j[b];
+            R t = bsv[b];
+            R xi = buf[i * cw + a], xj = buf[j * cw + a];
+            buf[i * cw + a] = xi + t * xj;
+            buf[j * cw + a] = xj + t * xi;
+          }
+        } else {
+          for (int idx = TID; idx < work; idx += NTHR) {
+            int bb = idx / cw, a = idx - bb * cw;
+            int b = b0 + bb;
+            int i = lat.bond_i[b], j = lat.bond_j[b];
+            R c = bcv[b], s = bsv[b];
+            R xi = buf[i * cw + a], xj = buf[j * cw + a];
+            buf[i * cw + a] = c * xi + s * xj;
+            buf[j * cw + a] = s * xi + c * xj;
+          }
         }
         __syncthreads();
       }
     }
+    const bool scale = sizeof(R) == 8 && op != 0 && lat.unif != 0u;
+    const R cpr = (R)lat.cprod;
     for (int idx = TID; idx < tot; idx += NTHR) {
       int i = idx / cw, a = idx - i * cw;
       R v = buf[idx];
+      if (scale) v *= cpr;
       if (op == 2 && ceps) v *= ceps[i];
       if (spost) v *= (R)dfac(C, sigma, spost[i]);
       dst[(size_t)i * ld + c0 + a] = v;
@@ -640,6 +670,7 @@ template <class RowT> struct OpsF64 {
     __device__ void st(int i, V v) const { t[i] = v; }
   };
   __device__ static TRef tref(Smem& sm, int sg) { return TRef{sm.T[sg]}; }
+  __device__ static TRef tref_at(double* Tsg, const Smem&) { return TRef{Tsg}; }
   __device__ static V zero() { return 0.0; }
   __device__ static void acc(V& s, Row a, V t) { s = fma((double)a, t, s); }
   __device__ static void accT(V& s, V t, Row a) { s = fma(t, (double)a, s); }
@@ -724,6 +755,10 @@ struct OpsDW {
   };
   __device__ static TRef tref(Smem& sm, int sg) {
     float* h = (float*)sm.T[sg];
+    return TRef{h, h + (size_t)sm.M * sm.MP};
+  }
+  __device__ static TRef tref_at(double* Tsg, const Smem& sm) {
+    float* h = (float*)Tsg;
     return TRef{h, h + (size_t)sm.M * sm.MP};
   }
   __device__ static V zero() { return dw{0.f, 0.f}; }
@@ -815,7 +850,7 @@ struct OpsDW {
 // ratio, the quotient, the product and one update per site for both spins at
 // once, and moves every m-length product off it.
 // ---------------------------------------------------------------------------
-template <class R, class Ops, int MT>
+template <class R, class Ops, int MT, bool BIG>
 __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag,
                                 Smem& sm) {
   PhaseTimer pt_(PH_FLIP);
@@ -834,7 +869,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   const size_t per_site = (size_t)4 * MP * sizeof(Row) + 8 + sizeof(U) + 4 + 4;
   int cs = (int)(sm.buf_bytes / per_site);
   if (cs > 512) cs = 512;
-  Row* rrow = (Row*)sm.buf;
+  Row* rrow = plan_ptr<BIG>((Row*)sm.buf);
   Row* lrow = rrow + (size_t)2 * cs * MP;
   double* racc = (double*)(lrow + (size_t)2 * cs * MP);  // accepted ratios (packed), multiplied per chunk
   U* uni = (U*)(racc + cs);
@@ -858,7 +893,9 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   const V id_p = Ops::of(lam0 ? 1.0 : 1.0 / C.delta_p), id_m = Ops::of(lam0 ? 1.0 : 1.0 / C.delta_m);
   const int warp = TID >> 5, lane = TID & 31;
   const bool leader = warp == sm.ip[14];
-  V* const win0 = (V*)sm.win;
+  V* const win0 = plan_ptr<BIG>((V*)sm.win);
+  double* const T0s = plan_ptr<BIG>(sm.T[0]);
+  double* const T1s = plan_ptr<BIG>(sm.T[1]);
   // window buffers of spin sg: X (K x MP), Y (K x MP), G (K x KP), c (K), c-scaled G factors (K x K)
   auto Xb = [&](int sg) { return win0 + (size_t)sg * LQ_WIN_ELEMS(MP); };
   auto Yb = [&](int sg) { return Xb(sg) + K * MP; };
@@ -910,7 +947,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         const int b = e % MT, t = (e / MT) % K, xy = (e / (MT * K)) & 1, sg = e / (2 * MT * K);
         const int m = sg ? m1 : m0;
         if (e < NXY && t < kw && b < m) {
-          const typename Ops::TRef T = Ops::tref(sm, sg);
+          const typename Ops::TRef T = Ops::tref_at(sg ? T1s : T0s, sm);
           const Row* row = (xy ? lrow : rrow) + ((size_t)sg * cs + t0 + t) * MP;
           V acc[GP];
 #pragma unroll
@@ -1051,7 +1088,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         const int b = e % MT, a = (e / MT) % MT, sg = e / (MT * MT);
         const int m = sg ? m1 : m0;
         if (e < NT && a < m && b < m) {
-          const typename Ops::TRef T = Ops::tref(sm, sg);
+          const typename Ops::TRef T = Ops::tref_at(sg ? T1s : T0s, sm);
           const V* Xs = Xb(sg);
           const V* Ys = Yb(sg);
           V tv = T.ld(a * MP + b);
@@ -1379,10 +1416,10 @@ template <class R, class Ops, bool BIG>
 __device__ void flip_slice_any(LqChainDev& C, int l, R* a, R* b, const R* c, const R* d, uint32_t tag, Smem& sm) {
   const int m = max(C.ns[0], C.ns[1]);
   if (BIG && m > LQ_NS_SMALL) flip_slice_big<R, Ops>(C, l, a, b, c, d, tag, sm);
-  else if (m <= 4) flip_slice_pair<R, Ops, 4>(C, l, a, b, c, d, tag, sm);
-  else if (m <= 8) flip_slice_pair<R, Ops, 8>(C, l, a, b, c, d, tag, sm);
-  else if (m <= 16) flip_slice_pair<R, Ops, 16>(C, l, a, b, c, d, tag, sm);
-  else flip_slice_pair<R, Ops, 32>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 4) flip_slice_pair<R, Ops, 4, BIG>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 8) flip_slice_pair<R, Ops, 8, BIG>(C, l, a, b, c, d, tag, sm);
+  else if (m <= 16) flip_slice_pair<R, Ops, 16, BIG>(C, l, a, b, c, d, tag, sm);
+  else flip_slice_pair<R, Ops, 32, BIG>(C, l, a, b, c, d, tag, sm);
 }
 
 // T (FP64, ld MP) -> double-word halves in place of T[sg]
@@ -2139,7 +2176,7 @@ __global__ void __launch_bounds__(LQ_THREADS, BIG ? 1 : 2)
     if (q >= n_order) break;
     LqChainDev* g = chains + order[q];
     load_chain(g, sm);
-    LqChainDev& C = *sm.C;
+    LqChainDev& C = *sh_rebase(sm.C);  // the descriptor copy is in shared memory in every plan
     // a chain runs caps[q] sweeps (n_sweeps without caps); with a budget it
     // starts no further sweep that, judged by the one just done, would end
     // more than budget_ns after the chain was taken
