@@ -863,7 +863,6 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   // one accumulator per m-long product: on GB300 a dependent FP64 FMA costs
   // its sub-partition the same 64 cycles as an independent one, so partial
   // sums would only add instructions
-  constexpr int GP = 1;
   const int N = C.N, MP = sm.MP;
   const int m0 = C.ns[0], m1 = C.ns[1];
   const size_t per_site = (size_t)4 * MP * sizeof(Row) + 8 + sizeof(U) + 4 + 4;
@@ -949,19 +948,28 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         if (e < NXY && t < kw && b < m) {
           const typename Ops::TRef T = Ops::tref_at(sg ? T1s : T0s, sm);
           const Row* row = (xy ? lrow : rrow) + ((size_t)sg * cs + t0 + t) * MP;
-          V acc[GP];
+          // operands of CH terms loaded ahead of their FMAs, so that the
+          // loads overlap and the dependent FMA chain does not wait on each
+          constexpr int CH = MT < 8 ? MT : 8;
+          V acc = Ops::zero();
 #pragma unroll
-          for (int q = 0; q < GP; ++q) acc[q] = Ops::zero();
+          for (int a0 = 0; a0 < MT; a0 += CH) {
+            V tv[CH];
+            Row rv[CH];
 #pragma unroll
-          for (int a = 0; a < MT; ++a)
-            if (a < m) {
-              if (xy) Ops::accT(acc[a % GP], T.ld(b * MP + a), row[a]);
-              else Ops::acc(acc[a % GP], row[a], T.ld(a * MP + b));
+            for (int q = 0; q < CH; ++q) {
+              const int a = a0 + q;
+              tv[q] = a < m ? T.ld(xy ? b * MP + a : a * MP + b) : Ops::zero();
+              rv[q] = a < m ? row[a] : (Row)0;
             }
-          V v = Ops::finish(acc[0]);
 #pragma unroll
-          for (int q = 1; q < GP; ++q) v = Ops::add(v, Ops::finish(acc[q]));
-          (xy ? Yb(sg) : Xb(sg))[t * MP + b] = v;
+            for (int q = 0; q < CH; ++q)
+              if (a0 + q < m) {
+                if (xy) Ops::accT(acc, tv[q], rv[q]);
+                else Ops::acc(acc, rv[q], tv[q]);
+              }
+          }
+          (xy ? Yb(sg) : Xb(sg))[t * MP + b] = Ops::finish(acc);
         }
       }
       __syncthreads();
@@ -981,10 +989,21 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         if (u < kw && v < kw && upd) {
           const V* xr = Xb(h) + u * MP;
           const Row* lr = lrow + ((size_t)h * cs + t0 + v) * MP;
+          constexpr int CH = MT < 8 ? MT : 8;
           V acc = Ops::zero();
 #pragma unroll
-          for (int b = 0; b < MT; ++b)
-            if (b < m) Ops::accT(acc, xr[b], lr[b]);
+          for (int b0 = 0; b0 < MT; b0 += CH) {
+            V xv[CH];
+            Row lv[CH];
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+              xv[q] = b0 + q < m ? xr[b0 + q] : Ops::zero();
+              lv[q] = b0 + q < m ? lr[b0 + q] : (Row)0;
+            }
+#pragma unroll
+            for (int q = 0; q < CH; ++q)
+              if (b0 + q < m) Ops::accT(acc, xv[q], lv[q]);
+          }
           G = Ops::finish(acc);
         }
         // C: the serial chain of both spins, sites t0 .. t0 + kw - 1
