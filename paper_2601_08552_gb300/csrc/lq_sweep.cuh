@@ -418,7 +418,25 @@ __device__ void prop(const LqChainDev& C, int sigma, R* dst, const S* src, int m
   for (int c0 = 0; c0 < m; c0 += cmax) {
     const int cw = min(cmax, m - c0);
     const int tot = N * cw;
-    for (int idx = TID; idx < tot; idx += NTHR) {
+    // four elements' loads in flight per thread before their stores
+    int idx = TID;
+    for (; idx + 3 * NTHR < tot; idx += 4 * NTHR) {
+      R v4[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = (idx + q * NTHR) / cw, a = idx + q * NTHR - i * cw;
+        v4[q] = (R)src[(size_t)i * ld + c0 + a];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = (idx + q * NTHR) / cw;
+        R v = v4[q];
+        if (spre) v *= (R)dfac(C, sigma, spre[i]);
+        if (op == 1 && ceps) v *= ceps[i];
+        buf[idx + q * NTHR] = v;
+      }
+    }
+    for (; idx < tot; idx += NTHR) {
       int i = idx / cw, a = idx - i * cw;
       R v = (R)src[(size_t)i * ld + c0 + a];
       if (spre) v *= (R)dfac(C, sigma, spre[i]);
@@ -920,8 +938,26 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       const R* lp = sg ? Lp1 : Lp0;
       Row* rr = rrow + (size_t)sg * cs * MP;
       Row* ll = lrow + (size_t)sg * cs * MP;
-      for (int ii = TID / MT; ii < cn; ii += NTHR / MT) {
-        const int a = TID % MT;
+      // four rows' loads in flight per thread before their stores
+      const int a = TID % MT, step = NTHR / MT;
+      int ii = TID / MT;
+      for (; ii + 3 * step < cn; ii += 4 * step) {
+        R r4[4], l4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const size_t g = (size_t)(i0 + ii + q * step) * m + a;
+          r4[q] = a < m ? rp[g] : (R)0;
+          l4[q] = a < m ? lp[g] : (R)0;
+        }
+        if (a < m) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            rr[(size_t)(ii + q * step) * MP + a] = (Row)r4[q];
+            ll[(size_t)(ii + q * step) * MP + a] = (Row)l4[q];
+          }
+        }
+      }
+      for (; ii < cn; ii += step) {
         if (a < m) {
           rr[(size_t)ii * MP + a] = (Row)rp[(size_t)(i0 + ii) * m + a];
           ll[(size_t)ii * MP + a] = (Row)lp[(size_t)(i0 + ii) * m + a];
@@ -1110,10 +1146,16 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
           const typename Ops::TRef T = Ops::tref_at(sg ? T1s : T0s, sm);
           const V* Xs = Xb(sg);
           const V* Ys = Yb(sg);
+          V ys[K], xs[K];
+#pragma unroll
+          for (int t = 0; t < K; ++t) {
+            ys[t] = t < kw ? Ys[t * MP + a] : Ops::zero();
+            xs[t] = t < kw ? Xs[t * MP + b] : Ops::zero();
+          }
           V tv = T.ld(a * MP + b);
 #pragma unroll
           for (int t = 0; t < K; ++t)
-            if (t < kw) tv = Ops::fnma(Ys[t * MP + a], Xs[t * MP + b], tv);
+            if (t < kw) tv = Ops::fnma(ys[t], xs[t], tv);
           T.st(a * MP + b, tv);
         }
       }
