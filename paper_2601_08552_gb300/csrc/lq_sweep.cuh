@@ -506,7 +506,23 @@ __device__ void gram(const RA* A, int lda, int ma, const RB* B, int ldb, int mb,
       if (o < nout) {
         a = o / mb;
         b = o - a * mb;
-        for (int i = part; i < N; i += tpo)
+        int i = part;
+        // four rows' operands in flight before their FMAs (same summation order)
+        for (; i + 3 * tpo < N; i += 4 * tpo) {
+          Acc a4[4], b4[4];
+          bool k4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const size_t r = (size_t)(i + q * tpo);
+            a4[q] = (Acc)A[r * lda + a];
+            b4[q] = (Acc)B[r * ldb + b];
+            k4[q] = !sub || sub[r] == mval;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (k4[q]) acc += a4[q] * b4[q];
+        }
+        for (; i < N; i += tpo)
           if (!sub || sub[i] == mval) acc += (Acc)A[(size_t)i * lda + a] * (Acc)B[(size_t)i * ldb + b];
       }
       for (int off = tpo >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(FULL, acc, off, tpo);
