@@ -481,12 +481,14 @@ lq_status lq_device_fp64_rate(double ms, double* host_tflops, double* host_cycle
  * LQ_EINVAL, LQ_ECUDA. */
 lq_status lq_probe_gram(int32_t N, int32_t m, int32_t variant, int32_t n_panels, double* host_us,
                         double* host_max_rel_err);
-/* Test hook (no counterpart in the paper): the field-flip loop divides by
- * 1 + Delta G_tt with a hardware reciprocal seed and one third-order
- * Newton-Raphson step instead of the IEEE division sequence.  This evaluates
- * that quotient and the IEEE quotient d[k] / r[k] on the device for n host
- * operand pairs (host arrays of n; outputs host arrays of n).  Allocates
- * device memory; synchronous.  Errors: LQ_EINVAL, LQ_ECUDA. */
+/* Test hook (no counterpart in the paper): the field-flip loops form
+ * c = Delta / (1 + Delta G_tt) with a hardware reciprocal seed and one
+ * third-order Newton-Raphson step instead of the IEEE division sequence (the
+ * four-warp path as the quotient d / r, the paired path as the reciprocal
+ * 1 / (1/Delta + G_tt), which is this quotient at d = 1 bit for bit).  This
+ * evaluates that quotient and the IEEE quotient d[k] / r[k] on the device for
+ * n host operand pairs (host arrays of n; outputs host arrays of n).
+ * Allocates device memory; synchronous.  Errors: LQ_EINVAL, LQ_ECUDA. */
 lq_status lq_test_quotient(int32_t n, const double* host_d, const double* host_r, double* host_q,
                            double* host_q_ieee);
 

@@ -24,8 +24,9 @@ def test_fp64_instruction_cost_and_rate():
 
 
 def test_flip_quotient_against_ieee():
-    """The flip loop divides with a reciprocal seed and one third-order
-    Newton-Raphson step; against CUDA's IEEE quotient it stays within 4 ulp
+    """The flip loops divide (and take reciprocals, d = 1) with a reciprocal
+    seed and one third-order Newton-Raphson step; against CUDA's IEEE
+    quotient it stays within 4 ulp
     over operands spanning the ratio factors 1 + Delta G_tt the loop meets
     (and far beyond), and is exact for d = 0 and r = 1."""
     torch = pytest.importorskip("torch")
@@ -40,6 +41,7 @@ def test_flip_quotient_against_ieee():
     r = rng.choice([-1, 1], n) * np.exp(rng.uniform(-40, 40, n))
     r[:1000] = 1.0 + rng.uniform(-1, 1, 1000) * 1e-12  # near 1
     d[1000:2000] = 0.0
+    d[2000:3000] = 1.0  # the paired flip loop's reciprocal 1 / r is this quotient at d = 1
     q, qi = flip_quotient(d, r)
     assert np.all(q[1000:2000] == 0.0)
     assert np.array_equal(q[:1000][r[:1000] == 1.0], d[:1000][r[:1000] == 1.0])
