@@ -751,7 +751,7 @@ def main():
                   enumerate(["flips", "propagation", "qr", "block_inverse", "swaps", "measure"])}
         if pr[8:12].sum() > 0:  # parts of the flips (chains of up to 32 particles per spin)
             phases.update({k: round(float(pr[8 + i]) / tot, 4) for i, k in
-                           enumerate(["flip_staging", "flip_xy_products", "flip_serial_chain", "flip_update_T"])})
+                           enumerate(["flip_staging", "flip_first_window", "flip_serial_chain", "flip_loop_rest"])})
         # per-chain means of the measured observables (warm-up and timed sweeps)
         if sp is spec:
             run.obs[prec] = np.stack([sim.records(c).mean(axis=0) for c in range(n_chains)])

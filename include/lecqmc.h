@@ -272,8 +272,11 @@ lq_status lq_sim_stats(lq_sim* sim, int32_t chain, int64_t* host_counts4);
  * removal (Givens rotations, M^-1, downdate, rotated Q panels) and the
  * addition (vector propagation and Gram-Schmidt); then four parts of the flip
  * cycles of chains with at most 32 particles per spin: row staging and
- * write-back, the window's x/y products, the serial per-site chain (with the
- * window block), the recurrences and the update of T (host array of 12). */
+ * write-back, the products and blocks of each chunk's first window, the
+ * leader warp's serial per-site chains, and the rest of the window loop (the
+ * leader forming the next window's block and waiting for the other warps,
+ * which meanwhile run the recurrences, the update of T and the next window's
+ * products) (host array of 12). */
 lq_status lq_sim_profile(lq_sim* sim, int32_t chain, int64_t* host_cycles12);
 /* Test hook: panel j of the right (side 0) or left (side 1) chain of a spin,
  * as FP64 host arrays Q (N x N_sigma) and V (N_sigma x N_sigma, nullable). */

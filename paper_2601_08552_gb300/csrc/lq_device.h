@@ -103,8 +103,8 @@ struct LqChainDev {
   long long prof[12];       // cycles per phase: flips, propagation, QR, block inverse, swaps, measurement;
                             // then two parts of the swaps: removal (with Q streaming), addition; then
                             // four parts of the flips (chains of up to 32 particles per spin): row staging and
-                            // write-back, the window's x/y products, the serial chain (with the window
-                            // block), the recurrences and the update of T
+                            // write-back, each chunk's first window products and blocks, the leader's serial
+                            // chains, the rest of the window loop (next block, waits)
   long long sweep_ns_last;  // wall time of the chain's most recent sweep (device global timer)
   long long sweep_ns_sum;   // summed wall time of its sweeps (the caller may reset it)
   long long sweep_ns_ring[LQ_SWEEP_RING];  // wall time of sweep k at [k % LQ_SWEEP_RING]

@@ -865,25 +865,59 @@ struct OpsDW {
 // two spins' factors and one K x K rank-1 update; the m-length dot products
 // are batched per window, the x/y recurrences run after the window's sites,
 // and T takes the window's rank-1 terms at its end.
-// For m <= 32 particles per spin the window is K = 4 sites, the work of a
-// window is spread over the CTA and the serial chain of BOTH spins runs on one
-// leader warp:
-//   A  (all warps)  x_t = R~_t T and y_t = T L~_t of both spins, one output
-//                   per thread;
-//   B  (leader)     the window blocks G = X L~_W of both spins, one element
-//                   per lane (lanes 0-15 spin up, 16-31 spin down);
-//   C  (leader)     per site: G[t][t], the ratio factor 1 + Delta G[t][t] of
-//                   each spin, their product by one shuffle between the half
-//                   warps, the Metropolis test, and the rank-1 update of the
-//                   rest of each block (one element per lane);
-//   D  (4 warps)    the x and y recurrences of both spins, one warp each;
-//   E  (all warps)  T -= sum_t (c_t y_t) x_t^T of both spins.
+//
+// For m <= 32 particles per spin the window is K = 4 sites and the serial
+// chain of BOTH spins runs on one leader warp (lanes 0-15 spin up, 16-31 spin
+// down, one block element per lane).  The other warps (the workers) run one
+// window behind it, so that the leader never waits for the dense work:
+//   leader, window w:  the chain of w's sites on its block G_w (in registers),
+//                      then the c-scaled factors CG_w (CG[j][t] = c_t G[j][t],
+//                      CG[t][j] = c_t G[t][j], j > t) for the workers, then
+//                      the next window's block from three K x K blocks that
+//                      the workers formed against T_w (the T before window w):
+//                        A1 = Z L~_{w+1} ... rows of w+1, columns of w,
+//                        A2 = X_w L~_{w+1},  B = Z L~_{w+1} (rows and columns of w+1),
+//                      Z = R~_{w+1} T_w.  Window w's flips act on them by the
+//                      same recurrences as on x and y,
+//                        A1[u][j] -= CG[t][j] A1[u][t],  A2[j][v] -= CG[j][t] A2[t][v]  (j > t),
+//                      and G_{w+1} = B - sum_t c_t A1[u][t] A2[t][v]: eleven
+//                      FP64 instructions on the leader instead of the window
+//                      products, the recurrences and the T update.
+//   workers, window w: (with CG_{w-1}) the x/y recurrences of window w-1 and
+//                      T_w = T_{w-1} - sum_t (c_t y_t) x_t^T, then x_t, y_t
+//                      of window w, z of window w+1 and the three blocks.
+// They meet at named barriers: the leader arrives at P once CG_w is stored
+// and the workers wait there before window w-1's update; the workers arrive
+// at Q once the blocks of window w+1 are stored and the leader waits there.
+// Each alternates between two barrier ids and two buffers by window parity,
+// so neither side can arrive twice at one barrier before the other has
+// passed it.  A window of the chunk's first pair (x, y of window 0, its block
+// and the blocks of window 1) is formed by the whole CTA before the loop.
 // On GB300 an FP64 warp instruction occupies its sub-partition for tens of
-// cycles whatever the number of active lanes, so the per-site chain is the
+// cycles whatever the number of active lanes, so the leader's chain is the
 // count of dependent FP64 instructions on one warp: this path keeps it at the
 // ratio, the quotient, the product and one update per site for both spins at
 // once, and moves every m-length product off it.
 // ---------------------------------------------------------------------------
+// Named barriers with compile-time ids (so the kernel reserves only the ids it
+// names).  Ids of the pipelined pair path: 1 and 2 (P: a window's CG stored;
+// the leader arrives, the workers wait), 3 and 4 (Q: the next window's blocks
+// stored; the workers arrive, the leader waits), 5 (the workers among
+// themselves).  The m > 32 path uses 1-3 in another phase of the sweep, in
+// which every instance completes before it returns.
+template <int ID> __device__ __forceinline__ void nbar_sync(int n) {
+  asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(n) : "memory");
+}
+template <int ID> __device__ __forceinline__ void nbar_arrive(int n) {
+  asm volatile("bar.arrive %0, %1;" ::"n"(ID), "r"(n) : "memory");
+}
+#define LQ_BAR_P 1
+#define LQ_BAR_Q 3
+#define LQ_BAR_W 5
+// the barrier of parity p (0 or 1) of a pair of ids (warp-uniform branch)
+#define LQ_NBAR_SYNC(B, p, n) ((p) ? nbar_sync<(B) + 1>(n) : nbar_sync<(B)>(n))
+#define LQ_NBAR_ARRIVE(B, p, n) ((p) ? nbar_arrive<(B) + 1>(n) : nbar_arrive<(B)>(n))
+
 template <class R, class Ops, int MT, bool BIG>
 __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* Lp0, const R* Lp1, uint32_t tag,
                                 Smem& sm) {
@@ -891,9 +925,8 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   typedef typename Ops::V V;
   typedef typename Ops::Row Row;
   typedef typename Ops::U U;
-  constexpr int K = 4, KP = K + 1;
-  constexpr int NXY = 2 * 2 * K * MT;  // x and y outputs of both spins
-  constexpr int NT = 2 * MT * MT;      // T elements of both spins
+  constexpr int K = 4, KK = K * K;
+  constexpr int NT = 2 * MT * MT;  // T elements of both spins
   // one accumulator per m-long product: on GB300 a dependent FP64 FMA costs
   // its sub-partition the same 64 cycles as an independent one, so partial
   // sums would only add instructions
@@ -925,18 +958,151 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   // 1/Delta for s sp > 0 and < 0, formed once per slice (an IEEE division is a dozen FP64 instructions)
   const V id_p = Ops::of(lam0 ? 1.0 : 1.0 / C.delta_p), id_m = Ops::of(lam0 ? 1.0 : 1.0 / C.delta_m);
   const int warp = TID >> 5, lane = TID & 31;
-  const bool leader = warp == sm.ip[14];
+  const int lw = sm.ip[14];
+  const bool leader = warp == lw;
+  // workers: the other warps, renumbered 0 .. NWK/32 - 1
+  const int NWK = NTHR - 32, wt = (warp < lw ? warp : warp - 1) * 32 + lane;
   V* const win0 = plan_ptr<BIG>((V*)sm.win);
   double* const T0s = plan_ptr<BIG>(sm.T[0]);
   double* const T1s = plan_ptr<BIG>(sm.T[1]);
-  // window buffers of spin sg: X (K x MP), Y (K x MP), G (K x KP), c (K), c-scaled G factors (K x K)
+  // window buffers of spin sg: X, Y, Z (K x MP each), then by window parity p the blocks A1, A2, B
+  // (K x K each), the c-scaled factors CG (K x K) and c (K)
   auto Xb = [&](int sg) { return win0 + (size_t)sg * LQ_WIN_ELEMS(MP); };
   auto Yb = [&](int sg) { return Xb(sg) + K * MP; };
-  auto Gb = [&](int sg) { return Yb(sg) + K * MP; };
-  auto cb = [&](int sg) { return Gb(sg) + K * KP; };
-  auto CGb = [&](int sg) { return cb(sg) + K; };
-  // sub-phase cycles: staging, window products, recurrences and T (thread 0's clock between the
-  // barriers) and the serial chain (the leader's own clock from the window block to its last store)
+  auto Zb = [&](int sg) { return Yb(sg) + K * MP; };
+  auto BLb = [&](int sg, int p, int kind) { return Zb(sg) + K * MP + (p * 3 + kind) * KK; };
+  auto CGb = [&](int sg, int p) { return Zb(sg) + K * MP + 6 * KK + p * KK; };
+  auto cb = [&](int sg, int p) { return Zb(sg) + K * MP + 8 * KK + p * K; };
+
+  // x_t = R~_t T and y_t = T L~_t of the window at t0 (kw sites), z_t = R~_t T of the window at t0 + K
+  // (kz sites); element (sg, kind, t, b), kind 0 x, 1 y, 2 z
+  auto products = [&](int t0, int kw, int kz, int tid, int nth) {
+    constexpr int NE = 2 * 3 * K * MT;
+#pragma unroll 1
+    for (int e = tid; e < NE; e += nth) {
+      const int b = e % MT, t = (e / MT) % K, kind = (e / (MT * K)) % 3, sg = e / (3 * MT * K);
+      const int m = sg ? m1 : m0;
+      if (t < (kind == 2 ? kz : kw) && b < m) {
+        const typename Ops::TRef T = Ops::tref_at(sg ? T1s : T0s, sm);
+        const Row* row = (kind == 1 ? lrow : rrow) + ((size_t)sg * cs + t0 + (kind == 2 ? K : 0) + t) * MP;
+        // operands of CH terms loaded ahead of their FMAs, so that the
+        // loads overlap and the dependent FMA chain does not wait on each
+        constexpr int CH = MT < 8 ? MT : 8;
+        V acc = Ops::zero();
+#pragma unroll
+        for (int a0 = 0; a0 < MT; a0 += CH) {
+          V tv[CH];
+          Row rv[CH];
+#pragma unroll
+          for (int q = 0; q < CH; ++q) {
+            const int a = a0 + q;
+            tv[q] = a < m ? T.ld(kind == 1 ? b * MP + a : a * MP + b) : Ops::zero();
+            rv[q] = a < m ? row[a] : (Row)0;
+          }
+#pragma unroll
+          for (int q = 0; q < CH; ++q)
+            if (a0 + q < m) {
+              if (kind == 1) Ops::accT(acc, tv[q], rv[q]);
+              else Ops::acc(acc, rv[q], tv[q]);
+            }
+        }
+        (kind == 0 ? Xb(sg) : kind == 1 ? Yb(sg) : Zb(sg))[t * MP + b] = Ops::finish(acc);
+      }
+    }
+  };
+  // K x K blocks (m-long dots of a window vector with a staged L~ row): kind 0 A1 = Z L~_{t0+K},
+  // 1 A2 = X L~_{t0+K}, 2 B = Z L~_{t0+K}... rows of Z or X, columns at t0 (A1) or t0 + K (A2, B),
+  // into parity p; kind 3 (with g0) the window's own block X L~_{t0} into the B slot of parity 0.
+  // Entries outside the windows are zero.
+  auto blocks = [&](int t0, int kw, int kz, int p, bool g0, int tid, int nth) {
+    const int nk = g0 ? 4 : 3;
+#pragma unroll 1
+    for (int e = tid; e < 2 * nk * KK; e += nth) {
+      const int v = e % K, u = (e / K) % K, kind = (e / KK) % nk, sg = e / (nk * KK);
+      const int m = sg ? m1 : m0;
+      const bool rz = kind == 0 || kind == 2, cz = kind == 1 || kind == 2;
+      V acc = Ops::zero();
+      if (u < (rz ? kz : kw) && v < (cz ? kz : kw)) {
+        const V* xr = (rz ? Zb(sg) : Xb(sg)) + u * MP;
+        const Row* lr = lrow + ((size_t)sg * cs + t0 + (cz ? K : 0) + v) * MP;
+        constexpr int CH = MT < 8 ? MT : 8;
+#pragma unroll
+        for (int b0 = 0; b0 < MT; b0 += CH) {
+          V xv[CH];
+          Row lv[CH];
+#pragma unroll
+          for (int q = 0; q < CH; ++q) {
+            xv[q] = b0 + q < m ? xr[b0 + q] : Ops::zero();
+            lv[q] = b0 + q < m ? lr[b0 + q] : (Row)0;
+          }
+#pragma unroll
+          for (int q = 0; q < CH; ++q)
+            if (b0 + q < m) Ops::accT(acc, xv[q], lv[q]);
+        }
+        acc = Ops::finish(acc);
+      }
+      (kind == 3 ? BLb(sg, 0, 2) : BLb(sg, p, kind))[u * K + v] = acc;
+    }
+  };
+  // the x (xy = 0) or y (xy = 1) recurrences of spin sg over a window of kw sites with the factors
+  // of parity p: x_j -= CG[j][t] x_t, y_j -= CG[t][j] y_t (j > t, t ascending), then y_t <- c_t y_t;
+  // one warp, element (j, b)
+  auto recur = [&](int kw, int p, int sg, int xy) {
+    const int m = sg ? m1 : m0;
+    V* Wm = xy ? Yb(sg) : Xb(sg);
+    const V* CG = CGb(sg, p);
+    constexpr int RE = (K * MT + 31) / 32;
+    for (int t = 0; t + 1 < kw; ++t) {
+#pragma unroll
+      for (int it = 0; it < RE; ++it) {
+        const int e = lane + 32 * it, j = e / MT, b = e % MT;
+        if (e < K * MT && j > t && j < kw && b < m)
+          Wm[j * MP + b] = Ops::fnma(xy ? CG[t * K + j] : CG[j * K + t], Wm[t * MP + b], Wm[j * MP + b]);
+      }
+      __syncwarp();
+    }
+    if (xy) {
+      const V* cw = cb(sg, p);
+#pragma unroll
+      for (int it = 0; it < RE; ++it) {
+        const int e = lane + 32 * it, j = e / MT, b = e % MT;
+        if (e < K * MT && j < kw && b < m) Wm[j * MP + b] = Ops::mul(cw[j], Wm[j * MP + b]);
+      }
+    }
+  };
+  // T <- T - sum_t (c_t y_t) x_t^T over a window of kw sites, element (sg, a, b)
+  auto tupdate = [&](int kw, int tid, int nth) {
+#pragma unroll 1
+    for (int e = tid; e < NT; e += nth) {
+      const int b = e % MT, a = (e / MT) % MT, sg = e / (MT * MT);
+      const int m = sg ? m1 : m0;
+      if (a < m && b < m) {
+        const typename Ops::TRef T = Ops::tref_at(sg ? T1s : T0s, sm);
+        const V* Xs = Xb(sg);
+        const V* Ys = Yb(sg);
+        V ys[K], xs[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+          ys[t] = t < kw ? Ys[t * MP + a] : Ops::zero();
+          xs[t] = t < kw ? Xs[t * MP + b] : Ops::zero();
+        }
+        V tv = T.ld(a * MP + b);
+#pragma unroll
+        for (int t = 0; t < K; ++t)
+          if (t < kw) tv = Ops::fnma(ys[t], xs[t], tv);
+        T.st(a * MP + b, tv);
+      }
+    }
+  };
+  // the x/y recurrences (four warp tasks: spin x {x, y}) and the T update of a finished window
+  auto window_update = [&](int kw, int p) {
+    for (int d = wt >> 5; d < 4; d += NWK >> 5) recur(kw, p, d >> 1, d & 1);
+    nbar_sync<LQ_BAR_W>(NWK);
+    tupdate(kw, wt, NWK);
+  };
+
+  // sub-phase cycles: staging and write-back, the chunk's first window products, the leader's chains
+  // (its own clock) and the rest of the window loop (thread 0's clock, less the chains)
   __shared__ long long tsub, tchain;
   if (TID == 0) tsub = clock64();
   auto lap = [&](int k) {
@@ -987,80 +1153,34 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
       uni[ii] = Ops::make_u(u53(w[0], w[1]) * (s > 0 ? thr_p : thr_m));
       sf[ii] = s;
     }
+    if (TID == 0) tchain = 0;
     __syncthreads();
     lap(8);
-    int wsign = 1, nacc = 0, nbad = 0;  // kept by the leader's lane 0
-    for (int t0 = 0; t0 < cn; t0 += K) {
-      const int kw = min(K, cn - t0);
-      // A: x_t = R_t T (xy = 0) and y_t = T L_t (xy = 1), element (sg, xy, t, b)
-#pragma unroll 1
-      for (int e = TID; e < NXY; e += NTHR) {
-        const int b = e % MT, t = (e / MT) % K, xy = (e / (MT * K)) & 1, sg = e / (2 * MT * K);
-        const int m = sg ? m1 : m0;
-        if (e < NXY && t < kw && b < m) {
-          const typename Ops::TRef T = Ops::tref_at(sg ? T1s : T0s, sm);
-          const Row* row = (xy ? lrow : rrow) + ((size_t)sg * cs + t0 + t) * MP;
-          // operands of CH terms loaded ahead of their FMAs, so that the
-          // loads overlap and the dependent FMA chain does not wait on each
-          constexpr int CH = MT < 8 ? MT : 8;
-          V acc = Ops::zero();
-#pragma unroll
-          for (int a0 = 0; a0 < MT; a0 += CH) {
-            V tv[CH];
-            Row rv[CH];
-#pragma unroll
-            for (int q = 0; q < CH; ++q) {
-              const int a = a0 + q;
-              tv[q] = a < m ? T.ld(xy ? b * MP + a : a * MP + b) : Ops::zero();
-              rv[q] = a < m ? row[a] : (Row)0;
-            }
-#pragma unroll
-            for (int q = 0; q < CH; ++q)
-              if (a0 + q < m) {
-                if (xy) Ops::accT(acc, tv[q], rv[q]);
-                else Ops::acc(acc, rv[q], tv[q]);
-              }
-          }
-          (xy ? Yb(sg) : Xb(sg))[t * MP + b] = Ops::finish(acc);
-        }
-      }
+    const int nw = (cn + K - 1) / K;
+    // the chunk's first window: x, y of window 0 and z of window 1, then window 0's block and the
+    // blocks of window 1, by the whole CTA
+    {
+      const int kw = min(K, cn), kz = nw > 1 ? min(K, cn - K) : 0;
+      products(0, kw, kz, TID, NTHR);
       __syncthreads();
-      lap(9);
-      if (leader) {
+      blocks(0, kw, kz, 1, true, TID, NTHR);
+      __syncthreads();
+    }
+    lap(9);
+    if (leader) {
+      int wsign = 1, nacc = 0, nbad = 0;  // kept by lane 0
+      // lane 16 h + 4 u + v holds G[u][v] of spin h in a register for the
+      // whole window: every read of the serial chain is a shuffle
+      const int h = lane >> 4, hl = lane & 15;
+      const int m = h ? m1 : m0;
+      const int u = hl >> 2, v = hl & 3, hb = lane & 16;
+      const bool upd = m > 0 && !lam0;
+      const int sp = C.charge ? 1 : (h == 0 ? 1 : -1);
+      V G = upd ? BLb(h, 0, 2)[u * K + v] : Ops::zero();
+      long long tch = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int t0 = w * K, kw = min(K, cn - t0);
         const long long tl0 = clock64();
-        // lane 16 h + 4 u + v holds G[u][v] of spin h in a register for the
-        // whole window: every read of the serial chain is a shuffle
-        const int h = lane >> 4, hl = lane & 15;
-        const int m = h ? m1 : m0;
-        const int u = hl >> 2, v = hl & 3, hb = lane & 16;
-        const bool upd = m > 0 && !lam0;
-        // B: G[u][v] = x_u . L~_v of this half's spin (one dependent chain:
-        // on GB300 a dependent FP64 FMA costs its sub-partition no more than
-        // an independent one)
-        V G = Ops::zero();
-        if (u < kw && v < kw && upd) {
-          const V* xr = Xb(h) + u * MP;
-          const Row* lr = lrow + ((size_t)h * cs + t0 + v) * MP;
-          constexpr int CH = MT < 8 ? MT : 8;
-          V acc = Ops::zero();
-#pragma unroll
-          for (int b0 = 0; b0 < MT; b0 += CH) {
-            V xv[CH];
-            Row lv[CH];
-#pragma unroll
-            for (int q = 0; q < CH; ++q) {
-              xv[q] = b0 + q < m ? xr[b0 + q] : Ops::zero();
-              lv[q] = b0 + q < m ? lr[b0 + q] : (Row)0;
-            }
-#pragma unroll
-            for (int q = 0; q < CH; ++q)
-              if (b0 + q < m) Ops::accT(acc, xv[q], lv[q]);
-          }
-          G = Ops::finish(acc);
-        }
-        // C: the serial chain of both spins, sites t0 .. t0 + kw - 1
-        const int sp = C.charge ? 1 : (h == 0 ? 1 : -1);
-        V* cw = cb(h);  // c_t of this half's spin (0 when not flipped)
         int sacc = 0, sbad = 0, sneg = 0;
         // the window's fields and uniforms, loaded before the chain starts
         int sw[K];
@@ -1070,6 +1190,8 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
           sw[t] = t < kw ? sf[t0 + t] : 1;
           uw[t] = uni[t0 + (t < kw ? t : 0)];
         }
+        // c of site v (cv) and of site u (cu) of this half's spin, 0 when not flipped
+        V cv = Ops::zero(), cu = Ops::zero();
 #pragma unroll
         for (int t = 0; t < K; ++t) {
           if (t < kw) {
@@ -1084,7 +1206,7 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
             // every lane takes part in every shuffle (the halves' spins may differ
             // in m; an empty spin's block is zero)
             const V g = Ops::from_lane(G, hb + 5 * t);
-            const V w = Ops::mul(gut, gtv);   // G[u][t] G[t][v], independent of this site's decision
+            const V wp = Ops::mul(gut, gtv);  // G[u][t] G[t][v], independent of this site's decision
             const V rs = Ops::add(idd, g);     // 1/Delta_sigma + G_tt of this half's spin
             const V c = Ops::rcp(rs);          // Delta/(1 + Delta G_tt), used if accepted
             const V ro = Ops::xor_(rs, 16);    // the other spin's factor
@@ -1094,8 +1216,10 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
             const bool acc = Ops::accept(r, uu, &neg, &bad);
             neg ^= (ddn >> (s > 0 ? 0 : 1)) & 1;
             const bool flip = acc && upd;
-            if (flip && u > t && v > t) G = Ops::fnma(c, w, G);
-            if (hl == 0) cw[t] = flip ? c : Ops::zero();
+            if (flip && u > t && v > t) G = Ops::fnma(c, wp, G);
+            const V cf = flip ? c : Ops::zero();
+            if (v == t) cv = cf;
+            if (u == t) cu = cf;
             sacc |= acc << t;
             sneg |= neg << t;
             sbad |= bad << t;
@@ -1108,94 +1232,78 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
           nbad += __popc(sbad);
           if (__popc(sacc & sneg) & 1) wsign = -wsign;
         }
+        // c-scaled factors of the recurrences: CG[j][t] = c_t G[j][t] (lane (j, t), j > t) and
+        // CG[t][j] = c_t G[t][j] (lane (t, j)), for the workers and the next block
+        const V cg = (u < kw && v < kw && u != v) ? Ops::mul(u > v ? cv : cu, G) : Ops::zero();
+        CGb(h, w & 1)[u * K + v] = cg;
+        if (u == 0) cb(h, w & 1)[v] = cv;
         __syncwarp();
-        // c-scaled factors of the recurrences: CG[j][t] = c_t G[j][t] (j > t), CG[t][j] = c_t G[t][j]
-        {
-          V val = Ops::zero();
-          if (u > v && u < kw) val = Ops::mul(cw[v], G);
-          else if (u < v && v < kw) val = Ops::mul(cw[u], G);
-          CGb(h)[u * K + v] = val;
-        }
-        __syncwarp();
-        if (lane == 0) tchain = clock64() - tl0;
-      }
-      __syncthreads();
-      if (TID == 0) {
-        // the leader's chain time, and the rest of this stretch (the hand-over at the barrier) with D and E
-        const long long t = clock64();
-        C.prof[10] += tchain;
-        C.prof[11] += (t - tsub) - tchain;
-        tsub = t;
-      }
-      // D: x_j -= c_t G[j][t] x_t and y_j -= c_t G[t][j] y_t (j > t), t ascending; then y_t <- c_t y_t.
-      // Warp w < 4 takes spin w >> 1, x (even w) or y (odd w), element (j, b)
-      if (warp < 4) {
-        const int sg = warp >> 1, xy = warp & 1, m = sg ? m1 : m0;
-        V* Wm = xy ? Yb(sg) : Xb(sg);
-        const V* CG = CGb(sg);
-        constexpr int RE = (K * MT + 31) / 32;
-        for (int t = 0; t + 1 < kw; ++t) {
+        LQ_NBAR_ARRIVE(LQ_BAR_P, w & 1, NTHR);
+        tch += clock64() - tl0;
+        if (w + 1 < nw) {
+          // the next window's block: the three blocks against T_w, taken through this window's flips
+          const int p = (w + 1) & 1;
+          if (w >= 1) LQ_NBAR_SYNC(LQ_BAR_Q, p, NTHR);  // window 1's blocks came with window 0's
+          V a1 = BLb(h, p, 0)[u * K + v], a2 = BLb(h, p, 1)[u * K + v];
+          const V bb = BLb(h, p, 2)[u * K + v];
 #pragma unroll
-          for (int it = 0; it < RE; ++it) {
-            const int e = lane + 32 * it, j = e / MT, b = e % MT;
-            if (e < K * MT && j > t && j < kw && b < m)
-              Wm[j * MP + b] = Ops::fnma(xy ? CG[t * K + j] : CG[j * K + t], Wm[t * MP + b], Wm[j * MP + b]);
+          for (int t = 0; t + 1 < K; ++t) {
+            if (t + 1 < kw) {
+              const V cgtv = Ops::from_lane(cg, hb + 4 * t + v);  // CG[t][v]
+              const V cgut = Ops::from_lane(cg, hb + 4 * u + t);  // CG[u][t]
+              const V a1ut = Ops::from_lane(a1, hb + 4 * u + t);
+              const V a2tv = Ops::from_lane(a2, hb + 4 * t + v);
+              if (v > t) a1 = Ops::fnma(cgtv, a1ut, a1);
+              if (u > t) a2 = Ops::fnma(cgut, a2tv, a2);
+            }
           }
-          __syncwarp();
-        }
-        if (xy) {
-          const V* cw = cb(sg);
-#pragma unroll
-          for (int it = 0; it < RE; ++it) {
-            const int e = lane + 32 * it, j = e / MT, b = e % MT;
-            if (e < K * MT && j < kw && b < m) Wm[j * MP + b] = Ops::mul(cw[j], Wm[j * MP + b]);
-          }
-        }
-      }
-      __syncthreads();
-      // E: T <- T - sum_t (c_t y_t) x_t^T, element (sg, a, b)
-#pragma unroll 1
-      for (int e = TID; e < NT; e += NTHR) {
-        const int b = e % MT, a = (e / MT) % MT, sg = e / (MT * MT);
-        const int m = sg ? m1 : m0;
-        if (e < NT && a < m && b < m) {
-          const typename Ops::TRef T = Ops::tref_at(sg ? T1s : T0s, sm);
-          const V* Xs = Xb(sg);
-          const V* Ys = Yb(sg);
-          V ys[K], xs[K];
-#pragma unroll
-          for (int t = 0; t < K; ++t) {
-            ys[t] = t < kw ? Ys[t * MP + a] : Ops::zero();
-            xs[t] = t < kw ? Xs[t * MP + b] : Ops::zero();
-          }
-          V tv = T.ld(a * MP + b);
+          a1 = Ops::mul(cv, a1);  // c_t A1[u][t] (t = v)
+          V gn = bb;
 #pragma unroll
           for (int t = 0; t < K; ++t)
-            if (t < kw) tv = Ops::fnma(ys[t], xs[t], tv);
-          T.st(a * MP + b, tv);
+            if (t < kw) gn = Ops::fnma(Ops::from_lane(a1, hb + 4 * u + t), Ops::from_lane(a2, hb + 4 * t + v), gn);
+          G = upd ? gn : Ops::zero();
         }
       }
-      __syncthreads();
-      lap(11);
-    }
-    if (leader) {
+      if (lane == 0) tchain = tch;
       // product of the chunk's accepted ratios, lane-parallel
-      typename Ops::Prod wp;
-      wp.init();
+      typename Ops::Prod wpr;
+      wpr.init();
       const V add_p = Ops::of(fabs(dd_p)), add_m = Ops::of(fabs(dd_m));
       for (int ii = lane; ii < cn; ii += 32)
-        if (af[ii]) wp.mul(Ops::mul(Ops::unpack(racc[ii]), sf[ii] > 0 ? add_p : add_m));
+        if (af[ii]) wpr.mul(Ops::mul(Ops::unpack(racc[ii]), sf[ii] > 0 ? add_p : add_m));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) wp.combine_xor(o);
+      for (int o = 16; o > 0; o >>= 1) wpr.combine_xor(o);
       if (lane == 0) {
         C.cnt[0] += cn;
         C.cnt[1] += nacc;
-        C.logw += wp.log_value();
+        C.logw += wpr.log_value();
         if (wsign < 0) C.sign = -C.sign;
         if (nbad) C.err |= LQ_ERR_NONFINITE;
       }
+    } else {
+      for (int w = 1; w < nw; ++w) {
+        const int t0 = w * K, kw = min(K, cn - t0), kz = w + 1 < nw ? min(K, cn - t0 - K) : 0;
+        LQ_NBAR_SYNC(LQ_BAR_P, (w - 1) & 1, NTHR);  // CG of window w - 1
+        window_update(K, (w - 1) & 1);
+        nbar_sync<LQ_BAR_W>(NWK);
+        products(t0, kw, kz, wt, NWK);
+        if (w + 1 < nw) {
+          nbar_sync<LQ_BAR_W>(NWK);
+          blocks(t0, kw, kz, (w + 1) & 1, false, wt, NWK);
+          LQ_NBAR_ARRIVE(LQ_BAR_Q, (w + 1) & 1, NTHR);
+        }
+      }
+      LQ_NBAR_SYNC(LQ_BAR_P, (nw - 1) & 1, NTHR);
+      window_update(cn - (nw - 1) * K, (nw - 1) & 1);
     }
     __syncthreads();
+    if (TID == 0) {
+      const long long t = clock64();
+      C.prof[10] += tchain;
+      C.prof[11] += (t - tsub) - tchain;
+      tsub = t;
+    }
     // rows back to the panel; accepted sites scale their row by 1 + Delta_sigma
     for (int sg = 0; sg < 2; ++sg) {
       const int m = sg ? m1 : m0;
