@@ -958,10 +958,14 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   // 1/Delta for s sp > 0 and < 0, formed once per slice (an IEEE division is a dozen FP64 instructions)
   const V id_p = Ops::of(lam0 ? 1.0 : 1.0 / C.delta_p), id_m = Ops::of(lam0 ? 1.0 : 1.0 / C.delta_m);
   const int warp = TID >> 5, lane = TID & 31;
-  const int lw = sm.ip[14];
+  const int lw = sm.ip[14], mate = sm.ip[15];
   const bool leader = warp == lw;
-  // workers: the other warps, renumbered 0 .. NWK/32 - 1
-  const int NWK = NTHR - 32, wt = (warp < lw ? warp : warp - 1) * 32 + lane;
+  // workers: the other warps (NWK threads, all in the workers' barriers); the FP64 work goes to
+  // those other than the leader's mate, renumbered 0 .. NFW/32 - 1 (the mate's indexes start beyond
+  // every element count: it takes no element and no recurrence task)
+  const int NWK = NTHR - 32, NFW = mate >= 0 ? NWK - 32 : NWK;
+  const int fw = warp == mate ? NFW / 32 : warp - (warp > lw) - (mate >= 0 && warp > mate);
+  const int wt = warp == mate ? (1 << 30) : fw * 32 + lane;
   V* const win0 = plan_ptr<BIG>((V*)sm.win);
   double* const T0s = plan_ptr<BIG>(sm.T[0]);
   double* const T1s = plan_ptr<BIG>(sm.T[1]);
@@ -1096,9 +1100,9 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   };
   // the x/y recurrences (four warp tasks: spin x {x, y}) and the T update of a finished window
   auto window_update = [&](int kw, int p) {
-    for (int d = wt >> 5; d < 4; d += NWK >> 5) recur(kw, p, d >> 1, d & 1);
+    for (int d = fw; d < 4 && fw < NFW / 32; d += NFW / 32) recur(kw, p, d >> 1, d & 1);
     nbar_sync<LQ_BAR_W>(NWK);
-    tupdate(kw, wt, NWK);
+    tupdate(kw, wt, NFW);
   };
 
   // sub-phase cycles: staging and write-back, the chunk's first window products, the leader's chains
@@ -1287,10 +1291,10 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
         LQ_NBAR_SYNC(LQ_BAR_P, (w - 1) & 1, NTHR);  // CG of window w - 1
         window_update(K, (w - 1) & 1);
         nbar_sync<LQ_BAR_W>(NWK);
-        products(t0, kw, kz, wt, NWK);
+        products(t0, kw, kz, wt, NFW);
         if (w + 1 < nw) {
           nbar_sync<LQ_BAR_W>(NWK);
-          blocks(t0, kw, kz, (w + 1) & 1, false, wt, NWK);
+          blocks(t0, kw, kz, (w + 1) & 1, false, wt, NFW);
           LQ_NBAR_ARRIVE(LQ_BAR_Q, (w + 1) & 1, NTHR);
         }
       }
@@ -2312,11 +2316,15 @@ __device__ inline void store_chain(LqChainDev* g, Smem& sm) {
   __syncthreads();
 }
 
-// The flip warps (one per spin) are picked on two SM sub-partitions that the
-// other resident CTA of this SM does not use: the first CTA on an SM takes
-// sub-partitions {0,1}, the second {2,3} (sub-partition = hardware warp slot
-// mod 4).  FP64 issue on GB300 is per sub-partition, so this keeps four flip
-// warps on four different FP64 pipes.  Any mapping is correct; only speed
+// The leader warp of the field-flip loop (m <= 32) is picked on a sub-partition
+// that the other resident CTA of this SM does not lead from: the first CTA on
+// an SM takes sub-partition 0, the second 2 (sub-partition = hardware warp
+// slot mod 4).  FP64 issue on GB300 is per sub-partition, so this keeps the two
+// leaders' serial chains on different FP64 pipes.  In a 256-thread CTA the
+// other warp on the leader's sub-partition (its mate, sm.ip[15]) takes no
+// FP64 work of the flip loop, so that the chain shares its pipe with fewer
+// warps (the remaining six workers still cover the window products of up to
+// 8 particles per spin in one round).  Any mapping is correct; only speed
 // depends on it.
 static __device__ void pick_flip_warps(int* sm_ctr, Smem& sm) {
   __shared__ int wsub[LQ_THREADS / 32];
@@ -2333,14 +2341,15 @@ static __device__ void pick_flip_warps(int* sm_ctr, Smem& sm) {
   }
   __syncthreads();
   if (TID == 0) {
-    int f0 = -1, f1 = -1;
-    for (int w = 0; w < NTHR / 32; ++w) {
+    int f0 = -1, mate = -1;
+    for (int w = 0; w < NTHR / 32; ++w)
       if (f0 < 0 && wsub[w] == 2 * pair) f0 = w;
-      else if (f1 < 0 && wsub[w] == 2 * pair + 1) f1 = w;
-    }
-    if (f0 < 0 || f1 < 0 || f0 == f1) { f0 = 0; f1 = 1; }
+    if (f0 < 0) f0 = 0;
+    if (NTHR == LQ_THREADS)
+      for (int w = 0; w < NTHR / 32; ++w)
+        if (mate < 0 && w != f0 && wsub[w] == wsub[f0]) mate = w;
     sm.ip[14] = f0;
-    sm.ip[15] = f1;
+    sm.ip[15] = mate;
   }
   __syncthreads();
 }
