@@ -960,12 +960,19 @@ __device__ void flip_slice_pair(LqChainDev& C, int l, R* Rp0, R* Rp1, const R* L
   const int warp = TID >> 5, lane = TID & 31;
   const int lw = sm.ip[14], mate = sm.ip[15];
   const bool leader = warp == lw;
-  // workers: the other warps (NWK threads, all in the workers' barriers); the FP64 work goes to
-  // those other than the leader's mate, renumbered 0 .. NFW/32 - 1 (the mate's indexes start beyond
-  // every element count: it takes no element and no recurrence task)
-  const int NWK = NTHR - 32, NFW = mate >= 0 ? NWK - 32 : NWK;
-  const int fw = warp == mate ? NFW / 32 : warp - (warp > lw) - (mate >= 0 && warp > mate);
-  const int wt = warp == mate ? (1 << 30) : fw * 32 + lane;
+  // workers: the other warps (NWK threads, all in the workers' barriers).  The FP64 work goes to the
+  // warps of fmask, renumbered 0 .. NFW/32 - 1; the others' indexes start beyond every element count
+  // (no element, no recurrence task).  For up to 8 particles per spin (one round of window products
+  // on four warps) these are the warps on the two sub-partitions that neither resident CTA leads
+  // from (sm.ip[13]), so that FP64 bursts of the workers never queue ahead of a leader's chain;
+  // otherwise every worker but the leader's mate.
+  unsigned fmask = ((1u << (NTHR >> 5)) - 1u) & ~(1u << lw);
+  if (mate >= 0) fmask &= ~(1u << mate);
+  if (MT <= 8 && __popc((unsigned)sm.ip[13]) == 4) fmask = (unsigned)sm.ip[13];
+  const int NWK = NTHR - 32, NFW = 32 * __popc(fmask);
+  const bool fwk = (fmask >> warp) & 1u;
+  const int fw = fwk ? __popc(fmask & ((1u << warp) - 1u)) : NFW / 32;
+  const int wt = fwk ? fw * 32 + lane : (1 << 30);
   V* const win0 = plan_ptr<BIG>((V*)sm.win);
   double* const T0s = plan_ptr<BIG>(sm.T[0]);
   double* const T1s = plan_ptr<BIG>(sm.T[1]);
@@ -2323,9 +2330,8 @@ __device__ inline void store_chain(LqChainDev* g, Smem& sm) {
 // leaders' serial chains on different FP64 pipes.  In a 256-thread CTA the
 // other warp on the leader's sub-partition (its mate, sm.ip[15]) takes no
 // FP64 work of the flip loop, so that the chain shares its pipe with fewer
-// warps (the remaining six workers still cover the window products of up to
-// 8 particles per spin in one round).  Any mapping is correct; only speed
-// depends on it.
+// warps; sm.ip[13] lists the warps on sub-partitions 1 and 3, which no CTA
+// leads from.  Any mapping is correct; only speed depends on it.
 static __device__ void pick_flip_warps(int* sm_ctr, Smem& sm) {
   __shared__ int wsub[LQ_THREADS / 32];
   __shared__ int pair;
@@ -2345,9 +2351,13 @@ static __device__ void pick_flip_warps(int* sm_ctr, Smem& sm) {
     for (int w = 0; w < NTHR / 32; ++w)
       if (f0 < 0 && wsub[w] == 2 * pair) f0 = w;
     if (f0 < 0) f0 = 0;
+    unsigned odd = 0u;  // warps on sub-partitions 1 and 3
     if (NTHR == LQ_THREADS)
-      for (int w = 0; w < NTHR / 32; ++w)
+      for (int w = 0; w < NTHR / 32; ++w) {
         if (mate < 0 && w != f0 && wsub[w] == wsub[f0]) mate = w;
+        if ((wsub[w] & 1) && w != f0) odd |= 1u << w;
+      }
+    sm.ip[13] = (int)odd;
     sm.ip[14] = f0;
     sm.ip[15] = mate;
   }
