@@ -3,8 +3,6 @@
 // translation units that instantiate the kernels (one sweep-kernel instance
 // per unit, so that they compile in parallel).
 //
-// the stabilized QR update (LEC-QMC, arXiv 2601.08552).
-//
 // One CTA owns one Markov chain for a whole sweep (persistent over a queue of
 // chains, longest first).  Inside a CTA:
 //   * slice propagation (B_l = e^{-dtau K} e^{-dtau V(s_l)}, Eq. 1 and the
@@ -17,10 +15,11 @@
 //     are batched, and the serial chain of a site is its diagonal block
 //     element, the ratio and a K x K rank-1 update.  Up to 32 particles per
 //     spin one leader warp runs the chain of both spins (K = 4, one block
-//     element per lane, the spins' factors exchanged by one shuffle) and the
-//     whole CTA shares the window's dense work; above 32 a four-warp group per
-//     spin (K = 8) shares it and the m x m matrices sit in a global workspace
-//     per CTA;
+//     element per lane, the spins' factors exchanged by one shuffle) and
+//     forms the next window's block from three K x K blocks, while the other
+//     warps run the window's dense work one window behind it (named
+//     barriers); above 32 a four-warp group per spin (K = 8) shares the dense
+//     work and the m x m matrices sit in a global workspace per CTA;
 //   * particle-hole swaps: removal by permutation + Givens retriangulation
 //     (Eqs. S9-S12), addition by propagating one vector and orthogonalising
 //     it twice against each Q_i (Eqs. S1-S8, Eq. 4); the target is uniform
