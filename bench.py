@@ -659,6 +659,8 @@ def main():
                     help="only the paper-shaped uneven flat-band batch (1024 chains, N_sigma up to 384), beta scaled")
     ap.add_argument("--nsigma-scan", action="store_true",
                     help="only the cost-against-N_sigma study (flat-band chains, one sweep per N_sigma)")
+    ap.add_argument("--nsigma-sizes", default="",
+                    help="comma-separated N_sigma values for --nsigma-scan (default: 16 to 384)")
     ap.add_argument("--serving-window", type=float, default=10.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=["gas32x32", "gas64x64"],
                     help="gas64x64: the 64x64 mixed-precision comparison (512 chains, ~10 s per sweep)")
@@ -700,7 +702,8 @@ def main():
 
     stream = torch.cuda.current_stream()
     if args.nsigma_scan:
-        print(json.dumps(dict(study="cost against N_sigma", **nsigma_scan(lq, torch, stream))), flush=True)
+        kw = dict(sizes=tuple(int(x) for x in args.nsigma_sizes.split(","))) if args.nsigma_sizes else {}
+        print(json.dumps(dict(study="cost against N_sigma", **nsigma_scan(lq, torch, stream, **kw))), flush=True)
         return
     if args.uneven_full:
         print(json.dumps(dict(study="paper-shaped uneven batch", **uneven_full_leg(lq, inputs, torch, stream))),
