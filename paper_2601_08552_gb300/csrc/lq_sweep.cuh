@@ -890,8 +890,8 @@ struct OpsDW {
 // at Q once the blocks of window w+1 are stored and the leader waits there.
 // Each alternates between two barrier ids and two buffers by window parity,
 // so neither side can arrive twice at one barrier before the other has
-// passed it.  A window of the chunk's first pair (x, y of window 0, its block
-// and the blocks of window 1) is formed by the whole CTA before the loop.
+// passed it.  Each chunk of staged sites starts with the whole CTA forming
+// x, y and the block of its window 0 and the three blocks of its window 1.
 // On GB300 an FP64 warp instruction occupies its sub-partition for tens of
 // cycles whatever the number of active lanes, so the leader's chain is the
 // count of dependent FP64 instructions on one warp: this path keeps it at the
